@@ -1,0 +1,203 @@
+/*
+ * bf.h -- C ABI of the GB300 butterfly-factorisation (IBF-MAT) apply library.
+ *
+ * The library evaluates the discretised oscillatory integral transform
+ *     g = K f,   K_ij = alpha(x_i, xi_j) exp(2 pi i Phi(x_i, xi_j)),
+ * x_i = i/N, xi_j = j - N/2 (Sec. 5, Eq. 1D-FIO / 1D-xandxi, 0-based), for
+ * many right-hand sides at once, as
+ *     g = sum_k diag(a_k) BF(e^{2 pi i Phi}) diag(b_k) f          (Sec. 1, Eq. tg)
+ * where alpha ~ sum_k a_k(x) b_k(xi) comes from Algorithm 1 (Sec. 2.1) and BF
+ * is the butterfly factorisation of Eq. (BFM), Sec. 4,
+ *     e^{2 pi i Phi} ~ U^L G^{L-1} ... G^h M^h (H^h)^* ... (H^1)^* (V^0)^*,
+ * built from the interpolative low-rank factors of Algorithm 2 by the
+ * recursion of Algorithm 4.1 (Eqs. 1, 2, 3, bf3 and the switch step).
+ *
+ * Conventions for every entry point:
+ *  - Return value: BF_OK or an error code; bf_last_error() then returns a
+ *    thread-local message describing the last failure on the calling thread.
+ *  - Pointers documented as "device" are CUDA device pointers on the plan's
+ *    device; "host" pointers are ordinary (preferably page-locked) memory.
+ *  - Complex data are interleaved (re, im): "c64" = 2 x float, "c128" =
+ *    2 x double.  Right-hand-side blocks are row-major [N][m] with the m
+ *    right-hand sides innermost (PyTorch's layout for a contiguous (N, m)).
+ *  - The caller owns F and G; the plan owns its factors and workspace.
+ *  - Calls on one plan are not thread-safe, except that bf_apply calls on
+ *    distinct streams may overlap once the plan is uploaded and its
+ *    workspace is reserved for each stream (bf_reserve).
+ *  - No entry point calls exit(), abort() or traps on the device; GPU-side
+ *    failures (a bounded wait that ran out) are reported as BF_ERR_TIMEOUT
+ *    by bf_sync_status().
+ */
+#ifndef BF_H
+#define BF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bf_plan bf_plan;
+
+typedef enum {
+    BF_OK = 0,
+    BF_ERR_ARG = 1,         /* invalid argument (size, pointer, option)            */
+    BF_ERR_NOMEM = 2,       /* host or device allocation failed / budget exceeded  */
+    BF_ERR_CUDA = 3,        /* a CUDA runtime call failed                           */
+    BF_ERR_STATE = 4,       /* call out of order (e.g. apply before factor)        */
+    BF_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out                  */
+    BF_ERR_ACCURACY = 6,    /* construction could not meet the tolerance           */
+    BF_ERR_IO = 7,          /* plan file could not be read or written               */
+    BF_ERR_UNSUPPORTED = 8  /* feature not built for these parameters              */
+} bf_status;
+
+/* Arithmetic of the apply. */
+typedef enum {
+    BF_PREC_F64 = 0,    /* plain form: one launch per butterfly stage, c128 data    */
+    BF_PREC_F32 = 1,    /* fused two-pass persistent apply, c64 data (default)      */
+    BF_PREC_BF16X3 = 2  /* c64 data; level products on tensor cores with hi/lo BF16 */
+} bf_precision;
+
+/* Built-in phase functions Phi(x, xi) (numbering shared with the test oracle). */
+typedef enum {
+    BF_PHASE_DFT = 0,     /* x xi                                                         */
+    BF_PHASE_FIO = 1,     /* x xi + c(x)|xi|, c(x) = (2 + s sin 2 pi x)/16 (Sec. 5, 1D FIO) */
+    BF_PHASE_FIO_PW = 2,  /* x xi + c|xi| for x < 1/2; x xi - c|xi|/2 for x >= 1/2      */
+    BF_PHASE_ONES = 3,    /* 0                                                            */
+    BF_PHASE_SEP = 4,     /* 0.3 sin(2 pi x) + xi^2/(4N)  (R(A,B) of Eq. RAB vanishes)    */
+    BF_PHASE_USER = 100   /* Phi given by the phi callback                               */
+} bf_phase_kind;
+
+/* Built-in amplitudes alpha(x, xi). */
+typedef enum {
+    BF_AMP_ONE = 0,       /* 1                                                 */
+    BF_AMP_SMOOTH = 1,    /* 1 + 0.25 sin(2 pi x) cos(2 pi xi / N)  (rank 2)   */
+    BF_AMP_USER = 100     /* alpha given by the alpha callback (complex)       */
+} bf_amp_kind;
+
+/* User phase: returns Phi(x, xi) (real).  Only its value mod 1 matters. */
+typedef double (*bf_phase_fn)(double x, double xi, void* user);
+/* User amplitude: writes alpha(x, xi) = *re + i *im. */
+typedef void (*bf_amp_fn)(double x, double xi, void* user, double* re, double* im);
+
+/* The operator: an N x N block of the transform on a grid of n_global points
+ * (row0 = col0 = 0 and n_global = N for the whole transform). */
+typedef struct {
+    int64_t N;            /* power of two                                       */
+    int phase_kind;       /* bf_phase_kind                                      */
+    double phase_param;   /* s of BF_PHASE_FIO / FIO_PW (1.0 if 0 is given)      */
+    int amp_kind;         /* bf_amp_kind                                        */
+    bf_phase_fn phi;      /* used when phase_kind == BF_PHASE_USER              */
+    bf_amp_fn alpha;      /* used when amp_kind == BF_AMP_USER                  */
+    void* user;           /* passed to the callbacks                            */
+} bf_kernel_desc;
+
+typedef struct {
+    int r;                /* interpolation points per node (r_eps); 0: from eps           */
+    int n0;               /* leaf size of both trees (power of two, default 1, Fig. 2)    */
+    int split;            /* 1: one BF; 2: four N/2 x N/2 sub-BFs (rows and columns cut    *
+                           *    at N/2, i.e. at x = 1/2 and xi = 0)                        */
+    int amp_rank;         /* rank parameter of Algorithm 1 (default 20)                    */
+    int amp_oversample;   /* oversampling q of Algorithm 1 (default 5)                     */
+    double amp_tol;       /* relative singular-value cut for r_alpha (default 1e-13)       */
+    uint64_t seed;        /* sampling seed of Algorithm 1 (default 0)                      */
+    int keep_host;        /* keep the FP64 host factors after upload (default 1)           */
+    int device;           /* CUDA device of the plan (default 0)                           */
+} bf_options;
+
+typedef struct {
+    int64_t N;
+    int r, n0, L, h, l1;   /* levels: V at l1, H l1+1..h, switch at h, G h+1..L-l1, U at L-l1 */
+    int r_alpha;           /* amplitude rank                                                */
+    int split;             /* 1 or 2                                                        */
+    int64_t host_bytes;    /* FP64 host factors                                             */
+    int64_t dev_bytes_f64; /* device factors, c128                                          */
+    int64_t dev_bytes_f32; /* device factors, c64 (also used by BF16X3)                     */
+    int64_t dev_bytes_bf16;/* device hi/lo BF16 copies of the level matrices                */
+    int uploaded;
+    double amp_sigma_ratio;/* sigma_{r_alpha+1}/sigma_1 of the amplitude (0 if exact)        */
+} bf_plan_info;
+
+/* Fill *opt with the defaults listed above. */
+bf_status bf_default_options(bf_options* opt);
+
+/* Create a plan for the operator *desc to tolerance eps (the target relative
+ * l2 error eps^b of Sec. 5).  With opt->r == 0 the interpolation rank is taken
+ * from eps by the rule r = 4 + ceil(-log10 eps), measured for 1D-FIO-like
+ * phases (Table 1D-FIO).  opt may be NULL.  No GPU work.  *out owns the plan.
+ * Errors: BF_ERR_ARG (N not a power of two, N too small for this r and n0,
+ * eps not in (0, 1), bad kinds/callbacks). */
+bf_status bf_plan_create(const bf_kernel_desc* desc, double eps, const bf_options* opt,
+                         bf_plan** out);
+
+/* Build the factorisation on the host in FP64: the amplitude split by
+ * Algorithm 1 and, for each sub-BF, the factors V^0, H^l, M^h, G^l, U^L of
+ * Eq. (BFM) from Algorithms 2 and 4.1.  Idempotent.  No GPU work. */
+bf_status bf_factor(bf_plan* plan);
+
+/* Copy the factors to the plan's device in the layouts the kernels consume
+ * (c128 for F64, c64 for F32, plus BF16 hi/lo level matrices).  Called by the
+ * first bf_apply if not called before; call it before any stream capture.
+ * Errors: BF_ERR_STATE (not factored), BF_ERR_NOMEM, BF_ERR_CUDA. */
+bf_status bf_upload(bf_plan* plan);
+
+/* Pre-allocate device workspace for applies of up to m_max right-hand sides at
+ * precision prec (so that later bf_apply calls allocate nothing and can be
+ * captured in a CUDA graph).  Errors: BF_ERR_NOMEM, BF_ERR_CUDA. */
+bf_status bf_reserve(bf_plan* plan, bf_precision prec, int64_t m_max);
+
+/* G = K F for m right-hand sides, asynchronously on `stream` (a cudaStream_t,
+ * NULL = legacy default stream).  F, G: device, [N][m], c128 for BF_PREC_F64
+ * and c64 otherwise; G must not alias F.  Uses the plan's workspace (grown
+ * with cudaMalloc when m exceeds the reserved size -- not capture-safe).
+ * Errors: BF_ERR_ARG (m < 1, NULL pointers), BF_ERR_STATE, BF_ERR_NOMEM,
+ * BF_ERR_CUDA (launch failure), BF_ERR_UNSUPPORTED (no kernels for this r). */
+bf_status bf_apply(bf_plan* plan, bf_precision prec, const void* F, int64_t m, void* G,
+                   void* stream);
+
+/* Same as bf_apply but F and G are HOST buffers: copies F to the device,
+ * applies, copies G back, and synchronises `stream` before returning. */
+bf_status bf_apply_host(bf_plan* plan, bf_precision prec, const void* F_host, int64_t m,
+                        void* G_host, void* stream);
+
+/* Result of device-side checks of earlier applies on `stream` (synchronises):
+ * BF_OK or BF_ERR_TIMEOUT. */
+bf_status bf_sync_status(bf_plan* plan, void* stream);
+
+bf_status bf_plan_get_info(const bf_plan* plan, bf_plan_info* info);
+
+/* Read-only view of an FP64 host factor array of sub-BF `block` (0 unless
+ * split == 2, then block = 2*row_half + col_half).  what: 0 a (amplitude,
+ * [r_alpha][N] c128), 1 b ([r_alpha][N] c128), 2 Mv ([r][nv] real), 3 EV
+ * ([2^l1][N] c128), 4 MH (level, [r][2r] real), 5 EH (level, [P][2][r] c128),
+ * 6 S ([P][r][r] c128), 7 MG (level, [2][r][r] real), 8 FG (level, [P][2][r]
+ * c128), 9 MU ([nu][r] real), 10 EU ([2^l1][N] c128).  *data points into the
+ * plan (valid until bf_destroy), *count = number of doubles.  Requires a
+ * factored plan with host factors kept.  For tests and inspection. */
+bf_status bf_plan_view(const bf_plan* plan, int block, int what, int level,
+                       const double** data, int64_t* count);
+
+/* Save / load a factored plan (versioned header + FP64 factors), so that a
+ * restarted server skips bf_factor.  Callbacks are not saved: a loaded plan
+ * with user kinds can be applied but not re-factored. */
+bf_status bf_plan_save(const bf_plan* plan, const char* path);
+bf_status bf_plan_load(const char* path, const bf_options* opt, bf_plan** out);
+
+/* Release the plan and its host and device memory.  NULL-safe. */
+void bf_destroy(bf_plan* plan);
+
+/* The mock-Chebyshev index grid of Eq. (gdA)/(gdB) for a node of n indices:
+ * writes min(n, r) increasing 0-based offsets to out, *count = their number. */
+bf_status bf_grid_indices(int64_t n, int r, int64_t* out, int* count);
+
+/* Thread-local description of the last error on this thread. */
+const char* bf_last_error(void);
+
+/* Library version string. */
+const char* bf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BF_H */

@@ -29,10 +29,16 @@ def rsvd_sampled(entry, m, n, r, q=5, sweeps=2, seed=0):
         J = np.union1d(rng.choice(n, min(n, r * q), replace=False), pi_col)
         _, _, piv = sla.qr(entry(allr, J).conj().T, mode='economic', pivoting=True)
         pi_row = np.sort(piv[:min(r, piv.size)])
-    # column and row bases
-    Qc, _, _ = sla.qr(entry(allr, pi_col), mode='economic', pivoting=True)
-    Qr, _, _ = sla.qr(entry(pi_row, allc).conj().T, mode='economic', pivoting=True)
-    Qc, Qr = Qc[:, :r], Qr[:, :r]
+    # column and row bases: the leading r columns of Q, with r capped at the
+    # numerical rank the pivoted QR reveals (|R_kk| > 1e-14 |R_00|); columns past
+    # it span nothing of K and would make the sampled core below singular.
+    def basis(A):
+        Q, R, _ = sla.qr(A, mode='economic', pivoting=True)
+        d = np.abs(np.diag(R))
+        k = int(np.sum(d > 1e-14 * d[0])) if d.size and d[0] > 0 else 0
+        return Q[:, :min(r, max(k, 1))]
+    Qc = basis(entry(allr, pi_col))
+    Qr = basis(entry(pi_row, allc).conj().T)
     # core from a few extra sampled rows/columns
     J = np.union1d(pi_col, rng.choice(n, min(n, r * q), replace=False))
     I = np.union1d(pi_row, rng.choice(m, min(m, r * q), replace=False))

@@ -1,0 +1,168 @@
+"""Python binding of the butterfly-factorisation apply (same names as the C ABI).
+
+Only argument marshalling lives here: every step of the apply runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+F64, F32, BF16X3 = L.PREC_F64, L.PREC_F32, L.PREC_BF16X3
+PREC_NAMES = {"f64": F64, "f32": F32, "bf16x3": BF16X3}
+
+
+def grid_indices(n, r):
+    """Mock-Chebyshev index grid of Eq. (gdA)/(gdB) (0-based offsets)."""
+    out = (ctypes.c_int64 * max(1, min(n, r)))()
+    cnt = ctypes.c_int()
+    L.check(L.lib().bf_grid_indices(n, r, out, ctypes.byref(cnt)), "bf_grid_indices")
+    return np.array(out[:cnt.value], dtype=np.int64)
+
+
+def default_options():
+    o = L.Options()
+    L.check(L.lib().bf_default_options(ctypes.byref(o)), "bf_default_options")
+    return o
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A factored operator g = K f (bf_plan_create + bf_factor)."""
+
+    def __init__(self, N, eps=1e-6, phase_kind=L.PHASE_FIO, phase_param=1.0, amp_kind=L.AMP_ONE,
+                 r=0, n0=1, split=1, seed=0, keep_host=True, device=0, factor=True, phi=None, alpha=None,
+                 _handle=None):
+        self._lib = L.lib()
+        self._h = ctypes.c_void_p()
+        self._keep = []
+        if _handle is not None:
+            self._h = _handle
+        else:
+            d = L.KernelDesc()
+            d.N = N
+            d.phase_kind = phase_kind
+            d.phase_param = phase_param
+            d.amp_kind = amp_kind
+            if phi is not None:
+                cb = L.PHASE_FN(lambda x, xi, u: phi(x, xi))
+                self._keep.append(cb)
+                d.phi = cb
+            if alpha is not None:
+                def _amp(x, xi, u, re, im):
+                    v = complex(alpha(x, xi))
+                    re[0], im[0] = v.real, v.imag
+                cb2 = L.AMP_FN(_amp)
+                self._keep.append(cb2)
+                d.alpha = cb2
+            o = default_options()
+            o.r, o.n0, o.split, o.seed, o.keep_host, o.device = r, n0, split, seed, int(keep_host), device
+            L.check(self._lib.bf_plan_create(ctypes.byref(d), eps, ctypes.byref(o), ctypes.byref(self._h)),
+                    "bf_plan_create")
+            if factor:
+                self.factor()
+
+    # -- life cycle
+    def factor(self):
+        L.check(self._lib.bf_factor(self._h), "bf_factor")
+        return self
+
+    def upload(self):
+        L.check(self._lib.bf_upload(self._h), "bf_upload")
+        return self
+
+    def reserve(self, prec, m_max):
+        L.check(self._lib.bf_reserve(self._h, prec, int(m_max)), "bf_reserve")
+        return self
+
+    def close(self):
+        if self._h:
+            self._lib.bf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- inspection
+    def info(self):
+        i = L.PlanInfo()
+        L.check(self._lib.bf_plan_get_info(self._h, ctypes.byref(i)), "bf_plan_get_info")
+        return {k: getattr(i, k) for k, _ in L.PlanInfo._fields_}
+
+    def view(self, what, level=0, block=0):
+        """Copy of a host FP64 factor array (see bf_plan_view); complex ones as complex128."""
+        ptr = ctypes.POINTER(ctypes.c_double)()
+        cnt = ctypes.c_int64()
+        L.check(self._lib.bf_plan_view(self._h, block, what, level, ctypes.byref(ptr), ctypes.byref(cnt)),
+                "bf_plan_view")
+        a = np.ctypeslib.as_array(ptr, shape=(cnt.value,)).copy() if cnt.value else np.zeros(0)
+        if what in (0, 1, 3, 5, 6, 8, 10):
+            a = a.view(np.complex128)
+        return a
+
+    def save(self, path):
+        L.check(self._lib.bf_plan_save(self._h, str(path).encode()), "bf_plan_save")
+
+    @classmethod
+    def load(cls, path, device=0):
+        o = default_options()
+        o.device = device
+        h = ctypes.c_void_p()
+        L.check(L.lib().bf_plan_load(str(path).encode(), ctypes.byref(o), ctypes.byref(h)), "bf_plan_load")
+        return cls(0, _handle=h)
+
+    # -- apply
+    def apply(self, F, G=None, prec=F32, stream=None):
+        """G = K F on the GPU.  F: torch CUDA tensor (N,) or (N, m), complex64
+        (F32, BF16X3) or complex128 (F64), contiguous.  Returns G."""
+        import torch
+        dt = torch.complex128 if prec == F64 else torch.complex64
+        if F.dtype != dt or not F.is_cuda or not F.is_contiguous():
+            raise ValueError("F must be a contiguous CUDA %s tensor" % dt)
+        m = 1 if F.dim() == 1 else F.shape[1]
+        if G is None:
+            G = torch.empty_like(F)
+        elif G.dtype != dt or not G.is_contiguous() or G.shape != F.shape:
+            raise ValueError("G must match F")
+        L.check(self._lib.bf_apply(self._h, prec, ctypes.c_void_p(F.data_ptr()), m,
+                                   ctypes.c_void_p(G.data_ptr()), _stream_ptr(stream)), "bf_apply")
+        return G
+
+    def apply_host(self, F, G=None, prec=F32, stream=None):
+        """G = K F with HOST buffers (numpy arrays or CPU tensors, pinned preferred):
+        copies in, applies, copies out, synchronises."""
+        if isinstance(F, np.ndarray):
+            dt = np.complex128 if prec == F64 else np.complex64
+            if F.dtype != dt or not F.flags.c_contiguous:
+                raise ValueError("F must be C-contiguous %s" % dt)
+            m = 1 if F.ndim == 1 else F.shape[1]
+            if G is None:
+                G = np.empty_like(F)
+            fp, gp = F.ctypes.data, G.ctypes.data
+        else:
+            m = 1 if F.dim() == 1 else F.shape[1]
+            if G is None:
+                G = F.new_empty(F.shape)
+            fp, gp = F.data_ptr(), G.data_ptr()
+        L.check(self._lib.bf_apply_host(self._h, prec, ctypes.c_void_p(fp), m, ctypes.c_void_p(gp),
+                                        _stream_ptr(stream)), "bf_apply_host")
+        return G
+
+    def sync_status(self, stream=None):
+        return self._lib.bf_sync_status(self._h, _stream_ptr(stream))
+
+
+def version():
+    return L.lib().bf_version().decode()

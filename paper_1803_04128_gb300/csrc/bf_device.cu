@@ -1,0 +1,342 @@
+// Device residency of the factors, workspaces and apply dispatch.
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bf_device.h"
+
+namespace bfi {
+namespace {
+
+#define BF_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            set_error("%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return e_ == cudaErrorMemoryAllocation ? BF_ERR_NOMEM : BF_ERR_CUDA;   \
+        }                                                                          \
+    } while (0)
+
+// Byte-packed host image of an arena; pointers are recorded as offsets.
+struct Packer {
+    std::vector<unsigned char> buf;
+    size_t add(const void* src, size_t n)
+    {
+        size_t off = (buf.size() + 255) & ~(size_t)255;
+        buf.resize(off + n);
+        if (n) std::memcpy(buf.data() + off, src, n);
+        return off;
+    }
+};
+
+template <typename T>
+std::vector<T> real_as(const std::vector<double>& v)
+{
+    std::vector<T> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
+    return o;
+}
+template <typename C>
+std::vector<C> cplx_as(const std::vector<cd>& v)
+{
+    std::vector<C> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        o[i].x = (decltype(o[i].x))v[i].real();
+        o[i].y = (decltype(o[i].y))v[i].imag();
+    }
+    return o;
+}
+template <typename C, typename V>
+std::vector<C> cplx_concat(const std::vector<V>& vs)
+{
+    std::vector<C> o;
+    for (auto& v : vs) {
+        auto c = cplx_as<C>(v);
+        o.insert(o.end(), c.begin(), c.end());
+    }
+    return o;
+}
+template <typename T>
+size_t add_vec(Packer& pk, const std::vector<T>& v) { return pk.add(v.data(), v.size() * sizeof(T)); }
+
+// transposes used by the fused kernels
+std::vector<double> transpose(const std::vector<double>& M, int rows, int cols)
+{
+    std::vector<double> T((size_t)rows * cols);
+    for (int i = 0; i < rows; ++i)
+        for (int j = 0; j < cols; ++j) T[(size_t)j * rows + i] = M[(size_t)i * cols + j];
+    return T;
+}
+
+struct Offs {
+    size_t a, b, Mv, EV, MH, EH, S, MG, FG, MU, EU;
+};
+
+template <typename T, typename C>
+Offs pack_block(Packer& pk, const BlockFactors& B, bool transposed)
+{
+    Offs o;
+    const int r = B.r;
+    o.a = add_vec(pk, cplx_as<C>(B.a));
+    o.b = add_vec(pk, cplx_as<C>(B.b));
+    o.Mv = add_vec(pk, real_as<T>(transposed ? transpose(B.Mv, r, B.nv) : B.Mv));
+    o.EV = add_vec(pk, cplx_as<C>(B.EV));
+    std::vector<double> mh;
+    for (auto& M : B.MH) {
+        auto t = transposed ? transpose(M, r, 2 * r) : M;
+        mh.insert(mh.end(), t.begin(), t.end());
+    }
+    o.MH = add_vec(pk, real_as<T>(mh));
+    o.EH = add_vec(pk, cplx_concat<C>(B.EH));
+    o.S = add_vec(pk, cplx_as<C>(B.S));
+    std::vector<double> mg;
+    for (auto& M : B.MG) {
+        // natural [pos][t][s]; transposed [pos][s][t]
+        for (int pos = 0; pos < 2; ++pos) {
+            std::vector<double> blk(M.begin() + (size_t)pos * r * r, M.begin() + (size_t)(pos + 1) * r * r);
+            auto t = transposed ? transpose(blk, r, r) : blk;
+            mg.insert(mg.end(), t.begin(), t.end());
+        }
+    }
+    o.MG = add_vec(pk, real_as<T>(mg));
+    o.FG = add_vec(pk, cplx_concat<C>(B.FG));
+    o.MU = add_vec(pk, real_as<T>(B.MU));
+    o.EU = add_vec(pk, cplx_as<C>(B.EU));
+    return o;
+}
+
+template <typename T, typename C>
+void bind(DevFactors<T, C>& f, unsigned char* base, const Offs& o)
+{
+    f.a = reinterpret_cast<C*>(base + o.a);
+    f.b = reinterpret_cast<C*>(base + o.b);
+    f.Mv = reinterpret_cast<T*>(base + o.Mv);
+    f.EV = reinterpret_cast<C*>(base + o.EV);
+    f.MH = reinterpret_cast<T*>(base + o.MH);
+    f.EH = reinterpret_cast<C*>(base + o.EH);
+    f.S = reinterpret_cast<C*>(base + o.S);
+    f.MG = reinterpret_cast<T*>(base + o.MG);
+    f.FG = reinterpret_cast<C*>(base + o.FG);
+    f.MU = reinterpret_cast<T*>(base + o.MU);
+    f.EU = reinterpret_cast<C*>(base + o.EU);
+}
+
+Geo geo_of(const BlockFactors& B)
+{
+    Geo g;
+    g.N = B.N;
+    g.P = B.P();
+    g.r = B.r;
+    g.n0 = B.n0;
+    g.L = B.L;
+    g.h = B.h;
+    g.l1 = B.l1;
+    g.nv = B.nv;
+    g.kH = B.nH();
+    g.kG = B.nG();
+    g.ra = B.ra;
+    return g;
+}
+
+bf_status ensure(void** p, size_t* have, size_t need)
+{
+    if (*have >= need && *p) return BF_OK;
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+        *have = 0;
+    }
+    BF_CUDA(cudaMalloc(p, need));
+    *have = need;
+    return BF_OK;
+}
+
+}  // namespace
+
+bf_status device_upload(bf_plan* p)
+{
+    if (p->dev) return BF_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        set_error("bf_upload: no CUDA device available");
+        return BF_ERR_CUDA;
+    }
+    if (p->opt.device < 0 || p->opt.device >= ndev) {
+        set_error("bf_upload: device %d not present (%d devices)", p->opt.device, ndev);
+        return BF_ERR_ARG;
+    }
+    BF_CUDA(cudaSetDevice(p->opt.device));
+    DeviceState* ds = new (std::nothrow) DeviceState();
+    if (!ds) {
+        set_error("bf_upload: out of host memory");
+        return BF_ERR_NOMEM;
+    }
+    ds->device = p->opt.device;
+    Packer pk64, pk32;
+    std::vector<Offs> o64, o32;
+    try {
+        for (auto& B : p->blocks) {
+            o64.push_back(pack_block<double, double2>(pk64, B, false));
+            o32.push_back(pack_block<float, float2>(pk32, B, true));
+        }
+    } catch (const std::bad_alloc&) {
+        delete ds;
+        set_error("bf_upload: out of host memory while packing");
+        return BF_ERR_NOMEM;
+    }
+    auto fail = [&](bf_status st) {
+        if (ds->arena64) cudaFree(ds->arena64);
+        if (ds->arena32) cudaFree(ds->arena32);
+        if (ds->err) cudaFree(ds->err);
+        delete ds;
+        return st;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&ds->arena64, pk64.buf.size())) != cudaSuccess ||
+        (e = cudaMalloc(&ds->arena32, pk32.buf.size())) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ds->err, sizeof(int))) != cudaSuccess) {
+        set_error("bf_upload: cudaMalloc: %s", cudaGetErrorString(e));
+        return fail(e == cudaErrorMemoryAllocation ? BF_ERR_NOMEM : BF_ERR_CUDA);
+    }
+    if ((e = cudaMemcpy(ds->arena64, pk64.buf.data(), pk64.buf.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(ds->arena32, pk32.buf.data(), pk32.buf.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(ds->err, 0, sizeof(int))) != cudaSuccess) {
+        set_error("bf_upload: copy: %s", cudaGetErrorString(e));
+        return fail(BF_ERR_CUDA);
+    }
+    ds->bytes64 = pk64.buf.size();
+    ds->bytes32 = pk32.buf.size();
+    for (size_t i = 0; i < p->blocks.size(); ++i) {
+        DevBlock db;
+        db.g = geo_of(p->blocks[i]);
+        db.row0 = p->blocks[i].row0;
+        db.col0 = p->blocks[i].col0;
+        bind(db.f64, (unsigned char*)ds->arena64, o64[i]);
+        bind(db.f32, (unsigned char*)ds->arena32, o32[i]);
+        ds->blocks.push_back(db);
+    }
+    p->dev = ds;
+    if (!p->opt.keep_host) {
+        for (auto& B : p->blocks) {
+            BlockFactors slim;
+            slim.N = B.N; slim.row0 = B.row0; slim.col0 = B.col0; slim.r = B.r; slim.n0 = B.n0;
+            slim.L = B.L; slim.h = B.h; slim.l1 = B.l1; slim.nv = B.nv; slim.ra = B.ra;
+            slim.amp_sigma_ratio = B.amp_sigma_ratio;
+            B = std::move(slim);
+        }
+    }
+    return BF_OK;
+}
+
+bf_status device_reserve(bf_plan* p, bf_precision prec, int64_t m, void*)
+{
+    DeviceState* ds = p->dev;
+    BF_CUDA(cudaSetDevice(ds->device));
+    size_t need = 0;
+    for (auto& B : ds->blocks) {
+        if (prec == BF_PREC_F64) need = std::max(need, 2 * plain_f64_ws_bytes(B.g, m));
+        else need = std::max(need, fused_f32_ws_bytes(B.g, m));
+    }
+    if (need == 0) need = 256;
+    if (prec == BF_PREC_F64) return ensure(&ds->ws64, &ds->ws64_bytes, need);
+    return ensure(&ds->ws32, &ds->ws32_bytes, need);
+}
+
+bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G, void* stream)
+{
+    DeviceState* ds = p->dev;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == BF_PREC_BF16X3) {
+        set_error("bf_apply: BF_PREC_BF16X3 not available in this build");
+        return BF_ERR_UNSUPPORTED;
+    }
+    if (prec == BF_PREC_F32) {
+        for (auto& B : ds->blocks)
+            if (!fused_f32_supported(B.g.r) || B.g.nv > 2 * B.g.r) {
+                set_error("bf_apply: no fused FP32 kernels for r=%d, nv=%d", B.g.r, B.g.nv);
+                return BF_ERR_UNSUPPORTED;
+            }
+    }
+    bf_status rs = device_reserve(p, prec, m, stream);
+    if (rs != BF_OK) return rs;
+    const int sp = p->opt.split;
+    for (size_t i = 0; i < ds->blocks.size(); ++i) {
+        const DevBlock& B = ds->blocks[i];
+        const int beta = (sp == 2 && (i % 2) == 1) ? 1 : 0;  // second column half accumulates
+        cudaError_t e;
+        if (prec == BF_PREC_F64) {
+            const double2* Fb = (const double2*)F + B.col0 * m;
+            double2* Gb = (double2*)G + B.row0 * m;
+            const size_t half = ds->ws64_bytes / 2 / sizeof(double2);
+            e = launch_plain_f64(B, Fb, m, Gb, beta, (double2*)ds->ws64, (double2*)ds->ws64 + half, st);
+        } else {
+            const float2* Fb = (const float2*)F + B.col0 * m;
+            float2* Gb = (float2*)G + B.row0 * m;
+            e = launch_fused_f32(B, Fb, m, Gb, beta, (float2*)ds->ws32, st);
+        }
+        if (e != cudaSuccess) {
+            set_error("bf_apply: kernel launch failed: %s", cudaGetErrorString(e));
+            return BF_ERR_CUDA;
+        }
+    }
+    return BF_OK;
+}
+
+bf_status device_apply_host(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G, void* stream)
+{
+    DeviceState* ds = p->dev;
+    cudaStream_t st = (cudaStream_t)stream;
+    BF_CUDA(cudaSetDevice(ds->device));
+    const size_t elt = prec == BF_PREC_F64 ? sizeof(double2) : sizeof(float2);
+    const size_t nb = (size_t)p->N * m * elt;
+    bf_status s = ensure(&ds->stage, &ds->stage_bytes, 2 * nb);
+    if (s != BF_OK) return s;
+    unsigned char* dF = (unsigned char*)ds->stage;
+    unsigned char* dG = dF + nb;
+    BF_CUDA(cudaMemcpyAsync(dF, F, nb, cudaMemcpyHostToDevice, st));
+    s = device_apply(p, prec, dF, m, dG, stream);
+    if (s != BF_OK) return s;
+    BF_CUDA(cudaMemcpyAsync(G, dG, nb, cudaMemcpyDeviceToHost, st));
+    BF_CUDA(cudaStreamSynchronize(st));
+    return BF_OK;
+}
+
+bf_status device_sync_status(bf_plan* p, void* stream)
+{
+    DeviceState* ds = p->dev;
+    BF_CUDA(cudaSetDevice(ds->device));
+    BF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int h = 0;
+    BF_CUDA(cudaMemcpy(&h, ds->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) {
+        set_error("device-side wait ran out (code %d)", h);
+        cudaMemset(ds->err, 0, sizeof(int));
+        return BF_ERR_TIMEOUT;
+    }
+    return BF_OK;
+}
+
+void device_free(bf_plan* p)
+{
+    DeviceState* ds = p->dev;
+    if (!ds) return;
+    cudaSetDevice(ds->device);
+    cudaFree(ds->arena64);
+    cudaFree(ds->arena32);
+    cudaFree(ds->ws64);
+    cudaFree(ds->ws32);
+    cudaFree(ds->stage);
+    cudaFree(ds->err);
+    delete ds;
+    p->dev = nullptr;
+}
+
+void device_info(const bf_plan* p, bf_plan_info* info)
+{
+    if (!p->dev) return;
+    info->uploaded = 1;
+    info->dev_bytes_f64 = (int64_t)p->dev->bytes64;
+    info->dev_bytes_f32 = (int64_t)p->dev->bytes32;
+}
+
+}  // namespace bfi

@@ -1,0 +1,83 @@
+// Device-side layouts of the IBF-MAT factors and the launch interfaces.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "bf_internal.h"
+
+namespace bfi {
+
+// Geometry of one sub-BF, as the kernels see it.
+struct Geo {
+    int64_t N;   // block size
+    int64_t P;   // pairs per level = N / n0 = 2^L
+    int r, n0, L, h, l1, nv;  // nv = n0 * 2^l1 (V and U leaf size)
+    int kH, kG;               // number of H and G levels
+    int ra;                   // amplitude rank
+};
+
+// Factor arrays of one sub-BF in one precision; T = float or double, C = float2/double2.
+// Layouts (all row-major):
+//   a, b  [ra][N]          Mv [r][nv]            EV [2^l1][N]
+//   MH    [kH][r][2r]      EH [kH][P][2][r]      S  [P][r][r]
+//   MG    [kG][2][r][r]    FG [kG][P][2][r]      MU [nv][r]      EU [2^l1][N]
+// where a pair index at level l is q = a * 2^(L-l) + b (A = node a of T_X at
+// level l, B = node b of T_Omega at level L-l).
+template <typename T, typename C>
+struct DevFactors {
+    C *a = nullptr, *b = nullptr;
+    T* Mv = nullptr;
+    C* EV = nullptr;
+    T* MH = nullptr;
+    C* EH = nullptr;
+    C* S = nullptr;
+    T* MG = nullptr;
+    C* FG = nullptr;
+    T* MU = nullptr;
+    C* EU = nullptr;
+};
+
+struct DevBlock {
+    Geo g{};
+    int64_t row0 = 0, col0 = 0;
+    DevFactors<double, double2> f64;
+    DevFactors<float, float2> f32;
+};
+
+struct DeviceState {
+    int device = 0;
+    std::vector<DevBlock> blocks;
+    void* arena64 = nullptr;
+    void* arena32 = nullptr;
+    size_t bytes64 = 0, bytes32 = 0;
+    // workspaces
+    void* ws64 = nullptr;
+    size_t ws64_bytes = 0;
+    void* ws32 = nullptr;
+    size_t ws32_bytes = 0;
+    void* stage = nullptr;  // F/G staging for bf_apply_host
+    size_t stage_bytes = 0;
+    int* err = nullptr;     // device error word (0 = ok)
+};
+
+// ---- launchers (return cudaGetLastError() of the last launch) ----
+// Plain FP64 form: one kernel per butterfly stage, state through global memory.
+cudaError_t launch_plain_f64(const DevBlock& B, const double2* F, int64_t m, double2* G, int beta,
+                             double2* ws0, double2* ws1, cudaStream_t st);
+size_t plain_f64_ws_bytes(const Geo& g, int64_t m);  // bytes of ONE of the two state buffers
+
+// Fused FP32 form: front pass (V + H levels + switch) and back pass (G levels + U).
+struct FusedCfg {
+    int mr;       // right-hand sides per column slice
+    int nslice;   // ceil(m / mr)
+};
+FusedCfg fused_f32_config(const Geo& g, int64_t m);
+size_t fused_f32_ws_bytes(const Geo& g, int64_t m);
+cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta,
+                             float2* ws, cudaStream_t st);
+bool fused_f32_supported(int r);
+
+}  // namespace bfi

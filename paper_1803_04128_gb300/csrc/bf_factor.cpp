@@ -1,0 +1,383 @@
+// Host FP64 construction of the IBF-MAT factors (off the timed path).
+//
+//  * amplitude split alpha ~ sum_k a_k(x) b_k(xi) by Algorithm 1 (Sec. 2.1);
+//  * the butterfly factors of Eq. (BFM), Sec. 4, from the interpolative
+//    low-rank factors of Algorithm 2 arranged by Algorithm 4.1, stored in a
+//    factored form: each level's transfer is
+//        (diagonal of phases) x (real Lagrange matrix, shared by all pairs of
+//        the level) x (diagonal of phases),
+//    which is the same sparse factor the paper stores, with its O(r^2) dense
+//    blocks written as products of their diagonal and real parts.
+//
+// Let mu^{AB}_t = e^{2 pi i Phi(c_A, xi^B_t)} lambda^{AB}_t on the xi side and
+// nu^{AB}_t = e^{-2 pi i Phi(x^A_t, c_B)} lambda^{AB}_t on the x side.  Then
+//   V (Eq. 1, level l1):   mu^{AB}   = Mv (e^{2 pi i Phi(c_A, .)} y|_B)
+//   H (Eq. 2, l1 < l <= h): mu^{AB}  = MH_l [EH_{A,C1} mu^{PC1}; EH_{A,C2} mu^{PC2}],
+//                           EH_{A,C,s} = e^{2 pi i (Phi(c_A, xi^C_s) - Phi(c_P, xi^C_s))}
+//   switch (step 4, l = h): nu^{AB}_t = sum_s S_{ts} mu^{AB}_s,
+//                           S_{ts} = e^{2 pi i (Phi(x^A_t, xi^B_s) - Phi(x^A_t, c_B) - Phi(c_A, xi^B_s))}
+//   G (Eq. 3, h < l <= L-l1): nu^{AB} = sum_{C > B} FG_{A,C} (MG_{pos(A)} nu^{PC}),
+//                           FG_{A,C,t} = e^{2 pi i (Phi(x^A_t, c_C) - Phi(x^A_t, c_B))}
+//   U (Eq. bf3, l = L-l1):  u(x) = sum_{C} e^{2 pi i Phi(x, c_C)} (MU nu^{AC})(x)
+// Levels whose nodes have <= r indices use every index as grid point; there
+// Algorithm 4.1 only copies (xi side) or sums (x side) coefficients, and those
+// levels are folded into V (first l1 levels) and U (last l1 levels).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "bf_internal.h"
+
+namespace bfi {
+
+static const double kTwoPi = 6.283185307179586476925286766559;
+
+static int64_t mod_pos(int64_t a, int64_t n)
+{
+    int64_t r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+double KernelFn::phase_frac(int64_t i, int64_t j) const
+{
+    const int64_t Ng = n_global;
+    const int64_t xi = j - Ng / 2;
+    const double x = (double)i / (double)Ng;
+    const double axi = (double)(xi < 0 ? -xi : xi);
+    const double s = d.phase_param;
+    double t1 = 0.0, t2 = 0.0;
+    switch (d.phase_kind) {
+    case BF_PHASE_DFT:
+        t1 = (double)mod_pos(i * xi, Ng) / (double)Ng;
+        break;
+    case BF_PHASE_FIO:
+        t1 = (double)mod_pos(i * xi, Ng) / (double)Ng;
+        t2 = (2.0 + s * std::sin(kTwoPi * x)) / 16.0 * axi;
+        break;
+    case BF_PHASE_FIO_PW: {
+        t1 = (double)mod_pos(i * xi, Ng) / (double)Ng;
+        const double c = (2.0 + s * std::sin(kTwoPi * x)) / 16.0;
+        t2 = (2 * i < Ng) ? c * axi : -0.5 * c * axi;
+        break;
+    }
+    case BF_PHASE_ONES:
+        break;
+    case BF_PHASE_SEP:
+        t2 = 0.3 * std::sin(kTwoPi * x) + (double)mod_pos(xi * xi, 4 * Ng) / (double)(4 * Ng);
+        break;
+    default: {
+        double v = d.phi(x, (double)xi, d.user);
+        t2 = v - std::floor(v);
+        break;
+    }
+    }
+    t2 -= std::nearbyint(t2);
+    return t1 + t2;
+}
+
+cd KernelFn::amplitude(int64_t i, int64_t j) const
+{
+    const int64_t Ng = n_global;
+    const double x = (double)i / (double)Ng;
+    const double xi = (double)(j - Ng / 2);
+    switch (d.amp_kind) {
+    case BF_AMP_ONE:
+        return 1.0;
+    case BF_AMP_SMOOTH:
+        return 1.0 + 0.25 * std::sin(kTwoPi * x) * std::cos(kTwoPi * xi / (double)Ng);
+    default: {
+        double re = 0, im = 0;
+        d.alpha(x, xi, d.user, &re, &im);
+        return cd(re, im);
+    }
+    }
+}
+
+static inline cd expi(double frac) { return cd(std::cos(kTwoPi * frac), std::sin(kTwoPi * frac)); }
+
+// ---------------------------------------------------------------------------
+std::vector<int64_t> grid_rel(int64_t n, int r)
+{
+    std::vector<int64_t> g;
+    if (n <= r) {
+        for (int64_t i = 0; i < n; ++i) g.push_back(i);
+        return g;
+    }
+    // Eq. (gdA)/(gdB) read as Round(t + (n - r)(1/2 - z_t)), z_t = cos((t-1) pi/(r-1))/2,
+    // Round = nearest with ties (within 1e-9) to the lower index.
+    for (int t = 1; t <= r; ++t) {
+        double z = 0.5 * std::cos((double)(t - 1) * M_PI / (double)(r - 1));
+        double v = (double)t + (double)(n - r) * (0.5 - z);
+        g.push_back((int64_t)std::ceil(v - 0.5 - 1e-9) - 1);
+    }
+    return g;
+}
+
+std::vector<double> lagrange(const std::vector<int64_t>& nodes, const std::vector<double>& pts)
+{
+    const size_t r = nodes.size(), n = pts.size();
+    std::vector<double> M(r * n, 1.0);
+    for (size_t t = 0; t < r; ++t)
+        for (size_t k = 0; k < n; ++k) {
+            double v = 1.0;
+            for (size_t j = 0; j < r; ++j)
+                if (j != t) v *= (pts[k] - (double)nodes[j]) / (double)(nodes[t] - nodes[j]);
+            M[t * n + k] = v;
+        }
+    return M;
+}
+
+int choose_l1(int r, int n0)
+{
+    int l = 0;
+    while ((int64_t)n0 << l <= r) ++l;
+    return l;
+}
+
+size_t BlockFactors::host_bytes() const
+{
+    size_t s = (a.size() + b.size() + EV.size() + S.size() + EU.size()) * sizeof(cd) +
+               (Mv.size() + MU.size()) * sizeof(double);
+    for (auto& v : MH) s += v.size() * sizeof(double);
+    for (auto& v : MG) s += v.size() * sizeof(double);
+    for (auto& v : EH) s += v.size() * sizeof(cd);
+    for (auto& v : FG) s += v.size() * sizeof(cd);
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 on the amplitude window [row0, row0+N) x [col0, col0+N).
+namespace {
+struct SplitMix {
+    uint64_t s;
+    uint64_t next()
+    {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+};
+
+std::vector<int64_t> sample_union(SplitMix& rng, int64_t n, int64_t k, const std::vector<int64_t>& base)
+{
+    std::vector<int64_t> out(base);
+    k = std::min(k, n);
+    // Floyd's algorithm for k distinct indices
+    std::vector<int64_t> pick;
+    for (int64_t j = n - k; j < n; ++j) {
+        int64_t t = (int64_t)(rng.next() % (uint64_t)(j + 1));
+        if (std::find(pick.begin(), pick.end(), t) != pick.end()) t = j;
+        pick.push_back(t);
+    }
+    out.insert(out.end(), pick.begin(), pick.end());
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+    return out;
+}
+}  // namespace
+
+bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0, int64_t col0,
+                          int64_t N, std::vector<cd>& a, std::vector<cd>& b, int& ra,
+                          double& sigma_ratio)
+{
+    const int r = std::max(1, opt.amp_rank);
+    const int64_t rq = (int64_t)r * std::max(1, opt.amp_oversample);
+    SplitMix rng{opt.seed * 0x9E3779B97F4A7C15ull + 12345};
+    auto entries = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J) {
+        CMat M((int64_t)I.size(), (int64_t)J.size());
+#pragma omp parallel for schedule(static)
+        for (int64_t jj = 0; jj < (int64_t)J.size(); ++jj)
+            for (size_t ii = 0; ii < I.size(); ++ii)
+                M((int64_t)ii, jj) = k.amplitude(row0 + I[ii], col0 + J[(size_t)jj]);
+        return M;
+    };
+    std::vector<int64_t> all((size_t)N);
+    for (int64_t i = 0; i < N; ++i) all[(size_t)i] = i;
+    std::vector<int64_t> pi_col, pi_row, piv;
+    CMat Q;
+    const double qr_tol = 1e-15;
+    for (int sweep = 0; sweep < 2; ++sweep) {
+        // rq random rows + important rows; pivoted QR of K(I, :) picks columns
+        auto I = sample_union(rng, N, rq, pi_row);
+        int kr = pivoted_qr(entries(I, all), r, qr_tol, Q, piv);
+        pi_col.assign(piv.begin(), piv.begin() + std::max(kr, 1));
+        std::sort(pi_col.begin(), pi_col.end());
+        // rq random columns + important columns; pivoted LQ of K(:, J) picks rows
+        auto J = sample_union(rng, N, rq, pi_col);
+        kr = pivoted_qr(adjoint(entries(all, J)), r, qr_tol, Q, piv);
+        pi_row.assign(piv.begin(), piv.begin() + std::max(kr, 1));
+        std::sort(pi_row.begin(), pi_row.end());
+    }
+    CMat Qc, Qr;
+    int kc = pivoted_qr(entries(all, pi_col), r, qr_tol, Qc, piv);
+    int kr = pivoted_qr(adjoint(entries(pi_row, all)), r, qr_tol, Qr, piv);
+    if (kc == 0 || kr == 0) {  // zero amplitude
+        ra = 0;
+        a.clear();
+        b.clear();
+        sigma_ratio = 0;
+        return BF_OK;
+    }
+    auto J = sample_union(rng, N, rq, pi_col);
+    auto I = sample_union(rng, N, rq, pi_row);
+    CMat QcI((int64_t)I.size(), kc), QrJ(kr, (int64_t)J.size());
+    for (size_t ii = 0; ii < I.size(); ++ii)
+        for (int64_t c = 0; c < kc; ++c) QcI((int64_t)ii, c) = Qc(I[ii], c);
+    for (size_t jj = 0; jj < J.size(); ++jj)
+        for (int64_t c = 0; c < kr; ++c) QrJ(c, (int64_t)jj) = std::conj(Qr(J[jj], c));
+    CMat M = matmul(matmul(pinv(QcI, 1e-14), entries(I, J)), pinv(QrJ, 1e-14));
+    CMat UM, VM;
+    std::vector<double> SM;
+    jacobi_svd(M, UM, SM, VM);
+    int keep = 0;
+    const double tol = opt.amp_tol > 0 ? opt.amp_tol : 1e-13;
+    while (keep < (int)SM.size() && SM[(size_t)keep] > tol * SM[0]) ++keep;
+    sigma_ratio = keep < (int)SM.size() ? SM[(size_t)keep] / SM[0] : 0.0;
+    ra = keep;
+    CMat U0 = matmul(Qc, UM), V0 = matmul(Qr, VM);
+    a.assign((size_t)(ra * N), cd(0));
+    b.assign((size_t)(ra * N), cd(0));
+    for (int kk = 0; kk < ra; ++kk)
+        for (int64_t i = 0; i < N; ++i) {
+            a[(size_t)(kk * N + i)] = U0(i, kk) * SM[(size_t)kk];
+            b[(size_t)(kk * N + i)] = std::conj(V0(i, kk));
+        }
+    return BF_OK;
+}
+
+// ---------------------------------------------------------------------------
+bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B)
+{
+    const int64_t N = B.N;
+    const int r = B.r, n0 = B.n0;
+    B.L = 0;
+    while (((int64_t)n0 << B.L) < N) ++B.L;
+    B.h = B.L / 2;
+    B.l1 = choose_l1(r, n0);
+    B.nv = n0 << B.l1;
+    const int L = B.L, h = B.h, l1 = B.l1;
+    if (h < l1) {
+        set_error("N=%lld too small for r=%d, n0=%d (need floor(L/2) >= %d)", (long long)N, r, n0, l1);
+        return BF_ERR_ARG;
+    }
+    const int64_t P = N / n0;
+    auto F = [&](int64_t i, int64_t j) { return k.phase_frac(B.row0 + i, B.col0 + j); };
+
+    bf_status st = amplitude_split(k, opt, B.row0, B.col0, N, B.a, B.b, B.ra, B.amp_sigma_ratio);
+    if (st != BF_OK) return st;
+
+    // V at level l1 (Eq. 1 with the copy levels 1..l1-1 folded in)
+    {
+        const int64_t nv = B.nv, nA = (int64_t)1 << l1, na = N >> l1;
+        auto gB = grid_rel(nv, r);
+        std::vector<double> pts((size_t)nv);
+        for (int64_t x = 0; x < nv; ++x) pts[(size_t)x] = (double)x;
+        B.Mv = lagrange(gB, pts);
+        B.EV.assign((size_t)(nA * N), cd(0));
+#pragma omp parallel for schedule(static)
+        for (int64_t a = 0; a < nA; ++a) {
+            const int64_t cA = centre(a * na, na);
+            for (int64_t j = 0; j < N; ++j) B.EV[(size_t)(a * N + j)] = expi(F(cA, j));
+        }
+    }
+    // H levels (Eq. 2)
+    B.MH.clear();
+    B.EH.clear();
+    for (int l = l1 + 1; l <= h; ++l) {
+        const int64_t nA = (int64_t)1 << l, na = N >> l;
+        const int64_t nBl = (int64_t)1 << (L - l), nb = N >> (L - l);
+        auto gB = grid_rel(nb, r), gC = grid_rel(nb / 2, r);
+        std::vector<double> pts;
+        for (int c = 0; c < 2; ++c)
+            for (int s = 0; s < r; ++s) pts.push_back((double)(gC[(size_t)s] + c * (nb / 2)));
+        B.MH.push_back(lagrange(gB, pts));
+        std::vector<cd> E((size_t)(P * 2 * r));
+#pragma omp parallel for schedule(static)
+        for (int64_t a = 0; a < nA; ++a) {
+            const int64_t cA = centre(a * na, na), cP = centre((a >> 1) * 2 * na, 2 * na);
+            for (int64_t bb = 0; bb < nBl; ++bb)
+                for (int c = 0; c < 2; ++c)
+                    for (int s = 0; s < r; ++s) {
+                        const int64_t xi = bb * nb + c * (nb / 2) + gC[(size_t)s];
+                        E[(size_t)((((a * nBl + bb) * 2 + c) * r) + s)] = expi(F(cA, xi) - F(cP, xi));
+                    }
+        }
+        B.EH.push_back(std::move(E));
+    }
+    // switch at h
+    {
+        const int64_t nA = (int64_t)1 << h, na = N >> h;
+        const int64_t nBl = (int64_t)1 << (L - h), nb = N >> (L - h);
+        auto gA = grid_rel(na, r), gB = grid_rel(nb, r);
+        B.S.assign((size_t)(P * r * r), cd(0));
+#pragma omp parallel for schedule(static)
+        for (int64_t a = 0; a < nA; ++a) {
+            const int64_t cA = centre(a * na, na);
+            for (int64_t bb = 0; bb < nBl; ++bb) {
+                const int64_t cB = centre(bb * nb, nb);
+                for (int t = 0; t < r; ++t) {
+                    const int64_t x = a * na + gA[(size_t)t];
+                    const double fxc = F(x, cB);
+                    for (int s = 0; s < r; ++s) {
+                        const int64_t xi = bb * nb + gB[(size_t)s];
+                        B.S[(size_t)((((a * nBl + bb) * r) + t) * r + s)] = expi(F(x, xi) - fxc - F(cA, xi));
+                    }
+                }
+            }
+        }
+    }
+    // G levels (Eq. 3)
+    B.MG.clear();
+    B.FG.clear();
+    for (int l = h + 1; l <= L - l1; ++l) {
+        const int64_t nA = (int64_t)1 << l, na = N >> l;
+        const int64_t nBl = (int64_t)1 << (L - l), nb = N >> (L - l);
+        auto gA = grid_rel(na, r), gP = grid_rel(2 * na, r);
+        std::vector<double> MG((size_t)(2 * r * r));
+        for (int pos = 0; pos < 2; ++pos) {
+            std::vector<double> pts;
+            for (int t = 0; t < r; ++t) pts.push_back((double)(gA[(size_t)t] + pos * na));
+            auto Lg = lagrange(gP, pts);  // [s][t]
+            for (int t = 0; t < r; ++t)
+                for (int s = 0; s < r; ++s) MG[(size_t)((pos * r + t) * r + s)] = Lg[(size_t)(s * r + t)];
+        }
+        B.MG.push_back(std::move(MG));
+        std::vector<cd> E((size_t)(P * 2 * r));
+#pragma omp parallel for schedule(static)
+        for (int64_t a = 0; a < nA; ++a)
+            for (int64_t bb = 0; bb < nBl; ++bb) {
+                const int64_t cB = centre(bb * nb, nb);
+                for (int c = 0; c < 2; ++c) {
+                    const int64_t cC = centre(bb * nb + c * (nb / 2), nb / 2);
+                    for (int t = 0; t < r; ++t) {
+                        const int64_t x = a * na + gA[(size_t)t];
+                        E[(size_t)((((a * nBl + bb) * 2 + c) * r) + t)] = expi(F(x, cC) - F(x, cB));
+                    }
+                }
+            }
+        B.FG.push_back(std::move(E));
+    }
+    // U at level L-l1 (Eq. bf3 with the summing levels L-l1+1..L folded in)
+    {
+        const int64_t nu = B.nv, nC = (int64_t)1 << l1, nc = N >> l1;
+        auto gA = grid_rel(nu, r);
+        std::vector<double> pts((size_t)nu);
+        for (int64_t x = 0; x < nu; ++x) pts[(size_t)x] = (double)x;
+        auto Lg = lagrange(gA, pts);  // [s][x]
+        B.MU.assign((size_t)(nu * r), 0.0);
+        for (int64_t x = 0; x < nu; ++x)
+            for (int s = 0; s < r; ++s) B.MU[(size_t)(x * r + s)] = Lg[(size_t)(s * nu + x)];
+        B.EU.assign((size_t)(nC * N), cd(0));
+#pragma omp parallel for schedule(static)
+        for (int64_t c = 0; c < nC; ++c) {
+            const int64_t cC = centre(c * nc, nc);
+            for (int64_t x = 0; x < N; ++x) B.EU[(size_t)(c * N + x)] = expi(F(x, cC));
+        }
+    }
+    return BF_OK;
+}
+
+}  // namespace bfi

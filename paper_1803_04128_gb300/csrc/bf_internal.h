@@ -1,0 +1,113 @@
+// Internal types of the butterfly-factorisation library (host side).
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bf.h"
+
+namespace bfi {
+
+using cd = std::complex<double>;
+
+void set_error(const char* fmt, ...);
+
+// ---------------------------------------------------------------------------
+// The operator: entries of alpha and of e^{2 pi i Phi} at global grid indices.
+struct KernelFn {
+    bf_kernel_desc d{};
+    int64_t n_global = 0;  // grid size of x_i = i/n_global, xi_j = j - n_global/2
+    // Phi(x_i, xi_j) reduced mod 1 (exactly for the built-in kinds).
+    double phase_frac(int64_t i, int64_t j) const;
+    cd amplitude(int64_t i, int64_t j) const;
+};
+
+// ---------------------------------------------------------------------------
+// Factors of one N x N sub-BF, FP64, in the layouts documented in bf.h
+// (bf_plan_view).  Levels: V at l1, H at l1+1..h, switch M^h at h, G at
+// h+1..L-l1, U at L-l1 (levels with nodes of <= r indices are exact copies in
+// Algorithm 4.1 and are merged into V and U).
+struct BlockFactors {
+    int64_t N = 0, row0 = 0, col0 = 0;
+    int r = 0, n0 = 1, L = 0, h = 0, l1 = 0, nv = 0;
+    int ra = 0;
+    std::vector<cd> a, b;                 // [ra][N]
+    std::vector<double> Mv;               // [r][nv]
+    std::vector<cd> EV;                   // [2^l1][N]
+    std::vector<std::vector<double>> MH;  // per H level: [r][2r]
+    std::vector<std::vector<cd>> EH;      // per H level: [P][2][r]
+    std::vector<cd> S;                    // [P][r][r]
+    std::vector<std::vector<double>> MG;  // per G level: [2][r][r]
+    std::vector<std::vector<cd>> FG;      // per G level: [P][2][r]
+    std::vector<double> MU;               // [nu][r]
+    std::vector<cd> EU;                   // [2^l1][N]
+    double amp_sigma_ratio = 0.0;
+    int64_t P() const { return N / n0; }
+    int nH() const { return h - l1; }
+    int nG() const { return L - l1 - h; }
+    size_t host_bytes() const;
+};
+
+struct DeviceState;  // defined in the CUDA translation units
+
+}  // namespace bfi
+
+struct bf_plan {
+    bfi::KernelFn kern;
+    bf_options opt{};
+    double eps = 0;
+    int64_t N = 0;
+    int r = 0, n0 = 1, L = 0, h = 0, l1 = 0;
+    bool factored = false;
+    bool user_kinds_lost = false;  // loaded from file with user callbacks
+    std::vector<bfi::BlockFactors> blocks;  // 1 or 4
+    bfi::DeviceState* dev = nullptr;
+};
+
+namespace bfi {
+
+// grids / interpolation (Sec. 2.1)
+std::vector<int64_t> grid_rel(int64_t n, int r);
+std::vector<double> lagrange(const std::vector<int64_t>& nodes, const std::vector<double>& pts);
+inline int64_t centre(int64_t start, int64_t n) { return start + (n - 1) / 2; }
+int choose_l1(int r, int n0);
+
+// construction
+bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B);
+bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0, int64_t col0,
+                          int64_t N, std::vector<cd>& a, std::vector<cd>& b, int& ra,
+                          double& sigma_ratio);
+
+// small dense complex linear algebra (column-major)
+struct CMat {
+    int64_t m = 0, n = 0;
+    std::vector<cd> v;
+    CMat() = default;
+    CMat(int64_t m_, int64_t n_) : m(m_), n(n_), v((size_t)(m_ * n_)) {}
+    cd& operator()(int64_t i, int64_t j) { return v[(size_t)(i + j * m)]; }
+    const cd& operator()(int64_t i, int64_t j) const { return v[(size_t)(i + j * m)]; }
+};
+// Householder QR with column pivoting, stopped after kmax steps or when the
+// largest remaining column norm falls below tol * (first pivot norm).
+// Returns the rank k; Q is m x k (orthonormal columns), piv the full pivot order.
+int pivoted_qr(const CMat& A, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv);
+// One-sided Jacobi SVD of a small matrix: A = U diag(S) V^*.
+void jacobi_svd(const CMat& A, CMat& U, std::vector<double>& S, CMat& V);
+CMat pinv(const CMat& A, double rcond);
+CMat matmul(const CMat& A, const CMat& B);
+CMat adjoint(const CMat& A);
+
+// device side (bf_device.cu)
+bf_status device_upload(bf_plan* p);
+bf_status device_reserve(bf_plan* p, bf_precision prec, int64_t m, void* stream);
+bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G,
+                       void* stream);
+bf_status device_apply_host(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G,
+                            void* stream);
+bf_status device_sync_status(bf_plan* p, void* stream);
+void device_free(bf_plan* p);
+void device_info(const bf_plan* p, bf_plan_info* info);
+
+}  // namespace bfi

@@ -1,0 +1,181 @@
+// Small dense complex linear algebra for the host construction (FP64):
+// Householder QR with column pivoting (early stop at numerical rank),
+// one-sided Jacobi SVD, pseudo-inverse.  Used by Algorithm 1 (Sec. 2.1).
+#include <algorithm>
+#include <cmath>
+
+#include "bf_internal.h"
+
+namespace bfi {
+
+CMat matmul(const CMat& A, const CMat& B)
+{
+    CMat C(A.m, B.n);
+    for (int64_t j = 0; j < B.n; ++j)
+        for (int64_t k = 0; k < A.n; ++k) {
+            cd bkj = B(k, j);
+            if (bkj == cd(0)) continue;
+            for (int64_t i = 0; i < A.m; ++i) C(i, j) += A(i, k) * bkj;
+        }
+    return C;
+}
+
+CMat adjoint(const CMat& A)
+{
+    CMat T(A.n, A.m);
+    for (int64_t j = 0; j < A.n; ++j)
+        for (int64_t i = 0; i < A.m; ++i) T(j, i) = std::conj(A(i, j));
+    return T;
+}
+
+int pivoted_qr(const CMat& A, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv)
+{
+    const int64_t m = A.m, n = A.n;
+    CMat R = A;
+    piv.resize((size_t)n);
+    std::vector<double> nrm((size_t)n);
+    for (int64_t j = 0; j < n; ++j) {
+        piv[(size_t)j] = j;
+        double s = 0;
+        for (int64_t i = 0; i < m; ++i) s += std::norm(R(i, j));
+        nrm[(size_t)j] = s;
+    }
+    const int64_t kcap = std::min<int64_t>({(int64_t)kmax, m, n});
+    std::vector<std::vector<cd>> vs;
+    double ref = -1;
+    int64_t k = 0;
+    for (; k < kcap; ++k) {
+        int64_t p = k;
+        for (int64_t j = k + 1; j < n; ++j)
+            if (nrm[(size_t)j] > nrm[(size_t)p]) p = j;
+        // recompute the winner's norm exactly (downdating loses accuracy)
+        double s = 0;
+        for (int64_t i = k; i < m; ++i) s += std::norm(R(i, p));
+        double pn = std::sqrt(s);
+        if (ref < 0) ref = pn;
+        if (pn <= tol * ref || pn == 0.0) break;
+        if (p != k) {
+            for (int64_t i = 0; i < m; ++i) std::swap(R(i, k), R(i, p));
+            std::swap(nrm[(size_t)k], nrm[(size_t)p]);
+            std::swap(piv[(size_t)k], piv[(size_t)p]);
+        }
+        // Householder vector for R[k:, k]
+        std::vector<cd> v((size_t)(m - k));
+        for (int64_t i = k; i < m; ++i) v[(size_t)(i - k)] = R(i, k);
+        cd x0 = v[0];
+        double ax0 = std::abs(x0);
+        cd ph = ax0 > 0 ? x0 / ax0 : cd(1);
+        cd alpha = -ph * pn;
+        v[0] -= alpha;
+        double vn = 0;
+        for (auto& e : v) vn += std::norm(e);
+        vn = std::sqrt(vn);
+        if (vn > 0)
+            for (auto& e : v) e /= vn;
+        // apply H = I - 2 v v^* to R[k:, k:]
+        for (int64_t j = k; j < n; ++j) {
+            cd dot = 0;
+            for (int64_t i = k; i < m; ++i) dot += std::conj(v[(size_t)(i - k)]) * R(i, j);
+            dot *= 2.0;
+            for (int64_t i = k; i < m; ++i) R(i, j) -= v[(size_t)(i - k)] * dot;
+        }
+        for (int64_t j = k + 1; j < n; ++j) {
+            nrm[(size_t)j] -= std::norm(R(k, j));
+            if (nrm[(size_t)j] < 0) nrm[(size_t)j] = 0;
+        }
+        vs.push_back(std::move(v));
+    }
+    // Q = H_0 ... H_{k-1} [I_k; 0]
+    Q = CMat(m, k);
+    for (int64_t j = 0; j < k; ++j) Q(j, j) = 1;
+    for (int64_t s2 = k - 1; s2 >= 0; --s2) {
+        const auto& v = vs[(size_t)s2];
+        for (int64_t j = 0; j < k; ++j) {
+            cd dot = 0;
+            for (int64_t i = s2; i < m; ++i) dot += std::conj(v[(size_t)(i - s2)]) * Q(i, j);
+            dot *= 2.0;
+            for (int64_t i = s2; i < m; ++i) Q(i, j) -= v[(size_t)(i - s2)] * dot;
+        }
+    }
+    return (int)k;
+}
+
+void jacobi_svd(const CMat& A0, CMat& U, std::vector<double>& S, CMat& V)
+{
+    CMat A = A0;
+    const int64_t m = A.m, n = A.n;
+    V = CMat(n, n);
+    for (int64_t j = 0; j < n; ++j) V(j, j) = 1;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0;
+        for (int64_t p = 0; p < n; ++p)
+            for (int64_t q = p + 1; q < n; ++q) {
+                double al = 0, be = 0;
+                cd ga = 0;
+                for (int64_t i = 0; i < m; ++i) {
+                    al += std::norm(A(i, p));
+                    be += std::norm(A(i, q));
+                    ga += std::conj(A(i, p)) * A(i, q);
+                }
+                double ag = std::abs(ga);
+                if (ag == 0.0 || ag <= 1e-15 * std::sqrt(al * be)) continue;
+                off = std::max(off, ag / std::sqrt(al * be));
+                cd e = ga / ag;  // rotate column q by conj(e) so that the Gram entry is real
+                double zeta = (be - al) / (2 * ag);
+                double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1 + zeta * zeta));
+                double c = 1 / std::sqrt(1 + t * t), s = c * t;
+                for (int64_t i = 0; i < m; ++i) {
+                    cd ap = A(i, p), aq = A(i, q) * std::conj(e);
+                    A(i, p) = c * ap - s * aq;
+                    A(i, q) = s * ap + c * aq;
+                }
+                for (int64_t i = 0; i < n; ++i) {
+                    cd vp = V(i, p), vq = V(i, q) * std::conj(e);
+                    V(i, p) = c * vp - s * vq;
+                    V(i, q) = s * vp + c * vq;
+                }
+            }
+        if (off < 1e-15) break;
+    }
+    std::vector<double> s0((size_t)n);
+    for (int64_t j = 0; j < n; ++j) {
+        double t = 0;
+        for (int64_t i = 0; i < m; ++i) t += std::norm(A(i, j));
+        s0[(size_t)j] = std::sqrt(t);
+    }
+    std::vector<int64_t> ord((size_t)n);
+    for (int64_t j = 0; j < n; ++j) ord[(size_t)j] = j;
+    std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return s0[(size_t)x] > s0[(size_t)y]; });
+    U = CMat(m, n);
+    CMat V2(n, n);
+    S.assign((size_t)n, 0.0);
+    for (int64_t jj = 0; jj < n; ++jj) {
+        int64_t j = ord[(size_t)jj];
+        S[(size_t)jj] = s0[(size_t)j];
+        for (int64_t i = 0; i < m; ++i) U(i, jj) = s0[(size_t)j] > 0 ? A(i, j) / s0[(size_t)j] : cd(0);
+        for (int64_t i = 0; i < n; ++i) V2(i, jj) = V(i, j);
+    }
+    V = V2;
+}
+
+CMat pinv(const CMat& A, double rcond)
+{
+    // A = U S V^*  ->  A^+ = V S^+ U^*; work on the thinner orientation
+    if (A.m < A.n) return adjoint(pinv(adjoint(A), rcond));
+    CMat U, V;
+    std::vector<double> S;
+    jacobi_svd(A, U, S, V);
+    CMat P(A.n, A.m);
+    double smax = S.empty() ? 0 : S[0];
+    for (size_t k = 0; k < S.size(); ++k) {
+        if (S[k] <= rcond * smax || S[k] == 0.0) continue;
+        double inv = 1.0 / S[k];
+        for (int64_t j = 0; j < A.m; ++j) {
+            cd u = std::conj(U(j, (int64_t)k)) * inv;
+            for (int64_t i = 0; i < A.n; ++i) P(i, j) += V(i, (int64_t)k) * u;
+        }
+    }
+    return P;
+}
+
+}  // namespace bfi

@@ -1,0 +1,127 @@
+"""CPU tests of the product's host construction (bf_factor) and ABI surface."""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from conftest import relerr
+import factored_ref
+from oracle import butterfly as obf
+from oracle import direct as od
+from oracle import lowrank as olr
+from paper_1803_04128_gb300 import _lib as L
+from paper_1803_04128_gb300 import api, inputs
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1803_04128_gb300 import build
+    build.build()
+
+
+def test_library_exports_every_declared_symbol():
+    import ctypes
+    lib = ctypes.CDLL(L.LIB_PATH)
+    names = L.declared_symbols()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("n,r", [(3, 10), (16, 10), (17, 9), (256, 10), (1000, 12), (65536, 16)])
+def test_grid_matches_oracle_reading(n, r):
+    assert np.array_equal(api.grid_indices(n, r), obf.grid(n, r))
+
+
+def oracle_ibf(kind, N, F, r, amp, s=1.0):
+    ent = lambda I, J: od.amplitude(amp, N, np.asarray(I)[:, None], np.asarray(J)[None, :])
+    a, b = olr.amplitude_split(ent, N, N)
+    return obf.ibf_apply(kind, N, F, r, a, b, s=s)
+
+
+@pytest.mark.parametrize("kind,amp,N,r", [(L.PHASE_FIO, 0, 1024, 10), (L.PHASE_FIO, 1, 1024, 10),
+                                          (L.PHASE_FIO, 1, 256, 8), (L.PHASE_FIO_PW, 1, 2048, 10),
+                                          (L.PHASE_DFT, 0, 512, 6), (L.PHASE_FIO, 1, 4096, 12),
+                                          (L.PHASE_FIO, 1, 2048, 16)])
+def test_factors_reproduce_algorithm_4_1(kind, amp, N, r):
+    # The factored, level-merged form built by bf_factor equals Algorithm 4.1
+    # evaluated on the fly (oracle) up to FP64 rounding.
+    p = api.Plan(N, r=r, phase_kind=kind, amp_kind=amp)
+    F = inputs.complex_gaussian(N, 3, seed=1)
+    g_prod = factored_ref.apply(p, F)
+    g_orc = oracle_ibf(kind, N, F, r, amp)
+    assert relerr(g_prod, g_orc) < 1e-11
+    # and the BF approximates K f to the accuracy the rank buys
+    gd = od.direct(kind, N, F, amp=amp)
+    assert relerr(g_prod, gd) < {6: 1e-2, 8: 1e-4, 10: 1e-6, 12: 1e-8, 16: 1e-11}[r]
+
+
+def test_split_plan_sums_four_sub_butterflies():
+    N = 2048
+    p = api.Plan(N, r=10, phase_kind=L.PHASE_FIO_PW, amp_kind=L.AMP_SMOOTH, split=2)
+    F = inputs.complex_gaussian(N, 2, seed=2)
+    g = factored_ref.apply(p, F)
+    gd = od.direct(od.FIOPW, N, F, amp=1)
+    assert relerr(g, gd) < 1e-6
+    assert p.info()["split"] == 2
+
+
+def test_exact_kernels_are_reproduced():
+    for kind in (L.PHASE_ONES, L.PHASE_SEP):
+        N = 1024
+        p = api.Plan(N, r=6, phase_kind=kind)
+        F = inputs.complex_gaussian(N, 2, seed=3)
+        assert relerr(factored_ref.apply(p, F), od.direct(kind, N, F)) < 1e-12
+
+
+def test_amplitude_rank_two():
+    p = api.Plan(4096, eps=1e-6, amp_kind=L.AMP_SMOOTH)
+    info = p.info()
+    assert info["r_alpha"] == 2 and info["r"] == 10
+    a = p.view(0).reshape(2, -1); b = p.view(1).reshape(2, -1)
+    S = np.arange(0, 4096, 13)
+    A = od.amplitude(1, 4096, S[:, None], S[None, :])
+    assert np.linalg.norm(A - a[:, S].T @ b[:, S], 2) / np.linalg.norm(A, 2) < 1e-12
+
+
+def test_r_from_eps_rule():
+    for eps, r in [(1e-3, 8), (1e-4, 8), (1e-5, 10), (1e-6, 10), (1e-8, 12), (1e-10, 14)]:
+        assert api.Plan(4096, eps=eps, factor=False).info()["r"] == r
+
+
+def test_bad_arguments_raise():
+    with pytest.raises(L.BFError):
+        api.Plan(1000)                       # not a power of two
+    with pytest.raises(L.BFError):
+        api.Plan(64, r=10)                   # too small for r = 10
+    with pytest.raises(L.BFError):
+        api.Plan(1024, eps=2.0)
+    with pytest.raises(L.BFError):
+        api.Plan(1024, r=20)                 # r outside the built kernels
+
+
+def test_save_load_roundtrip():
+    p = api.Plan(1024, r=10, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(1024, 2, seed=4)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "plan.bf")
+        p.save(path)
+        q = api.Plan.load(path)
+        assert q.info()["r"] == 10 and q.info()["r_alpha"] == 2
+        assert np.array_equal(factored_ref.apply(p, F), factored_ref.apply(q, F))
+        with open(path, "r+b") as fh:
+            fh.truncate(1000)
+        with pytest.raises(L.BFError):
+            api.Plan.load(path)
+
+
+def test_user_callbacks_match_builtin():
+    import math
+    N = 512
+    phi = lambda x, xi: x * xi + (2 + math.sin(2 * math.pi * x)) / 16 * abs(xi)
+    alpha = lambda x, xi: 1 + 0.25 * math.sin(2 * math.pi * x) * math.cos(2 * math.pi * xi / N)
+    p_user = api.Plan(N, r=10, phase_kind=L.PHASE_USER, amp_kind=L.AMP_USER, phi=phi, alpha=alpha)
+    p_built = api.Plan(N, r=10, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(N, 1, seed=5)
+    assert relerr(factored_ref.apply(p_user, F), factored_ref.apply(p_built, F)) < 1e-9

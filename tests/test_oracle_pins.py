@@ -217,6 +217,17 @@ def test_lowrank_amplitude_rank_two():
     assert eps_amp < 1e-12                                      # Table 1D-FIO: eps^amp ~ 1e-15
 
 
+@pytest.mark.parametrize("amp,rank", [(0, 1), (1, 2)])
+def test_lowrank_exact_low_rank_amplitudes(amp, rank):
+    # alpha = 1 (rank 1) and the smooth amplitude (rank 2) are recovered exactly
+    N = 1024
+    ent = lambda I, J: d.amplitude(amp, N, np.asarray(I)[:, None], np.asarray(J)[None, :])
+    a, b = lr.amplitude_split(ent, N, N)
+    assert a.shape[0] == rank
+    A = ent(np.arange(N), np.arange(N))
+    assert np.abs(a.T @ b - A).max() < 1e-12
+
+
 def test_lowrank_random_complex_matches_svd():
     rng = np.random.default_rng(14)
     m, n, k = 300, 200, 4
