@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the butterfly-factorisation apply (one JSON line on rank 0).
+
+Default workload: the 1D FIO of Sec. 5 with the smooth rank-2 amplitude,
+N = 65536, m = 64 complex right-hand sides, complex FP32 apply, BF built to
+eps = 1e-6.  One step = one full apply G = K F (amplitude split-in, V, all H
+levels, switch, all G levels, U, amplitude split-out).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload fio2|fio1|fio3] [--prec f32|f64]
+
+Under torchrun each rank applies its own operator replica to its own m
+right-hand sides (weak scaling, no data-path collective).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BF-apply complex GN·RHS/s at stated rel err vs FP64; % HBM peak; serve p99 ms"
+UNIT = "GN·RHS/s"
+
+WORKLOADS = {
+    # name: N, m, phase, amp, eps, prec, split, description
+    "fio2": dict(N=65536, m=64, phase=1, amp=1, eps=1e-6, prec="f32", split=1,
+                 desc="1D FIO Phi=x xi+c(x)|xi|, c=(2+sin 2pi x)/16, alpha=1+0.25 sin(2pi x)cos(2pi xi/N), "
+                      "N=65536, m=64 complex Gaussian RHS, complex FP32 apply, eps=1e-6"),
+    "fio1": dict(N=1024, m=1, phase=1, amp=0, eps=1e-6, prec="f64", split=1,
+                 desc="1D FIO, alpha=1, N=1024, one RHS, FP64 apply, eps=1e-6"),
+    "fio3": dict(N=262144, m=256, phase=2, amp=1, eps=1e-6, prec="f32", split=2,
+                 desc="piecewise FIO (jump at x=1/2), N=262144 as four N/2 sub-BFs, m=256, complex FP32 apply"),
+}
+
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def algorithmic(info, m, N, split):
+    """Algorithmic flops per launch of the front and back kernels and the
+    algorithmic bytes of one apply (c64), from the factored form's stage
+    formulas (stated in the design doc)."""
+    r, l1, ra = info["r"], info["l1"], info["r_alpha"]
+    L, h = info["L"], info["h"]
+    Nb = N // split
+    P = Nb // info["n0"]
+    kH, kG = h - l1, L - l1 - h
+    M = ra * m
+    front = M * (6 * Nb + (2 ** l1) * Nb * (6 + 4 * r) + kH * P * (12 * r + 8 * r * r) + 8 * P * r * r)
+    back = M * (kG * P * (8 * r * r + 16 * r) + (2 ** l1) * Nb * (4 * r + 8) + 8 * Nb)
+    nblk = split * split
+    fac = 8 * ((2 ** l1) * Nb * 2 + (kH + kG) * P * 2 * r + P * r * r + 2 * ra * Nb)  # EV, EU, EH/FG, S, a/b
+    bytes_apply = nblk * fac + 2 * 8 * N * m
+    return front, back, bytes_apply
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("bf_kernels_f32.cu", "bf_kernels_f64.cu"):
+        with open(os.path.join(ROOT, "paper_1803_04128_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    if it was captured from a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_oracle_rate(w, F, G_gpu, budget_s, max_rows=None):
+    """Time the FP64 direct oracle on sampled rows (all m RHS); also the rel.
+    error of the GPU result on those rows.  Returns a dict."""
+    import numpy as np
+    from oracle import direct as od
+    from paper_1803_04128_gb300 import inputs
+    N, m = w["N"], w["m"]
+    kind = w["phase"]
+    probe = inputs.sample_rows(N, 8, seed=11)
+    t0 = time.perf_counter()
+    od.direct(kind, N, F, probe, amp=w["amp"])
+    per_row = (time.perf_counter() - t0) / probe.size
+    k = int(max(8, min(N, budget_s / max(per_row, 1e-9))))
+    if max_rows:
+        k = min(k, max_rows)
+    rows = inputs.sample_rows(N, k, seed=12)
+    t0 = time.perf_counter()
+    gd = od.direct(kind, N, F, rows, amp=w["amp"])
+    dt = time.perf_counter() - t0
+    out = {"value": rows.size * m / dt / 1e9, "unit": UNIT, "cores": od.num_threads(), "kind": "oracle",
+           "sample": "%d of N=%d rows x all %d RHS, FP64 direct O(N^2) oracle (compensated sums), %.1f s"
+                     % (rows.size, N, m, dt), "seconds": dt}
+    if G_gpu is not None:
+        g = G_gpu[rows].astype(np.complex128)
+        out["rel_err_gpu"] = float(np.linalg.norm(g - gd) / np.linalg.norm(gd))
+        out["rows_compared"] = int(rows.size)
+    return out
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import direct as od
+    from paper_1803_04128_gb300 import inputs
+    F = inputs.complex_gaussian(w["N"], w["m"], seed=0)
+    rows_all = inputs.sample_rows(w["N"], 4096, seed=13)
+    probe = rows_all[:4]
+    t0 = time.perf_counter()
+    od.direct(w["phase"], w["N"], F, probe, amp=w["amp"])
+    per_row = (time.perf_counter() - t0) / probe.size
+    k = int(max(1, min(rows_all.size // max(1, args.steps + args.warmup), 8.0 / max(per_row, 1e-9))))
+    t_total, done = 0.0, 0
+    for s in range(args.warmup + args.steps):
+        rows = rows_all[(s * k) % rows_all.size:][:k]
+        t0 = time.perf_counter()
+        od.direct(w["phase"], w["N"], F, rows, amp=w["amp"])
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            t_total += dt
+            done += rows.size
+    v = done * w["m"] / t_total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded complex Gaussian F; analytic kernel)",
+            "config": {"workload": w["desc"], "N": w["N"], "m": w["m"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": od.num_threads(), "kind": "oracle",
+                             "sample": "%d rows x all %d RHS per step, FP64 direct oracle" % (k, w["m"])},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fio2", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default=None, choices=["f32", "f64"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload])
+    if args.prec:
+        w["prec"] = args.prec
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1803_04128_gb300 import _lib as L
+    from paper_1803_04128_gb300 import api, inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    N, m = w["N"], w["m"]
+    prec = api.F64 if w["prec"] == "f64" else api.F32
+    cdt = torch.complex128 if prec == api.F64 else torch.complex64
+    t0 = time.perf_counter()
+    plan = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local)
+    t_factor = time.perf_counter() - t0
+    info = plan.info()
+    plan.reserve(prec, m)
+    Fh = inputs.complex_gaussian(N, m, seed=rank)
+    F = torch.from_numpy(Fh).to(cdt).cuda()
+    G = torch.empty_like(F)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        plan.apply(F, G, prec)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        with api.KernelTimer() as kt:
+            for i in range(args.steps):
+                flush.zero_()                      # L2 flush between timed steps (not timed)
+                ev[i][0].record(stream)
+                plan.apply(F, G, prec)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * N * m * args.steps / (ms_max * 1e-3) / 1e9
+
+    peaks, peak_src = load_peaks()
+    front, back, bytes_apply = algorithmic(info, m, N, w["split"])
+    sm_mhz_max = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12   # TFLOP/s FP32 FMA
+    roof = None
+    launches = sum(n for n, _ in kt.result.values())
+    if prec == api.F32 and "front_f32" in kt.result:
+        nf, tf = kt.result["front_f32"]
+        nb, tb = kt.result["back_f32"]
+        nblk = w["split"] ** 2
+        dom, n_l, t_l, flops = ("front_f32", nf, tf, front) if tf >= tb else ("back_f32", nb, tb, back)
+        avg_ms = t_l / n_l
+        achieved = flops / (avg_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": ncu_traffic(dom, args.workload),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)" % (sm_mhz_max, peak_src),
+                "kernel_ms": {k: v[1] / v[0] for k, v in kt.result.items()},
+                "share": {k: v[1] / sum(x[1] for x in kt.result.values()) for k, v in kt.result.items()}}
+        _ = nblk
+    elif kt.result:
+        tot = sum(v[1] for v in kt.result.values())
+        dom = max(kt.result, key=lambda k: kt.result[k][1])
+        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": None, "traffic": None,
+                "kernel_ms": {k: v[1] / v[0] for k, v in kt.result.items()},
+                "share": {k: v[1] / tot for k, v in kt.result.items()}}
+    hbm_frac = bytes_apply / (ms_max / args.steps * 1e-3) / (peaks["hbm_gbs"] * 1e9)
+
+    # end to end through bf_apply_host with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Fp = torch.from_numpy(Fh).to(cdt).pin_memory()
+        Gp = torch.empty_like(Fp).pin_memory()
+        for _ in range(2):
+            plan.apply_host(Fp, Gp, prec)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.apply_host(Fp, Gp, prec)
+        t_e2e = time.perf_counter() - t0
+        te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        nbytes = Fp.numel() * Fp.element_size()
+        e2e = {"value": world * N * m * args.steps / float(te.item()) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Gh = G.cpu().numpy()
+        cpu = cpu_oracle_rate(w, Fh, Gh, args.cpu_budget)
+
+    if rank == 0:
+        cfg = {"workload": w["desc"], "N": N, "m": m, "r": info["r"], "r_alpha": info["r_alpha"],
+               "eps": w["eps"], "L": info["L"], "split": w["split"], "l2": "flushed (512 MB write) between timed steps",
+               "t_factor_s": round(t_factor, 3), "parallelism": "replicas" if world > 1 else "single GPU",
+               "hbm_frac_of_measured": hbm_frac, "algorithmic_bytes_per_step": bytes_apply,
+               "algorithmic_flops_per_step": (front + back) * w["split"] ** 2}
+        if cpu is not None and "rel_err_gpu" in cpu:
+            cfg["rel_err_vs_fp64_oracle"] = cpu.pop("rel_err_gpu")
+            cfg["rel_err_rows"] = cpu.pop("rows_compared")
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == api.F64 else "f32",
+                "data": "synthetic (seeded complex Gaussian F; analytic kernel)", "config": cfg,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary()}
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -81,8 +81,7 @@ typedef double (*bf_phase_fn)(double x, double xi, void* user);
 /* User amplitude: writes alpha(x, xi) = *re + i *im. */
 typedef void (*bf_amp_fn)(double x, double xi, void* user, double* re, double* im);
 
-/* The operator: an N x N block of the transform on a grid of n_global points
- * (row0 = col0 = 0 and n_global = N for the whole transform). */
+/* The operator: the N x N transform on the grid x_i = i/N, xi_j = j - N/2. */
 typedef struct {
     int64_t N;            /* power of two                                       */
     int phase_kind;       /* bf_phase_kind                                      */
@@ -98,8 +97,8 @@ typedef struct {
     int n0;               /* leaf size of both trees (power of two, default 1, Fig. 2)    */
     int split;            /* 1: one BF; 2: four N/2 x N/2 sub-BFs (rows and columns cut    *
                            *    at N/2, i.e. at x = 1/2 and xi = 0)                        */
-    int amp_rank;         /* rank parameter of Algorithm 1 (default 20)                    */
-    int amp_oversample;   /* oversampling q of Algorithm 1 (default 5)                     */
+    int amp_rank;         /* rank parameter r of Algorithm 1 (default 8)                   */
+    int amp_oversample;   /* oversampling q of Algorithm 1 (default 3)                     */
     double amp_tol;       /* relative singular-value cut for r_alpha (default 1e-13)       */
     uint64_t seed;        /* sampling seed of Algorithm 1 (default 0)                      */
     int keep_host;        /* keep the FP64 host factors after upload (default 1)           */
@@ -196,6 +195,18 @@ const char* bf_last_error(void);
 
 /* Library version string. */
 const char* bf_version(void);
+
+/* Kernel timing, for measurement: between bf_profile_begin() and
+ * bf_profile_end() every kernel the library launches is bracketed by CUDA
+ * events recorded on the stream it is launched on.  bf_profile_end()
+ * synchronises those events and aggregates them per kernel name;
+ * bf_profile_count()/bf_profile_get() then read the aggregate (name,
+ * launches, total milliseconds).  Process-wide; not for use inside stream
+ * capture. */
+bf_status bf_profile_begin(void);
+bf_status bf_profile_end(void);
+int bf_profile_count(void);
+bf_status bf_profile_get(int i, const char** name, int64_t* launches, double* total_ms);
 
 #ifdef __cplusplus
 }

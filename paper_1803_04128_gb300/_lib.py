@@ -64,6 +64,11 @@ _SIGS = {
     "bf_grid_indices": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int)]),
     "bf_last_error": (ctypes.c_char_p, []),
+    "bf_profile_begin": (ctypes.c_int, []),
+    "bf_profile_end": (ctypes.c_int, []),
+    "bf_profile_count": (ctypes.c_int, []),
+    "bf_profile_get": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_double)]),
     "bf_version": (ctypes.c_char_p, []),
 }
 

@@ -164,5 +164,26 @@ class Plan:
         return self._lib.bf_sync_status(self._h, _stream_ptr(stream))
 
 
+class KernelTimer:
+    """Context manager: CUDA-event times of every library kernel launched inside
+    (bf_profile_begin/end).  ``.result`` maps kernel name -> (launches, total_ms)."""
+
+    def __enter__(self):
+        L.check(L.lib().bf_profile_begin(), "bf_profile_begin")
+        return self
+
+    def __exit__(self, *exc):
+        lib = L.lib()
+        L.check(lib.bf_profile_end(), "bf_profile_end")
+        self.result = {}
+        for i in range(lib.bf_profile_count()):
+            name = ctypes.c_char_p()
+            n = ctypes.c_int64()
+            ms = ctypes.c_double()
+            L.check(lib.bf_profile_get(i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms)), "bf_profile_get")
+            self.result[name.value.decode()] = (n.value, ms.value)
+        return False
+
+
 def version():
     return L.lib().bf_version().decode()

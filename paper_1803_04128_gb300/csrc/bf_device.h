@@ -80,4 +80,14 @@ cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, floa
                              float2* ws, cudaStream_t st);
 bool fused_f32_supported(int r);
 
+// per-launch event timing (bf_profile_*); no-ops unless profiling is on
+void prof_start(const char* name, cudaStream_t st, void** tok);
+void prof_stop(void* tok, cudaStream_t st);
+struct ProfScope {
+    void* tok;
+    cudaStream_t st;
+    ProfScope(const char* name, cudaStream_t s) : st(s) { prof_start(name, s, &tok); }
+    ~ProfScope() { prof_stop(tok, st); }
+};
+
 }  // namespace bfi

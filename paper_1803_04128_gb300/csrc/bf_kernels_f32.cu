@@ -421,7 +421,10 @@ cudaError_t launch_r(const DevBlock& B, const float2* F, int64_t m, float2* G, i
         attr_set = true;
     }
     const int64_t ntile = ((int64_t)1 << g.l1) * ((int64_t)1 << (g.L - g.h));
-    front_f32<R><<<(unsigned)(ntile * cfg.nslice), kThreads, sf, st>>>(fa);
+    {
+        ProfScope ps("front_f32", st);
+        front_f32<R><<<(unsigned)(ntile * cfg.nslice), kThreads, sf, st>>>(fa);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     BackArgs ba;
@@ -440,7 +443,10 @@ cudaError_t launch_r(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     ba.beta = beta;
     const size_t sb = back_smem(g, R, fa.CT, cfg.mr);
     const int64_t nback = ((int64_t)1 << g.h) * cfg.nslice;
-    back_f32<R, NU><<<(unsigned)nback, kThreads, sb, st>>>(ba);
+    {
+        ProfScope ps("back_f32", st);
+        back_f32<R, NU><<<(unsigned)nback, kThreads, sb, st>>>(ba);
+    }
     return cudaGetLastError();
 }
 

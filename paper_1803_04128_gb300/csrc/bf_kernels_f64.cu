@@ -180,23 +180,38 @@ cudaError_t launch_plain_f64(const DevBlock& B, const double2* F, int64_t m, dou
         if (!beta) return cudaMemsetAsync(G, 0, (size_t)g.N * m * sizeof(double2), st);
         return cudaSuccess;
     }
-    v_f64<<<grid_for(nst, T), T, 0, st>>>(g, f.Mv, f.EV, f.b, F, m, ws0);
+    {
+        ProfScope ps("v_f64", st);
+        v_f64<<<grid_for(nst, T), T, 0, st>>>(g, f.Mv, f.EV, f.b, F, m, ws0);
+    }
     double2 *cur = ws0, *nxt = ws1;
     for (int j = 0; j < g.kH; ++j) {
         const int l = g.l1 + 1 + j;
+        {
+        ProfScope ps("h_f64", st);
         h_f64<<<grid_for(nst, T), T, 0, st>>>(g, l, f.MH + (size_t)j * g.r * 2 * g.r,
-                                               f.EH + (size_t)j * g.P * 2 * g.r, cur, M, nxt);
+                                                   f.EH + (size_t)j * g.P * 2 * g.r, cur, M, nxt);
+    }
         std::swap(cur, nxt);
     }
-    s_f64<<<grid_for(nst, T), T, 0, st>>>(g, f.S, cur, M, nxt);
+    {
+        ProfScope ps("s_f64", st);
+        s_f64<<<grid_for(nst, T), T, 0, st>>>(g, f.S, cur, M, nxt);
+    }
     std::swap(cur, nxt);
     for (int j = 0; j < g.kG; ++j) {
         const int l = g.h + 1 + j;
+        {
+        ProfScope ps("g_f64", st);
         g_f64<<<grid_for(nst, T), T, 0, st>>>(g, l, f.MG + (size_t)j * 2 * g.r * g.r,
-                                               f.FG + (size_t)j * g.P * 2 * g.r, cur, M, nxt);
+                                                   f.FG + (size_t)j * g.P * 2 * g.r, cur, M, nxt);
+    }
         std::swap(cur, nxt);
     }
-    u_f64<<<grid_for(g.N * m, T), T, 0, st>>>(g, f.MU, f.EU, f.a, cur, m, beta, G);
+    {
+        ProfScope ps("u_f64", st);
+        u_f64<<<grid_for(g.N * m, T), T, 0, st>>>(g, f.MU, f.EU, f.a, cur, m, beta, G);
+    }
     return cudaGetLastError();
 }
 

@@ -1,0 +1,168 @@
+"""GPU parity: the CUDA apply (through the C ABI) against the oracle.
+
+Two oracles: (i) Algorithm 4.1 evaluated on the fly in FP64
+(oracle/butterfly.py) -- the same approximation the library stores, so the
+difference is rounding only; (ii) the direct FP64 matvec (oracle/direct.c) --
+the plain definition, so the difference is the BF error plus rounding.
+
+Tolerances (relative l2 over the compared entries, eps^b of Sec. 5):
+  * FP64 plain form vs (i): 1e-12 (rounding of ~2L+3 stages of short sums).
+  * FP32 vs (i): 2e-6.  Each stage multiplies by unit-modulus phases and
+    applies Lagrange weights with sum of |weights| <= ~3 (Lebesgue constant of
+    the mock-Chebyshev grids, r <= 16); over <= 2L+3 <= 40 stages with
+    u = 2^-24 the worst-case relative growth is ~40 * 3 * 6e-8 = 7e-6 and the
+    random-walk estimate sqrt(40) * 3 * 6e-8 = 1.1e-6; 2e-6 sits between.
+  * FP32 vs (ii): 1e-5, the stated FP32 target; FP64 vs (ii): eps = 1e-6.
+"""
+import numpy as np
+import pytest
+
+from conftest import relerr
+from oracle import butterfly as obf
+from oracle import direct as od
+from oracle import lowrank as olr
+from paper_1803_04128_gb300 import _lib as L
+from paper_1803_04128_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_04128_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def oracle_ibf(kind, N, F, r, amp, n_global=None):
+    ent = lambda I, J: od.amplitude(amp, N, np.asarray(I)[:, None], np.asarray(J)[None, :])
+    a, b = olr.amplitude_split(ent, N, N)
+    return obf.ibf_apply(kind, N, F, r, a, b)
+
+
+def run(plan, F, prec):
+    dt = torch.complex128 if prec == api.F64 else torch.complex64
+    Ft = torch.from_numpy(np.ascontiguousarray(F)).to(dt).cuda()
+    G = plan.apply(Ft, prec=prec)
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    return G.cpu().numpy().astype(np.complex128)
+
+
+# ------------------------------------------------ precision-only parity ----
+@pytest.mark.parametrize("N,r,m", [(256, 8, 1), (1024, 10, 3), (1024, 10, 37), (4096, 12, 5),
+                                   (2048, 16, 2), (4096, 6, 130), (8192, 10, 17)])
+@pytest.mark.parametrize("kind", [L.PHASE_FIO, L.PHASE_FIO_PW])
+def test_f32_and_f64_match_algorithm_4_1(N, r, m, kind):
+    plan = api.Plan(N, r=r, phase_kind=kind, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(N, m, seed=N + m)
+    ref = oracle_ibf(kind, N, F, r, 1)
+    g32 = run(plan, F, api.F32)
+    assert relerr(g32, ref) < 2e-6
+    g64 = run(plan, F, api.F64)
+    assert relerr(g64, ref) < 1e-12
+
+
+@pytest.mark.parametrize("kind", [L.PHASE_DFT, L.PHASE_ONES, L.PHASE_SEP])
+def test_special_kernels(kind):
+    N, m = 2048, 4
+    plan = api.Plan(N, r=10, phase_kind=kind)
+    F = inputs.complex_gaussian(N, m, seed=3)
+    gd = od.direct(kind, N, F)
+    assert relerr(run(plan, F, api.F32), gd) < 1e-5
+    if kind != L.PHASE_DFT:                      # R(A,B) = 0: the BF is exact
+        assert relerr(run(plan, F, api.F64), gd) < 1e-12
+
+
+def test_split_plan():
+    N, m = 4096, 6
+    plan = api.Plan(N, r=10, phase_kind=L.PHASE_FIO_PW, amp_kind=L.AMP_SMOOTH, split=2)
+    F = inputs.complex_gaussian(N, m, seed=5)
+    gd = od.direct(od.FIOPW, N, F, amp=1)
+    assert relerr(run(plan, F, api.F32), gd) < 1e-5
+    assert relerr(run(plan, F, api.F64), gd) < 1e-6
+
+
+# ------------------------------------------------------- direct oracle -----
+def test_config1_fp64_n1024():
+    # 1D FIO, N = 1024, alpha = 1, eps = 1e-6, one RHS, FP64 apply
+    N = 1024
+    plan = api.Plan(N, eps=1e-6, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_ONE)
+    F = inputs.complex_gaussian(N, 1, seed=0)
+    g = run(plan, F, api.F64)
+    gd = od.direct(od.FIO, N, F)
+    assert relerr(g, gd) < 1e-6
+
+
+def test_config2_fp32_full_size_sampled_rows():
+    # N = 65536, m = 64, smooth amplitude, complex FP32: 128 sampled rows
+    N, m = 65536, 64
+    plan = api.Plan(N, eps=1e-6, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(N, m, seed=0)
+    g = run(plan, F, api.F32)
+    rows = inputs.sample_rows(N, 128, seed=0)
+    gd = od.direct(od.FIO, N, F, rows, amp=1)
+    assert relerr(g[rows], gd) < 1e-5
+
+
+def test_config3_shape_fp32_sampled():
+    # N = 262144 piecewise phase, four N/2 sub-BFs; 48 rows x 8 columns sampled
+    N, m = 262144, 8
+    plan = api.Plan(N, eps=1e-6, phase_kind=L.PHASE_FIO_PW, amp_kind=L.AMP_SMOOTH, split=2)
+    F = inputs.complex_gaussian(N, m, seed=0)
+    g = run(plan, F, api.F32)
+    rows = np.concatenate([inputs.sample_rows(N // 2, 24, seed=1), N // 2 + inputs.sample_rows(N // 2, 24, seed=2)])
+    gd = od.direct(od.FIOPW, N, F, rows, amp=1)
+    assert relerr(g[rows], gd) < 1e-5
+
+
+# ----------------------------------------------------------- edge cases ----
+def test_columns_are_independent_and_bitwise_batch_invariant():
+    N, m = 4096, 24
+    plan = api.Plan(N, r=10, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(N, m, seed=7)
+    Gall = run(plan, F, api.F32)
+    for c in (0, 5, 23):
+        g1 = run(plan, F[:, c:c + 1], api.F32)
+        assert np.array_equal(g1[:, 0], Gall[:, c])
+    # repeated applies are deterministic
+    assert np.array_equal(run(plan, F, api.F32), Gall)
+
+
+def test_zero_impulse_linearity():
+    N = 1024
+    plan = api.Plan(N, r=10)
+    assert np.all(run(plan, np.zeros((N, 3), complex), api.F32) == 0)
+    e = np.zeros((N, 1), complex); e[17] = 1
+    col = od.entries(od.FIO, N, np.arange(N), [17])
+    assert relerr(run(plan, e, api.F32), col) < 1e-5
+    F = inputs.complex_gaussian(N, 2, seed=9)
+    a, b = 0.5 - 2j, 1.5 + 0.25j
+    lhs = run(plan, a * F[:, :1] + b * F[:, 1:], api.F64)
+    rhs = a * run(plan, F[:, :1], api.F64) + b * run(plan, F[:, 1:], api.F64)
+    assert relerr(lhs, rhs) < 1e-13
+
+
+def test_apply_host_matches_device_apply():
+    N, m = 2048, 9
+    plan = api.Plan(N, r=10, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(N, m, seed=11).astype(np.complex64)
+    Gh = plan.apply_host(F)
+    Gd = run(plan, F, api.F32)
+    assert np.array_equal(Gh.astype(np.complex128), Gd)
+
+
+def test_bad_calls_return_errors():
+    plan = api.Plan(1024, r=10)
+    F = torch.zeros((1024, 2), dtype=torch.complex64, device="cuda")
+    lib = L.lib()
+    import ctypes
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.bf_apply(plan._h, api.F32, ctypes.c_void_p(F.data_ptr()), 0, ctypes.c_void_p(F.data_ptr()), s) == L.BF_ERR_ARG
+    assert lib.bf_apply(plan._h, api.F32, ctypes.c_void_p(F.data_ptr()), 2, ctypes.c_void_p(F.data_ptr()), s) == L.BF_ERR_ARG
+    assert lib.bf_apply(plan._h, 7, ctypes.c_void_p(F.data_ptr()), 2, ctypes.c_void_p(F.data_ptr() + 64), s) == L.BF_ERR_ARG
+    assert lib.bf_apply(None, api.F32, ctypes.c_void_p(F.data_ptr()), 2, ctypes.c_void_p(F.data_ptr() + 64), s) == L.BF_ERR_ARG
