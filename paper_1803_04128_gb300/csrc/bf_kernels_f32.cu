@@ -6,7 +6,7 @@
 // writes the switch-level coefficients.  A front tile is fixed by an x-node p
 // at level l1 and a chunk c0 of T_Omega nodes: its 2^kH pairs stay closed
 // under the kH H levels because the pair (A, B) at level l only depends on
-// (parent(A), children(B)) at level l-1 (Sec. 4, "C > B", "P is A's parent").
+// (parent(A), children(B)) at level l-1 (Sec. 4).
 //
 // Back pass (one CTA per x-node p' at level h x column slice): loops over the
 // 2^l1 chunks c0' of T_Omega nodes; for each, loads 2^kG switch-level pairs,
@@ -18,9 +18,13 @@
 // the logical pair [a: j bits][b: K-j bits] live in slot b * 2^j + rev_j(a),
 // so every group of two pairs reads and writes the same two slots.
 //
-// Columns: a tile carries CT = r_alpha * mr columns, col = k * mr + c
-// (amplitude term k, right-hand side slice * mr + c).  Global state between
-// the passes: W[slice][q][t][CT] (q = switch-level pair index).
+// Columns: a tile carries CT = r_alpha * mr live columns, col = k * mr + c
+// (amplitude term k, right-hand side slice * mr + c), padded to CTp, a power
+// of two, so that a thread's column is tid & (CTp - 1).  Global state between
+// the passes: W[slice][q][t][CTp] (q = switch-level pair index).
+//
+// Every tile input (factor phases, Lagrange matrices, the F rows, b_k) is
+// staged into shared memory with cp.async in one commit group before use.
 #include <cstdio>
 
 #include "bf_device.h"
@@ -44,24 +48,57 @@ __device__ __forceinline__ unsigned brev(unsigned v, int bits)
     return bits == 0 ? 0u : (__brev(v) >> (32 - bits));
 }
 
+// ---- cp.async (16- and 8-byte, the latter with zero fill) ----
+__device__ __forceinline__ void cp16(void* dst, const void* src)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp8(void* dst, const void* src, bool valid)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    int n = valid ? 8 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_commit_wait()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// real rows x cols matrix (row-major, global) -> shared rows padded to c4 floats, 8-byte copies
+__device__ __forceinline__ void stage_matrix(float* dst, const float* src, int rows, int cols, int c4, int tid)
+{
+    const int half = cols / 2;
+    for (int e = tid; e < rows * half; e += kThreads) {
+        const int rr = e / half, cc = e - rr * half;
+        cp8(dst + rr * c4 + 2 * cc, src + rr * cols + 2 * cc, true);
+    }
+}
+
+template <int R>
+struct Pad4 {
+    static constexpr int v = (R + 3) & ~3;
+};
+
 struct FrontArgs {
     Geo g;
     const float2* F;  // [N][m]
     int64_t m;
-    int mr, CT, nslice;
+    int mr, lmr, CTp, lct, nslice;
     const float2* bk;  // [ra][N]
     const float* MvT;  // [nv][R]
     const float2* EV;  // [2^l1][N]
     const float* MHT;  // [kH][2R][R]
     const float2* EH;  // [kH][P][2][R]
     const float2* S;   // [P][R][R]
-    float2* W;         // [nslice][P][R][CT]
+    float2* W;         // [nslice][P][R][CTp]
 };
 
 struct BackArgs {
     Geo g;
     int64_t m;
-    int mr, CT, nslice;
+    int mr, lmr, CTp, lct, nslice;
     const float2* W;
     const float* MGT;  // [kG][2][R][R]  (pos, s, t)
     const float2* FG;  // [kG][P][2][R]
@@ -72,150 +109,250 @@ struct BackArgs {
     int beta;
 };
 
-// ------------------------------------------------------------------ front --
+// H level (Eq. 2) on one (group, column): two inputs -> two outputs in place.
 template <int R>
+__device__ __forceinline__ void h_item(float2* x0, float2* x1, int CTp, const float2* E0, const float2* E1,
+                                       const float* Mh)
+{
+    constexpr int R4 = Pad4<R>::v;
+    float2 lam[2 * R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+        lam[s] = x0[s * CTp];
+        lam[R + s] = x1[s * CTp];
+    }
+    float2 o0[R], o1[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) o0[t] = o1[t] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int cs2 = 0; cs2 < R; ++cs2) {
+        const float4 e0 = reinterpret_cast<const float4*>(E0)[cs2];
+        const float4 e1 = reinterpret_cast<const float4*>(E1)[cs2];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int cs = 2 * cs2 + h2;
+            const float2 u0 = cmulf(h2 ? make_float2(e0.z, e0.w) : make_float2(e0.x, e0.y), lam[cs]);
+            const float2 u1 = cmulf(h2 ? make_float2(e1.z, e1.w) : make_float2(e1.x, e1.y), lam[cs]);
+            const float4* mh = reinterpret_cast<const float4*>(Mh + cs * R4);
+#pragma unroll
+            for (int t4 = 0; t4 < R4 / 4; ++t4) {
+                const float4 w = mh[t4];
+                const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int t = 4 * t4 + q;
+                    if (t < R) {
+                        o0[t].x = fmaf(ww[q], u0.x, o0[t].x);
+                        o0[t].y = fmaf(ww[q], u0.y, o0[t].y);
+                        o1[t].x = fmaf(ww[q], u1.x, o1[t].x);
+                        o1[t].y = fmaf(ww[q], u1.y, o1[t].y);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        x0[t * CTp] = o0[t];
+        x1[t * CTp] = o1[t];
+    }
+}
+
+// G level (Eq. 3) on one (group, column): nu_pos = sum_c FG[pos][c] (MG[pos] nu_c).
+template <int R>
+__device__ __forceinline__ void g_item(float2* x0, float2* x1, int CTp, const float2* F0, const float2* F1,
+                                       const float* Mg)
+{
+    constexpr int R4 = Pad4<R>::v;
+    float2 nu0[R], nu1[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+        nu0[s] = x0[s * CTp];
+        nu1[s] = x1[s * CTp];
+    }
+#pragma unroll
+    for (int pos = 0; pos < 2; ++pos) {
+        float2 w0[R], w1[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) w0[t] = w1[t] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            const float4* mg = reinterpret_cast<const float4*>(Mg + (pos * R + s) * R4);
+#pragma unroll
+            for (int t4 = 0; t4 < R4 / 4; ++t4) {
+                const float4 w = mg[t4];
+                const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int t = 4 * t4 + q;
+                    if (t < R) {
+                        w0[t].x = fmaf(ww[q], nu0[s].x, w0[t].x);
+                        w0[t].y = fmaf(ww[q], nu0[s].y, w0[t].y);
+                        w1[t].x = fmaf(ww[q], nu1[s].x, w1[t].x);
+                        w1[t].y = fmaf(ww[q], nu1[s].y, w1[t].y);
+                    }
+                }
+            }
+        }
+        const float2* Fp = pos ? F1 : F0;  // [c][t]
+        float2* xo = pos ? x1 : x0;
+#pragma unroll
+        for (int t2 = 0; t2 < R / 2; ++t2) {
+            const float4 fa = reinterpret_cast<const float4*>(Fp)[t2];
+            const float4 fb = reinterpret_cast<const float4*>(Fp + R)[t2];
+            float2 o = cmulf(make_float2(fa.x, fa.y), w0[2 * t2]);
+            cfmaf(o, make_float2(fb.x, fb.y), w1[2 * t2]);
+            xo[(2 * t2) * CTp] = o;
+            float2 o2 = cmulf(make_float2(fa.z, fa.w), w0[2 * t2 + 1]);
+            cfmaf(o2, make_float2(fb.z, fb.w), w1[2 * t2 + 1]);
+            xo[(2 * t2 + 1) * CTp] = o2;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ front --
+template <int R, int NV>
 __global__ void __launch_bounds__(kThreads, 2) front_f32(FrontArgs A)
 {
+    constexpr int R4 = Pad4<R>::v;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geo& g = A.g;
-    const int K = g.kH, T = 1 << K, CT = A.CT, mr = A.mr, nv = g.nv;
+    const int K = g.kH, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra;
     const int slice = blockIdx.x % A.nslice;
     const int64_t tile = blockIdx.x / A.nslice;
-    const int nP = 1 << g.l1;                  // x-nodes at level l1
-    const int64_t p = tile % nP, c0 = tile / nP;
-    const int64_t nBh = (int64_t)1 << (g.L - g.h);  // T_Omega nodes at level L-h
+    const int nP = 1 << g.l1;                       // x-nodes at level l1
+    const int64_t p = tile & (nP - 1), c0 = tile >> g.l1;
+    const int64_t nBh = (int64_t)1 << (g.L - g.h);   // T_Omega nodes at level L-h
+    const int64_t xi_base = c0 * T * NV;
 
-    float2* X = reinterpret_cast<float2*>(smem_raw);             // [T][R][CT]
-    float2* EHs = X + (size_t)T * R * CT;                         // [K][T][2][R]
-    float2* Ss = EHs + (size_t)K * T * 2 * R;                     // [T][R][R]
-    float2* EVs = Ss + (size_t)T * R * R;                         // [T*nv]
-    float* MvTs = reinterpret_cast<float*>(EVs + (size_t)T * nv); // [nv][R]
-    float* MHTs = MvTs + nv * R;                                  // [K][2R][R]
+    float2* X = reinterpret_cast<float2*>(smem_raw);         // [T][R][CTp]
+    float2* Fs = X + (size_t)T * R * CTp;                     // [T*NV][mr]
+    float2* Bs = Fs + (size_t)T * NV * mr;                    // [ra][T*NV]
+    float2* EHs = Bs + (size_t)ra * T * NV;                   // [K][T][2][R]
+    float2* Ss = EHs + (size_t)K * T * 2 * R;                 // [T][R][R]
+    float2* EVs = Ss + (size_t)T * R * R;                     // [T*NV]
+    float* MvTs = reinterpret_cast<float*>(EVs + (size_t)T * NV);  // [NV][R4]
+    float* MHTs = MvTs + NV * R4;                                  // [K][2R][R4]
 
     const int tid = threadIdx.x;
-    // ---- stage factors of this tile into shared memory
-    for (int e = tid; e < nv * R; e += kThreads) MvTs[e] = A.MvT[e];
-    for (int e = tid; e < K * 2 * R * R; e += kThreads) MHTs[e] = A.MHT[e];
+    // ---- stage every input of this tile (one cp.async group)
+    stage_matrix(MvTs, A.MvT, NV, R, R4, tid);
+    stage_matrix(MHTs, A.MHT, K * 2 * R, R, R4, tid);
     {
-        const float2* ev = A.EV + p * g.N + c0 * T * nv;
-        for (int e = tid; e < T * nv; e += kThreads) EVs[e] = ev[e];
+        const float2* ev = A.EV + p * g.N + xi_base;
+        for (int e = tid; e < T * NV / 2; e += kThreads) cp16(EVs + 2 * e, ev + 2 * e);
     }
     for (int j = 1; j <= K; ++j) {
         const int l = g.l1 + j;
         const int64_t nBl = (int64_t)1 << (g.L - l);
         const float2* eh = A.EH + (size_t)(j - 1) * g.P * 2 * R;
-        for (int e = tid; e < T * 2 * R; e += kThreads) {
-            const int lp = e / (2 * R), w = e % (2 * R);
+        for (int e = tid; e < T * R; e += kThreads) {  // R 16-byte chunks per pair
+            const int lp = e / R, w = e - lp * R;
             const int64_t ap = (p << j) + (lp >> (K - j));
             const int64_t bp = (c0 << (K - j)) + (lp & ((1 << (K - j)) - 1));
-            EHs[((size_t)(j - 1) * T + lp) * 2 * R + w] = eh[(ap * nBl + bp) * 2 * R + w];
+            cp16(EHs + ((size_t)(j - 1) * T + lp) * 2 * R + 2 * w, eh + (ap * nBl + bp) * 2 * R + 2 * w);
         }
     }
-    for (int e = tid; e < T * R * R; e += kThreads) {
-        const int lp = e / (R * R), w = e % (R * R);
+    for (int e = tid; e < T * (R * R / 2); e += kThreads) {
+        const int lp = e / (R * R / 2), w = e - lp * (R * R / 2);
         const int64_t q = ((p << K) + lp) * nBh + c0;
-        Ss[(size_t)lp * R * R + w] = A.S[q * R * R + w];
+        cp16(Ss + (size_t)lp * R * R + 2 * w, A.S + q * R * R + 2 * w);
     }
+    {
+        const int64_t cbase = (int64_t)slice * mr;
+        for (int e = tid; e < T * NV * mr; e += kThreads) {
+            const int row = e >> lmr, c = e & (mr - 1);
+            const bool valid = cbase + c < A.m;
+            cp8(Fs + e, A.F + (xi_base + row) * A.m + (valid ? cbase + c : 0), valid);
+        }
+        for (int e = tid; e < ra * T * NV; e += kThreads) {
+            const int k = e / (T * NV), x = e - k * (T * NV);
+            cp8(Bs + e, A.bk + (size_t)k * g.N + xi_base + x, true);
+        }
+    }
+    // padding columns of the tile start (and stay) at zero
+    for (int e = tid; e < T * R * CTp; e += kThreads)
+        if ((e & (CTp - 1)) >= ra * mr) X[e] = make_float2(0.f, 0.f);
+    cp_commit_wait();
     __syncthreads();
 
     // ---- V (Eq. 1): item (j, c) computes mu[j][.][k*mr + c] for every k
-    for (int it = tid; it < T * mr; it += kThreads) {
-        const int j = it / mr, c = it % mr;
-        const int64_t cg = (int64_t)slice * mr + c;
-        const bool valid = cg < A.m;
-        const int64_t xi0 = (c0 * T + j) * nv;
-        for (int k = 0; k < g.ra; ++k) {
-            float2 acc[R];
+    {
+        const int c = tid & (mr - 1);
+        for (int j = tid >> lmr; j < T; j += kThreads >> lmr) {
+            const float2* fs = Fs + (size_t)j * NV * mr + c;
+            float2 f[NV];
 #pragma unroll
-            for (int t = 0; t < R; ++t) acc[t] = make_float2(0.f, 0.f);
-            const float2* bk = A.bk + (size_t)k * g.N + xi0;
-            for (int x = 0; x < nv; ++x) {
-                float2 f = valid ? A.F[(xi0 + x) * A.m + cg] : make_float2(0.f, 0.f);
-                float2 z = cmulf(EVs[j * nv + x], cmulf(__ldg(bk + x), f));
+            for (int x = 0; x < NV; ++x) f[x] = fs[x * mr];
+            for (int k = 0; k < ra; ++k) {
+                float2 acc[R];
 #pragma unroll
-                for (int t4 = 0; t4 < R / 2; ++t4) {
-                    // R is even: read pairs of weights
-                    float2 w = reinterpret_cast<const float2*>(MvTs + x * R)[t4];
-                    acc[2 * t4].x = fmaf(w.x, z.x, acc[2 * t4].x);
-                    acc[2 * t4].y = fmaf(w.x, z.y, acc[2 * t4].y);
-                    acc[2 * t4 + 1].x = fmaf(w.y, z.x, acc[2 * t4 + 1].x);
-                    acc[2 * t4 + 1].y = fmaf(w.y, z.y, acc[2 * t4 + 1].y);
+                for (int t = 0; t < R; ++t) acc[t] = make_float2(0.f, 0.f);
+                const float2* bs = Bs + (size_t)k * T * NV + j * NV;
+#pragma unroll
+                for (int x = 0; x < NV; ++x) {
+                    const float2 z = cmulf(EVs[j * NV + x], cmulf(bs[x], f[x]));
+                    const float4* mv = reinterpret_cast<const float4*>(MvTs + x * R4);
+#pragma unroll
+                    for (int t4 = 0; t4 < R4 / 4; ++t4) {
+                        const float4 w = mv[t4];
+                        const float ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int t = 4 * t4 + q;
+                            if (t < R) {
+                                acc[t].x = fmaf(ww[q], z.x, acc[t].x);
+                                acc[t].y = fmaf(ww[q], z.y, acc[t].y);
+                            }
+                        }
+                    }
                 }
-            }
-            float2* xo = X + (size_t)j * R * CT + k * mr + c;
+                float2* xo = X + (size_t)j * R * CTp + k * mr + c;
 #pragma unroll
-            for (int t = 0; t < R; ++t) xo[t * CT] = acc[t];
+                for (int t = 0; t < R; ++t) xo[t * CTp] = acc[t];
+            }
         }
     }
 
     // ---- H levels (Eq. 2), in place
+    const int col = tid & (CTp - 1);
     for (int j = 1; j <= K; ++j) {
         __syncthreads();
-        const int half = 1 << (K - j);  // b' range
-        const float* Mh = MHTs + (size_t)(j - 1) * 2 * R * R;
+        const int kj = K - j, half = 1 << kj;
+        const float* Mh = MHTs + (size_t)(j - 1) * 2 * R * R4;
         const float2* Eh = EHs + (size_t)(j - 1) * T * 2 * R;
-        for (int it = tid; it < (T / 2) * CT; it += kThreads) {
-            const int grp = it / CT, col = it % CT;
-            const int a = grp / half, bp = grp % half;
+        for (int grp = tid >> lct; grp < T / 2; grp += kThreads >> lct) {
+            const int a = grp >> kj, bp = grp & (half - 1);
             const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
-            float2* x0 = X + (size_t)base * R * CT + col;
-            float2* x1 = X + (size_t)(base + (1 << (j - 1))) * R * CT + col;
-            float2 lam[2 * R];
-#pragma unroll
-            for (int s = 0; s < R; ++s) {
-                lam[s] = x0[s * CT];
-                lam[R + s] = x1[s * CT];
-            }
-            const float2* E0 = Eh + (size_t)((2 * a) * half + bp) * 2 * R;
-            const float2* E1 = Eh + (size_t)((2 * a + 1) * half + bp) * 2 * R;
-            float2 o0[R], o1[R];
-#pragma unroll
-            for (int t = 0; t < R; ++t) o0[t] = o1[t] = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int cs = 0; cs < 2 * R; ++cs) {
-                const float2 u0 = cmulf(E0[cs], lam[cs]);
-                const float2 u1 = cmulf(E1[cs], lam[cs]);
-                const float2* mh = reinterpret_cast<const float2*>(Mh + cs * R);
-#pragma unroll
-                for (int t2 = 0; t2 < R / 2; ++t2) {
-                    const float2 w = mh[t2];
-                    o0[2 * t2].x = fmaf(w.x, u0.x, o0[2 * t2].x);
-                    o0[2 * t2].y = fmaf(w.x, u0.y, o0[2 * t2].y);
-                    o0[2 * t2 + 1].x = fmaf(w.y, u0.x, o0[2 * t2 + 1].x);
-                    o0[2 * t2 + 1].y = fmaf(w.y, u0.y, o0[2 * t2 + 1].y);
-                    o1[2 * t2].x = fmaf(w.x, u1.x, o1[2 * t2].x);
-                    o1[2 * t2].y = fmaf(w.x, u1.y, o1[2 * t2].y);
-                    o1[2 * t2 + 1].x = fmaf(w.y, u1.x, o1[2 * t2 + 1].x);
-                    o1[2 * t2 + 1].y = fmaf(w.y, u1.y, o1[2 * t2 + 1].y);
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < R; ++t) {
-                x0[t * CT] = o0[t];
-                x1[t * CT] = o1[t];
-            }
+            float2* x0 = X + (size_t)base * R * CTp + col;
+            float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
+            h_item<R>(x0, x1, CTp, Eh + (size_t)((2 * a) * half + bp) * 2 * R,
+                      Eh + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mh);
         }
     }
     __syncthreads();
 
     // ---- switch (step 4) and write-out of the switch-level coefficients
-    float2* Wout = A.W + (size_t)slice * g.P * R * CT;
-    for (int it = tid; it < T * CT; it += kThreads) {
-        const int lp = it / CT, col = it % CT;
+    float2* Wout = A.W + (size_t)slice * g.P * R * CTp;
+    for (int lp = tid >> lct; lp < T; lp += kThreads >> lct) {
         const int slot = (int)brev((unsigned)lp, K);
-        const float2* xs = X + (size_t)slot * R * CT + col;
+        const float2* xs = X + (size_t)slot * R * CTp + col;
         float2 mu[R];
 #pragma unroll
-        for (int s = 0; s < R; ++s) mu[s] = xs[s * CT];
-        const float2* Sp = Ss + (size_t)lp * R * R;
+        for (int s = 0; s < R; ++s) mu[s] = xs[s * CTp];
+        const float4* Sp = reinterpret_cast<const float4*>(Ss + (size_t)lp * R * R);
         const int64_t q = ((p << K) + lp) * nBh + c0;
-        float2* wo = Wout + (size_t)q * R * CT + col;
+        float2* wo = Wout + (size_t)q * R * CTp + col;
 #pragma unroll
         for (int t = 0; t < R; ++t) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int s = 0; s < R; ++s) cfmaf(acc, Sp[t * R + s], mu[s]);
-            wo[t * CT] = acc;
+            for (int s2 = 0; s2 < R / 2; ++s2) {
+                const float4 sv = Sp[t * (R / 2) + s2];
+                cfmaf(acc, make_float2(sv.x, sv.y), mu[2 * s2]);
+                cfmaf(acc, make_float2(sv.z, sv.w), mu[2 * s2 + 1]);
+            }
+            wo[t * CTp] = acc;
         }
     }
 }
@@ -224,187 +361,170 @@ __global__ void __launch_bounds__(kThreads, 2) front_f32(FrontArgs A)
 template <int R, int NU>
 __global__ void __launch_bounds__(kThreads, 2) back_f32(BackArgs A)
 {
+    constexpr int R4 = Pad4<R>::v;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geo& g = A.g;
-    const int K = g.kG, T = 1 << K, CT = A.CT, mr = A.mr, nu = g.nv;
+    const int K = g.kG, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra;
     const int slice = blockIdx.x % A.nslice;
     const int64_t pp = blockIdx.x / A.nslice;     // x-node at level h
     const int nC = 1 << g.l1;                      // chunks c0' (= T_Omega nodes at level l1)
     const int64_t nBh = (int64_t)1 << (g.L - g.h);
-    const int XN = T * nu;                         // output points of this CTA
+    const int XN = T * NU;                         // output points of this CTA
 
-    float2* X = reinterpret_cast<float2*>(smem_raw);    // [T][R][CT]
-    float2* FGs = X + (size_t)T * R * CT;                // [K][T][2][R]
+    float2* X = reinterpret_cast<float2*>(smem_raw);    // [T][R][CTp]
+    float2* FGs = X + (size_t)T * R * CTp;               // [K][T][2][R]
     float2* EUs = FGs + (size_t)K * T * 2 * R;           // [XN]
-    float2* acc = EUs + XN;                              // [XN][mr]
-    float* MGTs = reinterpret_cast<float*>(acc + (size_t)XN * mr);  // [K][2][R][R]
-    float* MUs = MGTs + (size_t)K * 2 * R * R;                       // [nu][R]
+    float2* AKs = EUs + XN;                              // [ra][XN]
+    float2* acc = AKs + (size_t)ra * XN;                 // [XN][mr]
+    float* MGTs = reinterpret_cast<float*>(acc + (size_t)XN * mr);  // [K][2][R][R4]
+    float* MUs = MGTs + (size_t)K * 2 * R * R4;                      // [NU][R4]
 
     const int tid = threadIdx.x;
-    for (int e = tid; e < K * 2 * R * R; e += kThreads) MGTs[e] = A.MGT[e];
-    for (int e = tid; e < nu * R; e += kThreads) MUs[e] = A.MU[e];
-    for (int e = tid; e < XN * mr; e += kThreads) acc[e] = make_float2(0.f, 0.f);
-    const float2* Win = A.W + (size_t)slice * g.P * R * CT;
     const int64_t x0g = pp * XN;
+    stage_matrix(MGTs, A.MGT, K * 2 * R, R, R4, tid);
+    stage_matrix(MUs, A.MU, NU, R, R4, tid);
+    for (int e = tid; e < ra * XN / 2; e += kThreads) {
+        const int k = e / (XN / 2), x = e - k * (XN / 2);
+        cp16(AKs + (size_t)k * XN + 2 * x, A.ak + (size_t)k * g.N + x0g + 2 * x);
+    }
+    for (int e = tid; e < XN * mr; e += kThreads) acc[e] = make_float2(0.f, 0.f);
+    const float2* Win = A.W + (size_t)slice * g.P * R * CTp;
+    const int col = tid & (CTp - 1);
 
     for (int c0 = 0; c0 < nC; ++c0) {
         __syncthreads();
-        {   // coefficients of pairs (pp, c0 * T + j), j < T: one contiguous block
-            const float4* src = reinterpret_cast<const float4*>(Win + (size_t)(pp * nBh + (int64_t)c0 * T) * R * CT);
-            float4* dst = reinterpret_cast<float4*>(X);
-            const int n4 = T * R * CT / 2;
-            for (int e = tid; e < n4; e += kThreads) dst[e] = src[e];
-            if ((T * R * CT) & 1) {
-                if (tid == 0) X[T * R * CT - 1] = Win[(size_t)(pp * nBh + (int64_t)c0 * T) * R * CT + T * R * CT - 1];
-            }
+        {   // pairs (pp, c0 * T + j), j < T: one contiguous block of T*R*CTp
+            const float2* src = Win + (size_t)(pp * nBh + (int64_t)c0 * T) * R * CTp;
+            for (int e = tid; e < T * R * CTp / 2; e += kThreads) cp16(X + 2 * e, src + 2 * e);
         }
         for (int j = 1; j <= K; ++j) {
             const int l = g.h + j;
             const int64_t nBl = (int64_t)1 << (g.L - l);
             const float2* fg = A.FG + (size_t)(j - 1) * g.P * 2 * R;
-            for (int e = tid; e < T * 2 * R; e += kThreads) {
-                const int lp = e / (2 * R), w = e % (2 * R);
+            for (int e = tid; e < T * R; e += kThreads) {
+                const int lp = e / R, w = e - lp * R;
                 const int64_t ap = (pp << j) + (lp >> (K - j));
                 const int64_t bp = ((int64_t)c0 << (K - j)) + (lp & ((1 << (K - j)) - 1));
-                FGs[((size_t)(j - 1) * T + lp) * 2 * R + w] = fg[(ap * nBl + bp) * 2 * R + w];
+                cp16(FGs + ((size_t)(j - 1) * T + lp) * 2 * R + 2 * w, fg + (ap * nBl + bp) * 2 * R + 2 * w);
             }
         }
-        for (int e = tid; e < XN; e += kThreads) EUs[e] = A.EU[(size_t)c0 * g.N + x0g + e];
+        for (int e = tid; e < XN / 2; e += kThreads) cp16(EUs + 2 * e, A.EU + (size_t)c0 * g.N + x0g + 2 * e);
+        cp_commit_wait();
 
         // ---- G levels (Eq. 3), in place
         for (int j = 1; j <= K; ++j) {
             __syncthreads();
-            const int half = 1 << (K - j);
-            const float* Mg = MGTs + (size_t)(j - 1) * 2 * R * R;
+            const int kj = K - j, half = 1 << kj;
+            const float* Mg = MGTs + (size_t)(j - 1) * 2 * R * R4;
             const float2* Fg = FGs + (size_t)(j - 1) * T * 2 * R;
-            for (int it = tid; it < (T / 2) * CT; it += kThreads) {
-                const int grp = it / CT, col = it % CT;
-                const int a = grp / half, bp = grp % half;
+            for (int grp = tid >> lct; grp < T / 2; grp += kThreads >> lct) {
+                const int a = grp >> kj, bp = grp & (half - 1);
                 const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
-                float2* x0 = X + (size_t)base * R * CT + col;
-                float2* x1 = X + (size_t)(base + (1 << (j - 1))) * R * CT + col;
-                float2 nu0[R], nu1[R];
-#pragma unroll
-                for (int s = 0; s < R; ++s) {
-                    nu0[s] = x0[s * CT];
-                    nu1[s] = x1[s * CT];
-                }
-#pragma unroll
-                for (int pos = 0; pos < 2; ++pos) {
-                    // w_c = MG[pos] nu_c, for both children c
-                    float2 w0[R], w1[R];
-#pragma unroll
-                    for (int t = 0; t < R; ++t) w0[t] = w1[t] = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int s = 0; s < R; ++s) {
-                        const float2* mg = reinterpret_cast<const float2*>(Mg + (pos * R + s) * R);
-#pragma unroll
-                        for (int t2 = 0; t2 < R / 2; ++t2) {
-                            const float2 w = mg[t2];
-                            w0[2 * t2].x = fmaf(w.x, nu0[s].x, w0[2 * t2].x);
-                            w0[2 * t2].y = fmaf(w.x, nu0[s].y, w0[2 * t2].y);
-                            w0[2 * t2 + 1].x = fmaf(w.y, nu0[s].x, w0[2 * t2 + 1].x);
-                            w0[2 * t2 + 1].y = fmaf(w.y, nu0[s].y, w0[2 * t2 + 1].y);
-                            w1[2 * t2].x = fmaf(w.x, nu1[s].x, w1[2 * t2].x);
-                            w1[2 * t2].y = fmaf(w.x, nu1[s].y, w1[2 * t2].y);
-                            w1[2 * t2 + 1].x = fmaf(w.y, nu1[s].x, w1[2 * t2 + 1].x);
-                            w1[2 * t2 + 1].y = fmaf(w.y, nu1[s].y, w1[2 * t2 + 1].y);
-                        }
-                    }
-                    const float2* Fp = Fg + (size_t)((2 * a + pos) * half + bp) * 2 * R;  // [c][t]
-                    float2* xo = pos ? x1 : x0;
-#pragma unroll
-                    for (int t = 0; t < R; ++t) {
-                        float2 o = cmulf(Fp[t], w0[t]);
-                        cfmaf(o, Fp[R + t], w1[t]);
-                        xo[t * CT] = o;
-                    }
-                }
+                float2* x0 = X + (size_t)base * R * CTp + col;
+                float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
+                g_item<R>(x0, x1, CTp, Fg + (size_t)((2 * a) * half + bp) * 2 * R,
+                          Fg + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mg);
             }
         }
         __syncthreads();
 
         // ---- U (Eq. bf3) contribution of T_Omega node c0 to this CTA's points
-        for (int it = tid; it < T * mr; it += kThreads) {
-            const int lp = it / mr, c = it % mr;
-            const int slot = (int)brev((unsigned)lp, K);
-            const float2* xs = X + (size_t)slot * R * CT + c;
-            float2 res[NU];
+        {
+            const int c = tid & (mr - 1);
+            for (int lp = tid >> lmr; lp < T; lp += kThreads >> lmr) {
+                const int slot = (int)brev((unsigned)lp, K);
+                const float2* xs = X + (size_t)slot * R * CTp + c;
+                float2* ap = acc + (size_t)lp * NU * mr + c;
+                for (int k = 0; k < ra; ++k) {
+                    float2 v[R];
 #pragma unroll
-            for (int i = 0; i < NU; ++i) res[i] = make_float2(0.f, 0.f);
-            for (int k = 0; k < g.ra; ++k) {
-                float2 v[R];
-#pragma unroll
-                for (int s = 0; s < R; ++s) v[s] = xs[s * CT + k * mr];
-#pragma unroll
-                for (int i = 0; i < NU; ++i) {
-                    if (i < nu) {
+                    for (int s = 0; s < R; ++s) v[s] = xs[s * CTp + k * mr];
+                    const float2* ak = AKs + (size_t)k * XN + lp * NU;
+#pragma unroll 4
+                    for (int i = 0; i < NU; ++i) {
                         float2 w = make_float2(0.f, 0.f);
-                        const float2* mu = reinterpret_cast<const float2*>(MUs + i * R);
+                        const float4* mu = reinterpret_cast<const float4*>(MUs + i * R4);
 #pragma unroll
-                        for (int s2 = 0; s2 < R / 2; ++s2) {
-                            const float2 m2 = mu[s2];
-                            w.x = fmaf(m2.x, v[2 * s2].x, fmaf(m2.y, v[2 * s2 + 1].x, w.x));
-                            w.y = fmaf(m2.x, v[2 * s2].y, fmaf(m2.y, v[2 * s2 + 1].y, w.y));
+                        for (int s4 = 0; s4 < R4 / 4; ++s4) {
+                            const float4 m4 = mu[s4];
+                            const float mm[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int s = 4 * s4 + q;
+                                if (s < R) {
+                                    w.x = fmaf(mm[q], v[s].x, w.x);
+                                    w.y = fmaf(mm[q], v[s].y, w.y);
+                                }
+                            }
                         }
-                        const int64_t xg = x0g + lp * nu + i;
-                        cfmaf(res[i], cmulf(__ldg(A.ak + (size_t)k * g.N + xg), EUs[lp * nu + i]), w);
+                        float2 o = ap[i * mr];
+                        cfmaf(o, cmulf(ak[i], EUs[lp * NU + i]), w);
+                        ap[i * mr] = o;
                     }
                 }
             }
-#pragma unroll
-            for (int i = 0; i < NU; ++i)
-                if (i < nu) {
-                    float2* ap = acc + (size_t)(lp * nu + i) * mr + c;
-                    ap->x += res[i].x;
-                    ap->y += res[i].y;
-                }
         }
     }
     __syncthreads();
     // ---- write G
-    for (int it = tid; it < XN * mr; it += kThreads) {
-        const int x = it / mr, c = it % mr;
+    {
+        const int c = tid & (mr - 1);
         const int64_t cg = (int64_t)slice * mr + c;
-        if (cg >= A.m) continue;
-        float2* gp = A.G + (x0g + x) * A.m + cg;
-        float2 v = acc[it];
-        if (A.beta) {
-            float2 o = *gp;
-            v.x += o.x;
-            v.y += o.y;
+        if (cg < A.m) {
+            for (int x = tid >> lmr; x < XN; x += kThreads >> lmr) {
+                float2* gp = A.G + (x0g + x) * A.m + cg;
+                float2 v = acc[x * mr + c];
+                if (A.beta) {
+                    const float2 o = *gp;
+                    v.x += o.x;
+                    v.y += o.y;
+                }
+                *gp = v;
+            }
         }
-        *gp = v;
     }
 }
 
-size_t front_smem(const Geo& g, int R, int CT)
+int ilog2(int v)
 {
-    const int T = 1 << g.kH;
-    return sizeof(float2) * ((size_t)T * R * CT + (size_t)g.kH * T * 2 * R + (size_t)T * R * R + (size_t)T * g.nv) +
-           sizeof(float) * ((size_t)g.nv * R + (size_t)g.kH * 2 * R * R);
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
 }
 
-size_t back_smem(const Geo& g, int R, int CT, int mr)
+size_t front_smem(const Geo& g, int R, int NV, int CTp, int mr)
 {
-    const int T = 1 << g.kG;
-    const size_t XN = (size_t)T * g.nv;
-    return sizeof(float2) * ((size_t)T * R * CT + (size_t)g.kG * T * 2 * R + XN + XN * mr) +
-           sizeof(float) * ((size_t)g.kG * 2 * R * R + (size_t)g.nv * R);
+    const size_t T = (size_t)1 << g.kH, R4 = (R + 3) & ~3;
+    return sizeof(float2) * (T * R * CTp + T * NV * mr + (size_t)g.ra * T * NV + (size_t)g.kH * T * 2 * R +
+                             T * R * R + T * NV) +
+           sizeof(float) * ((size_t)NV * R4 + (size_t)g.kH * 2 * R * R4);
 }
 
-template <int R, int NU>
+size_t back_smem(const Geo& g, int R, int NU, int CTp, int mr)
+{
+    const size_t T = (size_t)1 << g.kG, R4 = (R + 3) & ~3;
+    const size_t XN = T * NU;
+    return sizeof(float2) * (T * R * CTp + (size_t)g.kG * T * 2 * R + XN + (size_t)g.ra * XN + XN * mr) +
+           sizeof(float) * ((size_t)g.kG * 2 * R * R4 + (size_t)NU * R4);
+}
+
+template <int R>
 cudaError_t launch_r(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws,
                      cudaStream_t st)
 {
+    constexpr int NV = (R < 8) ? 8 : (R < 16 ? 16 : 32);
     const Geo& g = B.g;
+    if (g.nv != NV) return cudaErrorNotSupported;
     const FusedCfg cfg = fused_f32_config(g, m);
+    const int CTp = 1 << ilog2(g.ra * cfg.mr);
     FrontArgs fa;
     fa.g = g;
     fa.F = F;
     fa.m = m;
     fa.mr = cfg.mr;
-    fa.CT = g.ra * cfg.mr;
+    fa.lmr = ilog2(cfg.mr);
+    fa.CTp = CTp;
+    fa.lct = ilog2(CTp);
     fa.nslice = cfg.nslice;
     fa.bk = B.f32.b;
     fa.MvT = B.f32.Mv;
@@ -413,25 +533,26 @@ cudaError_t launch_r(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     fa.EH = B.f32.EH;
     fa.S = B.f32.S;
     fa.W = ws;
-    const size_t sf = front_smem(g, R, fa.CT);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(front_f32<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(back_f32<R, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    const size_t sf = front_smem(g, R, NV, CTp, cfg.mr);
+    const size_t sb = back_smem(g, R, NV, CTp, cfg.mr);
+    cudaError_t e = cudaFuncSetAttribute(front_f32<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(back_f32<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    if (e != cudaSuccess) return e;
     const int64_t ntile = ((int64_t)1 << g.l1) * ((int64_t)1 << (g.L - g.h));
     {
         ProfScope ps("front_f32", st);
-        front_f32<R><<<(unsigned)(ntile * cfg.nslice), kThreads, sf, st>>>(fa);
+        front_f32<R, NV><<<(unsigned)(ntile * cfg.nslice), kThreads, sf, st>>>(fa);
     }
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     BackArgs ba;
     ba.g = g;
     ba.m = m;
     ba.mr = cfg.mr;
-    ba.CT = fa.CT;
+    ba.lmr = fa.lmr;
+    ba.CTp = CTp;
+    ba.lct = fa.lct;
     ba.nslice = cfg.nslice;
     ba.W = ws;
     ba.MGT = B.f32.MG;
@@ -441,11 +562,10 @@ cudaError_t launch_r(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     ba.ak = B.f32.a;
     ba.G = G;
     ba.beta = beta;
-    const size_t sb = back_smem(g, R, fa.CT, cfg.mr);
     const int64_t nback = ((int64_t)1 << g.h) * cfg.nslice;
     {
         ProfScope ps("back_f32", st);
-        back_f32<R, NU><<<(unsigned)nback, kThreads, sb, st>>>(ba);
+        back_f32<R, NV><<<(unsigned)nback, kThreads, sb, st>>>(ba);
     }
     return cudaGetLastError();
 }
@@ -458,17 +578,18 @@ FusedCfg fused_f32_config(const Geo& g, int64_t m)
 {
     const int Tmax = 1 << (g.kG > g.kH ? g.kG : g.kH);
     const int ra = g.ra > 0 ? g.ra : 1;
-    // about 256 (group, column) items per level, and a tile of at most 48 KB
-    int mr = 512 / (Tmax * ra);
-    const int cap = (int)(48 * 1024 / ((size_t)Tmax * g.r * ra * sizeof(float2)));
-    if (mr > cap) mr = cap;
-    if (mr > 64) mr = 64;
-    if (mr < 1) mr = 1;
-    if ((int64_t)mr > m) mr = (int)m;
-    // keep mr a power of two so that CT = ra * mr packs warps evenly
-    int p2 = 1;
-    while (p2 * 2 <= mr) p2 *= 2;
-    mr = p2;
+    const int NV = g.nv;
+    // largest power-of-two mr with at most 512 (group, column) items per level
+    // and a tile plus staged F rows within 80 KB of shared memory
+    int mr = 64;
+    while (mr > 1) {
+        const int CTp = 1 << ilog2(ra * mr);
+        const size_t tile = (size_t)Tmax * g.r * CTp * sizeof(float2);
+        const size_t fs = (size_t)Tmax * NV * mr * sizeof(float2);
+        if ((Tmax / 2) * CTp <= 512 && tile + fs <= 80 * 1024) break;
+        mr >>= 1;
+    }
+    while (mr > 1 && (int64_t)(mr / 2) >= m) mr >>= 1;
     FusedCfg c;
     c.mr = mr;
     c.nslice = (int)((m + mr - 1) / mr);
@@ -478,7 +599,8 @@ FusedCfg fused_f32_config(const Geo& g, int64_t m)
 size_t fused_f32_ws_bytes(const Geo& g, int64_t m)
 {
     const FusedCfg c = fused_f32_config(g, m);
-    return (size_t)c.nslice * g.P * g.r * g.ra * c.mr * sizeof(float2);
+    const int CTp = 1 << ilog2((g.ra > 0 ? g.ra : 1) * c.mr);
+    return (size_t)c.nslice * g.P * g.r * CTp * sizeof(float2);
 }
 
 cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws,
@@ -488,14 +610,13 @@ cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, floa
         if (!beta) return cudaMemsetAsync(G, 0, (size_t)B.g.N * m * sizeof(float2), st);
         return cudaSuccess;
     }
-    if (B.g.nv > 2 * B.g.r) return cudaErrorNotSupported;
     switch (B.g.r) {
-    case 6: return launch_r<6, 12>(B, F, m, G, beta, ws, st);
-    case 8: return launch_r<8, 16>(B, F, m, G, beta, ws, st);
-    case 10: return launch_r<10, 20>(B, F, m, G, beta, ws, st);
-    case 12: return launch_r<12, 24>(B, F, m, G, beta, ws, st);
-    case 14: return launch_r<14, 28>(B, F, m, G, beta, ws, st);
-    case 16: return launch_r<16, 32>(B, F, m, G, beta, ws, st);
+    case 6: return launch_r<6>(B, F, m, G, beta, ws, st);
+    case 8: return launch_r<8>(B, F, m, G, beta, ws, st);
+    case 10: return launch_r<10>(B, F, m, G, beta, ws, st);
+    case 12: return launch_r<12>(B, F, m, G, beta, ws, st);
+    case 14: return launch_r<14>(B, F, m, G, beta, ws, st);
+    case 16: return launch_r<16>(B, F, m, G, beta, ws, st);
     default: return cudaErrorNotSupported;
     }
 }
