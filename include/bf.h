@@ -155,6 +155,22 @@ bf_status bf_reserve(bf_plan* plan, bf_precision prec, int64_t m_max);
 bf_status bf_apply(bf_plan* plan, bf_precision prec, const void* F, int64_t m, void* G,
                    void* stream);
 
+/* Allocation-free form of bf_apply for BF_PREC_F32 (the paper has no
+ * counterpart: this is an integration aid).  For callers that may not
+ * allocate device memory when they apply -- a server or host application that
+ * owns all device memory through its own pool, or a latency-critical path
+ * that must not enter the CUDA allocator -- it uses a fixed 32 MiB scratch
+ * array compiled into the library instead of the plan's workspace; every GPU
+ * that loads the library holds that array until exit.  Requirements: the
+ * plan is uploaded (bf_upload); the switch-level workspace for this N and m
+ * fits in 32 MiB (else BF_ERR_ARG, message gives the size); bf_profile timing
+ * is off (else BF_ERR_STATE).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it: make that
+ * first call before any stream capture.  Calls share the array, so calls
+ * that overlap on the GPU race; nothing in it needs clearing between calls.
+ * F, G, m, stream as for bf_apply (c64).  Allocates nothing. */
+bf_status bf_apply_f32_noalloc(bf_plan* plan, const void* F, int64_t m, void* G, void* stream);
+
 /* Same as bf_apply but F and G are HOST buffers: copies F to the device,
  * applies, copies G back, and synchronises `stream` before returning. */
 bf_status bf_apply_host(bf_plan* plan, bf_precision prec, const void* F_host, int64_t m,

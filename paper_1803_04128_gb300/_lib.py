@@ -54,6 +54,7 @@ _SIGS = {
     "bf_reserve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     "bf_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, _P, _P]),
     "bf_apply_host": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, _P, _P]),
+    "bf_apply_f32_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
     "bf_sync_status": (ctypes.c_int, [_P, _P]),
     "bf_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),
     "bf_plan_view": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int,

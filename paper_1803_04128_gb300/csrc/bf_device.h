@@ -83,6 +83,7 @@ bool fused_f32_supported(int r);
 // per-launch event timing (bf_profile_*); no-ops unless profiling is on
 void prof_start(const char* name, cudaStream_t st, void** tok);
 void prof_stop(void* tok, cudaStream_t st);
+bool prof_active();
 struct ProfScope {
     void* tok;
     cudaStream_t st;

@@ -32,6 +32,12 @@ void prof_start(const char* name, cudaStream_t st, void** tok)
     *tok = (void*)(intptr_t)g_recs.size();
 }
 
+bool prof_active()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_on;
+}
+
 void prof_stop(void* tok, cudaStream_t st)
 {
     if (!tok) return;
