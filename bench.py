@@ -35,6 +35,9 @@ WORKLOADS = {
                       "N=65536, m=64 complex Gaussian RHS, complex FP32 apply, eps=1e-6"),
     "fio1": dict(N=1024, m=1, phase=1, amp=0, eps=1e-6, prec="f64", split=1,
                  desc="1D FIO, alpha=1, N=1024, one RHS, FP64 apply, eps=1e-6"),
+    "fio4": dict(N=0, m=0, phase=1, amp=1, eps=1e-6, prec="f32", split=1, n_ops=32,
+                 desc="32 operators of the fio2 kernel, N = 2^floor(U(12,19)), m ~ U{1..128} (seed 0), one "
+                      "persistent batched launch replayed from a CUDA graph, autotuned column slices, complex FP32"),
     "fio3": dict(N=262144, m=256, phase=2, amp=1, eps=1e-6, prec="f32", split=2,
                  desc="piecewise FIO (jump at x=1/2), N=262144 as four N/2 sub-BFs, m=256, complex FP32 apply"),
 }
@@ -210,6 +213,132 @@ def run_reference(args, w, rank, world):
     return 0
 
 
+def run_batched(args, w, rank, world, local):
+    """32 uneven operators applied in one persistent launch replayed from a CUDA graph."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1803_04128_gb300 import _lib as L
+    from paper_1803_04128_gb300 import api, inputs
+
+    shapes = inputs.uneven_batch(w["n_ops"], 12, 18, 1, 128, seed=0)
+    t0 = time.perf_counter()
+    plans = {}
+    for N, _ in shapes:
+        if N not in plans:
+            plans[N] = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], device=local)
+    t_factor = time.perf_counter() - t0
+    tune_path = os.path.join(tempfile.gettempdir(), "bf_autotune_%d.txt" % os.getpid())
+    t0 = time.perf_counter()
+    for N, m in shapes:
+        api.autotune(plans[N], m, tune_path)
+    t_tune = time.perf_counter() - t0
+    ops, Fh = [], []
+    for k, (N, m) in enumerate(shapes):
+        f = inputs.complex_gaussian(N, m, seed=1000 * rank + k)
+        Fh.append(f)
+        F = torch.from_numpy(f).to(torch.complex64).cuda()
+        ops.append((plans[N], F, torch.empty_like(F)))
+    batch = api.Batch(ops)
+    stream = torch.cuda.Stream()
+    batch.capture(stream)
+    units = sum(N * m for N, m in shapes)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            batch.replay(stream)
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        with api.KernelTimer() as kt:
+            with torch.cuda.stream(stream):
+                for i in range(args.steps):
+                    flush.zero_()
+                    ev[i][0].record(stream)
+                    batch.replay(stream)
+                    ev[i][1].record(stream)
+            stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    assert batch.status(stream) == 0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * units * args.steps / (ms_max * 1e-3) / 1e9
+    # the same 32 applies issued one operator at a time (2 launches each), for comparison
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(args.steps):
+        for plan, F, G in ops:
+            plan.apply(F, G, api.F32)
+    s1.record()
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1) / args.steps
+    peaks, peak_src = load_peaks()
+    flops = 0
+    bytes_apply = 0
+    for N, m in shapes:
+        info = plans[N].info()
+        fr, bk, by = algorithmic(info, m, N, 1)
+        flops += fr + bk
+        bytes_apply += by
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    nb, tb = kt.result.get("batch_f32", (0, 0.0))
+    roof = None
+    if nb:
+        achieved = flops / (tb / nb * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "batch_f32", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": ncu_traffic("batch_f32", args.workload),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s)" % (peaks.get("sm_max_mhz", 2070.0), peak_src),
+                "kernel_ms": {k: v[1] / v[0] for k, v in kt.result.items()}}
+    # end to end: pinned host F in, graph replay, G out
+    Fp = [torch.from_numpy(f).to(torch.complex64).pin_memory() for f in Fh]
+    Gp = [torch.empty_like(x).pin_memory() for x in Fp]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            for (plan, F, G), fp in zip(ops, Fp):
+                F.copy_(fp, non_blocking=True)
+            batch.replay(stream)
+            for (plan, F, G), gp in zip(ops, Gp):
+                gp.copy_(G, non_blocking=True)
+            stream.synchronize()
+    t_e2e = time.perf_counter() - t0
+    nbytes = sum(x.numel() * x.element_size() for x in Fp)
+    if rank == 0:
+        cfg = {"workload": w["desc"], "n_ops": len(shapes), "shapes": shapes, "units_per_step": units,
+               "r": plans[shapes[0][0]].info()["r"], "eps": w["eps"], "l2": "flushed (512 MB write) between timed steps",
+               "t_factor_s": round(t_factor, 2), "t_autotune_s": round(t_tune, 2),
+               "sequential_single_op_ms_per_step": seq_ms, "batched_ms_per_step": ms_max / args.steps,
+               "hbm_frac_of_measured": bytes_apply / (ms_max / args.steps * 1e-3) / (peaks["hbm_gbs"] * 1e9),
+               "algorithmic_flops_per_step": flops, "algorithmic_bytes_per_step": bytes_apply,
+               "parallelism": "replicas" if world > 1 else "single GPU"}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded complex Gaussian F; analytic kernel)", "config": cfg, "roofline": roof,
+                "cpu_baseline": None,
+                "e2e": {"value": world * units * args.steps / t_e2e / 1e9, "unit": UNIT,
+                        "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+                "gpu_launches": sum(n for n, _ in kt.result.values()), "clocks": clk.summary()}
+        print(json.dumps(line))
+    batch.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -243,6 +372,8 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "fio4":
+        return run_batched(args, w, rank, world, local)
 
     def barrier():
         if world > 1:

@@ -1,0 +1,80 @@
+/*
+ * bf_batch.h -- batched uneven apply, CUDA-graph capture and the column-slice
+ * autotuner of the butterfly-factorisation library (see bf.h for conventions).
+ *
+ * A batch applies many operators g_i = K_i f_i (each a plan of bf.h, of its own
+ * N_i, with its own m_i right-hand sides) in ONE persistent launch: every CTA
+ * takes work items -- the front tiles (V, H levels, switch) and back tiles (G
+ * levels, U) of all operators -- from an atomic counter; a back tile of
+ * operator i waits (bounded) until all front tiles of i are finished.  Each
+ * operator computes exactly what bf_apply(plan_i, BF_PREC_F32, ...) computes,
+ * bit for bit.  The paper applies one operator to one vector at a time
+ * (Sec. 5); batching is this library's addition, resting on the footnote of
+ * Sec. 1 that the precomputed factorisation is reused across many f.
+ */
+#ifndef BF_BATCH_H
+#define BF_BATCH_H
+
+#include "bf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bf_batch bf_batch;
+
+/* One operator of a batch: G = K F with K = plan (FP32 fused apply).
+ * F, G: device, [N][m] c64, caller-owned, must stay valid for the batch's
+ * lifetime (launches and graph replays read/write them). */
+typedef struct {
+    bf_plan* plan;
+    const void* F;
+    void* G;
+    int64_t m;
+} bf_batch_item;
+
+/* Build a batch (uploads plans, allocates one workspace per item and the work
+ * list).  All plans must share r and device and be unsplit (split == 1).
+ * Errors: BF_ERR_ARG, BF_ERR_UNSUPPORTED, BF_ERR_NOMEM, BF_ERR_CUDA. */
+bf_status bf_batch_create(const bf_batch_item* items, int n, bf_batch** out);
+
+/* Enqueue the batch on `stream`: a reset of the work counters, then one
+ * persistent launch (grid = resident CTAs per SM x SMs). */
+bf_status bf_batch_run(bf_batch* batch, void* stream);
+
+/* Capture bf_batch_run into a CUDA graph on `stream` (a created, non-default
+ * stream) and instantiate it; bf_batch_replay then launches the graph. */
+bf_status bf_batch_capture_graph(bf_batch* batch, void* stream);
+bf_status bf_batch_replay(bf_batch* batch, void* stream);
+
+/* Synchronise `stream` and report device-side failures of earlier runs:
+ * BF_ERR_TIMEOUT if a back tile stopped waiting for its front tiles. */
+bf_status bf_batch_status(bf_batch* batch, void* stream);
+
+/* Total work items, persistent grid size, workspace bytes, shared memory per CTA. */
+bf_status bf_batch_get_info(const bf_batch* batch, int64_t* work_items, int* grid, int64_t* ws_bytes,
+                            int64_t* smem);
+
+/* Polls a back tile makes before giving up (default 2^24, about 2-4 s). */
+bf_status bf_batch_set_spin_limit(bf_batch* batch, long long polls);
+
+/* Test hook for the failure path: with on != 0, back tiles wait for one more
+ * front completion than exists, so every wait runs out after the spin limit,
+ * the tile is skipped and bf_batch_status reports BF_ERR_TIMEOUT.  G is then
+ * not written.  Nothing faults or hangs: each wait is bounded. */
+bf_status bf_batch_debug_hold(bf_batch* batch, int on);
+
+void bf_batch_destroy(bf_batch* batch); /* NULL-safe */
+
+/* Choose the column-slice width (right-hand sides per CTA, a power of two) of
+ * the FP32 fused apply for this plan and m by timing the candidates on the
+ * GPU, and remember it in the plan (bf_apply and bf_batch_create use it).
+ * cache_path (nullable): a text cache; an entry for this (N, r, r_alpha,
+ * split, m) is used without timing, and new results are appended.
+ * *mr_out (nullable) receives the choice.  Allocates temporaries. */
+bf_status bf_autotune(bf_plan* plan, int64_t m, const char* cache_path, int* mr_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BF_BATCH_H */

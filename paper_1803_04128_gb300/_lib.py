@@ -36,6 +36,10 @@ class Options(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("keep_host", ctypes.c_int), ("device", ctypes.c_int)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("F", ctypes.c_void_p), ("G", ctypes.c_void_p), ("m", ctypes.c_int64)]
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("r", ctypes.c_int), ("n0", ctypes.c_int), ("L", ctypes.c_int),
                 ("h", ctypes.c_int), ("l1", ctypes.c_int), ("r_alpha", ctypes.c_int), ("split", ctypes.c_int),
@@ -71,6 +75,17 @@ _SIGS = {
     "bf_profile_get": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_double)]),
     "bf_version": (ctypes.c_char_p, []),
+    "bf_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_P)]),
+    "bf_batch_run": (ctypes.c_int, [_P, _P]),
+    "bf_batch_capture_graph": (ctypes.c_int, [_P, _P]),
+    "bf_batch_replay": (ctypes.c_int, [_P, _P]),
+    "bf_batch_status": (ctypes.c_int, [_P, _P]),
+    "bf_batch_get_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "bf_batch_set_spin_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
+    "bf_batch_debug_hold": (ctypes.c_int, [_P, ctypes.c_int]),
+    "bf_batch_destroy": (None, [_P]),
+    "bf_autotune": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lock = threading.Lock()

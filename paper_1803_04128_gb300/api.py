@@ -164,6 +164,66 @@ class Plan:
         return self._lib.bf_sync_status(self._h, _stream_ptr(stream))
 
 
+def autotune(plan, m, cache_path=None):
+    """Time the column-slice candidates of the FP32 apply for (plan, m); returns mr."""
+    mr = ctypes.c_int()
+    L.check(L.lib().bf_autotune(plan._h, int(m), None if cache_path is None else str(cache_path).encode(),
+                                ctypes.byref(mr)), "bf_autotune")
+    return mr.value
+
+
+class Batch:
+    """Many operators of different N and m applied in one persistent launch
+    (bf_batch_*).  ``items``: list of (plan, F, G) with F, G contiguous CUDA
+    complex64 tensors of shape (N, m); they must outlive the batch."""
+
+    def __init__(self, items):
+        self._lib = L.lib()
+        self._keep = list(items)
+        arr = (L.BatchItem * len(items))()
+        for i, (plan, F, G) in enumerate(items):
+            m = 1 if F.dim() == 1 else F.shape[1]
+            arr[i].plan, arr[i].F, arr[i].G, arr[i].m = plan._h.value, F.data_ptr(), G.data_ptr(), m
+        self._h = ctypes.c_void_p()
+        L.check(self._lib.bf_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(items), ctypes.byref(self._h)),
+                "bf_batch_create")
+
+    def run(self, stream=None):
+        L.check(self._lib.bf_batch_run(self._h, _stream_ptr(stream)), "bf_batch_run")
+
+    def capture(self, stream):
+        L.check(self._lib.bf_batch_capture_graph(self._h, _stream_ptr(stream)), "bf_batch_capture_graph")
+
+    def replay(self, stream=None):
+        L.check(self._lib.bf_batch_replay(self._h, _stream_ptr(stream)), "bf_batch_replay")
+
+    def status(self, stream=None):
+        return self._lib.bf_batch_status(self._h, _stream_ptr(stream))
+
+    def info(self):
+        w, g, ws, sm = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        L.check(self._lib.bf_batch_get_info(self._h, ctypes.byref(w), ctypes.byref(g), ctypes.byref(ws),
+                                            ctypes.byref(sm)), "bf_batch_get_info")
+        return {"work_items": w.value, "grid": g.value, "ws_bytes": ws.value, "smem": sm.value}
+
+    def set_spin_limit(self, polls):
+        L.check(self._lib.bf_batch_set_spin_limit(self._h, int(polls)), "bf_batch_set_spin_limit")
+
+    def debug_hold(self, on=True):
+        L.check(self._lib.bf_batch_debug_hold(self._h, int(on)), "bf_batch_debug_hold")
+
+    def close(self):
+        if self._h:
+            self._lib.bf_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class KernelTimer:
     """Context manager: CUDA-event times of every library kernel launched inside
     (bf_profile_begin/end).  ``.result`` maps kernel name -> (launches, total_ms)."""

@@ -1,0 +1,405 @@
+// Batched uneven apply (many operators of different N and m in one persistent
+// launch, optionally captured in a CUDA graph) and the column-slice autotuner.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bf_batch.h"
+#include "bf_fused.h"
+
+using namespace bfi;
+
+struct bf_batch {
+    int device = 0;
+    int r = 0;
+    BatchLaunch bl;
+    std::vector<BatchItem> items;
+    void* dmem = nullptr;  // items, offsets, counter/done, err
+    size_t dmem_bytes = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    unsigned char* reset_ptr = nullptr;  // counter + done, cleared before each launch
+    size_t reset_bytes = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+};
+
+namespace {
+
+bf_status cuda_fail(const char* where, cudaError_t e)
+{
+    set_error("%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BF_ERR_NOMEM : BF_ERR_CUDA;
+}
+
+void free_batch(bf_batch* b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->dmem) cudaFree(b->dmem);
+    if (b->ws) cudaFree(b->ws);
+    delete b;
+}
+
+bf_status enqueue(bf_batch* b, cudaStream_t st)
+{
+    if (b->bl.grid < 1) {
+        set_error("bf_batch: no persistent grid configured");
+        return BF_ERR_STATE;
+    }
+    cudaError_t e = cudaMemsetAsync(b->reset_ptr, 0, b->reset_bytes, st);
+    if (e != cudaSuccess) return cuda_fail("bf_batch: reset", e);
+    e = batch_launch_f32(b->r, b->bl, st, false, nullptr);
+    if (e != cudaSuccess) return cuda_fail("bf_batch: launch", e);
+    return BF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
+{
+    if (!in || n < 1 || !out) {
+        set_error("bf_batch_create: need n >= 1 items and an output pointer");
+        return BF_ERR_ARG;
+    }
+    *out = nullptr;
+    bf_batch* b = new (std::nothrow) bf_batch();
+    if (!b) {
+        set_error("bf_batch_create: out of host memory");
+        return BF_ERR_NOMEM;
+    }
+    // validate and upload
+    for (int i = 0; i < n; ++i) {
+        const bf_batch_item& it = in[i];
+        if (!it.plan || !it.F || !it.G || it.m < 1 || it.F == it.G) {
+            free_batch(b);
+            set_error("bf_batch_create: item %d: NULL plan/buffer, m < 1 or G aliasing F", i);
+            return BF_ERR_ARG;
+        }
+        bf_status st = bf_upload(it.plan);
+        if (st != BF_OK) {
+            free_batch(b);
+            return st;
+        }
+        if (it.plan->blocks.size() != 1) {
+            free_batch(b);
+            set_error("bf_batch_create: item %d: split plans are not batched (apply them with bf_apply)", i);
+            return BF_ERR_UNSUPPORTED;
+        }
+        const int r = it.plan->r;
+        if (i == 0) {
+            b->r = r;
+            b->device = it.plan->dev->device;
+        } else if (r != b->r || it.plan->dev->device != b->device) {
+            free_batch(b);
+            set_error("bf_batch_create: item %d: all items must share r and device (got r=%d vs %d)", i, r, b->r);
+            return BF_ERR_UNSUPPORTED;
+        }
+        if (it.plan->dev->blocks[0].g.ra < 1) {
+            free_batch(b);
+            set_error("bf_batch_create: item %d: zero amplitude", i);
+            return BF_ERR_UNSUPPORTED;
+        }
+    }
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail("bf_batch_create: cudaSetDevice", e);
+    }
+    // workspaces (one per item, packed) and argument blocks
+    std::vector<size_t> ws_off((size_t)n);
+    size_t ws_total = 0;
+    for (int i = 0; i < n; ++i) {
+        const DevBlock& B = in[i].plan->dev->blocks[0];
+        ws_off[(size_t)i] = ws_total;
+        ws_total += (fused_f32_ws_bytes(B.g, in[i].m, in[i].plan->mr_hint(in[i].m)) + 255) & ~(size_t)255;
+    }
+    if ((e = cudaMalloc(&b->ws, std::max<size_t>(ws_total, 256))) != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail("bf_batch_create: workspace", e);
+    }
+    b->ws_bytes = ws_total;
+    b->items.resize((size_t)n);
+    std::vector<int64_t> foff((size_t)n), boff((size_t)n);
+    int64_t tf = 0, tb = 0;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        const DevBlock& B = in[i].plan->dev->blocks[0];
+        BatchItem& bi = b->items[(size_t)i];
+        size_t sf, sb;
+        if (!fused_make_args(B, (const float2*)in[i].F, in[i].m, (float2*)in[i].G, 0,
+                             (float2*)((unsigned char*)b->ws + ws_off[(size_t)i]), in[i].plan->mr_hint(in[i].m),
+                             &bi.fa, &bi.ba, &sf, &sb, &bi.nfront, &bi.nback)) {
+            free_batch(b);
+            set_error("bf_batch_create: item %d: no fused FP32 kernels for r=%d", i, B.g.r);
+            return BF_ERR_UNSUPPORTED;
+        }
+        smem = std::max(smem, std::max(sf, sb));
+        foff[(size_t)i] = tf;
+        boff[(size_t)i] = tb;
+        tf += bi.nfront;
+        tb += bi.nback;
+    }
+    if (smem > 227 * 1024) {
+        free_batch(b);
+        set_error("bf_batch_create: a tile needs %zu bytes of shared memory", smem);
+        return BF_ERR_UNSUPPORTED;
+    }
+    // device copies: items | front_off | back_off | counter | done[n] | err
+    const size_t s_items = ((size_t)n * sizeof(BatchItem) + 255) & ~(size_t)255;
+    const size_t s_off = ((size_t)n * sizeof(int64_t) + 255) & ~(size_t)255;
+    const size_t s_reset = ((sizeof(unsigned long long) + (size_t)n * sizeof(int)) + 255) & ~(size_t)255;
+    b->dmem_bytes = s_items + 2 * s_off + s_reset + 256;
+    if ((e = cudaMalloc(&b->dmem, b->dmem_bytes)) != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail("bf_batch_create: descriptors", e);
+    }
+    unsigned char* base = (unsigned char*)b->dmem;
+    std::vector<unsigned char> host(b->dmem_bytes, 0);
+    std::memcpy(host.data(), b->items.data(), (size_t)n * sizeof(BatchItem));
+    std::memcpy(host.data() + s_items, foff.data(), (size_t)n * sizeof(int64_t));
+    std::memcpy(host.data() + s_items + s_off, boff.data(), (size_t)n * sizeof(int64_t));
+    if ((e = cudaMemcpy(base, host.data(), b->dmem_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail("bf_batch_create: upload", e);
+    }
+    b->bl.items = (const BatchItem*)base;
+    b->bl.nitems = n;
+    b->bl.front_off = (const int64_t*)(base + s_items);
+    b->bl.back_off = (const int64_t*)(base + s_items + s_off);
+    b->reset_ptr = base + s_items + 2 * s_off;
+    b->reset_bytes = s_reset;
+    b->bl.counter = (unsigned long long*)b->reset_ptr;
+    b->bl.done = (int*)(b->reset_ptr + sizeof(unsigned long long));
+    b->bl.err = (int*)(b->reset_ptr + s_reset);
+    b->bl.total_front = tf;
+    b->bl.total = tf + tb;
+    b->bl.smem = smem;
+    e = batch_launch_f32(b->r, b->bl, nullptr, true, nullptr);
+    if (e == cudaSuccess) e = batch_launch_f32(b->r, b->bl, nullptr, false, &b->bl.grid);
+    if (e != cudaSuccess || b->bl.grid < 1) {
+        free_batch(b);
+        return cuda_fail("bf_batch_create: occupancy", e == cudaSuccess ? cudaErrorInvalidConfiguration : e);
+    }
+    *out = b;
+    return BF_OK;
+}
+
+bf_status bf_batch_run(bf_batch* b, void* stream)
+{
+    if (!b) {
+        set_error("bf_batch_run: NULL batch");
+        return BF_ERR_ARG;
+    }
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return cuda_fail("bf_batch_run: cudaSetDevice", e);
+    return enqueue(b, (cudaStream_t)stream);
+}
+
+bf_status bf_batch_capture_graph(bf_batch* b, void* stream)
+{
+    if (!b || !stream) {
+        set_error("bf_batch_capture_graph: NULL batch or default stream (capture needs a created stream)");
+        return BF_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return cuda_fail("bf_batch_capture_graph: cudaSetDevice", e);
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail("bf_batch_capture_graph: begin", e);
+    bf_status s = enqueue(b, st);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    if (s != BF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail("bf_batch_capture_graph: end", e);
+    b->graph = g;
+    if ((e = cudaGraphInstantiate(&b->exec, g, 0)) != cudaSuccess) return cuda_fail("bf_batch_capture_graph: instantiate", e);
+    return BF_OK;
+}
+
+bf_status bf_batch_replay(bf_batch* b, void* stream)
+{
+    if (!b || !b->exec) {
+        set_error("bf_batch_replay: NULL batch or no captured graph");
+        return BF_ERR_STATE;
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail("bf_batch_replay", e);
+    return BF_OK;
+}
+
+bf_status bf_batch_status(bf_batch* b, void* stream)
+{
+    if (!b) {
+        set_error("bf_batch_status: NULL batch");
+        return BF_ERR_ARG;
+    }
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail("bf_batch_status: sync", e);
+    int h = 0;
+    if ((e = cudaMemcpy(&h, b->bl.err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail("bf_batch_status: read", e);
+    if (h) {
+        cudaMemset(b->bl.err, 0, sizeof(int));
+        set_error("bf_batch: a back tile gave up waiting for its front tiles (code %d)", h);
+        return BF_ERR_TIMEOUT;
+    }
+    return BF_OK;
+}
+
+bf_status bf_batch_get_info(const bf_batch* b, int64_t* work_items, int* grid, int64_t* ws_bytes, int64_t* smem)
+{
+    if (!b) {
+        set_error("bf_batch_get_info: NULL batch");
+        return BF_ERR_ARG;
+    }
+    if (work_items) *work_items = b->bl.total;
+    if (grid) *grid = b->bl.grid;
+    if (ws_bytes) *ws_bytes = (int64_t)b->ws_bytes;
+    if (smem) *smem = (int64_t)b->bl.smem;
+    return BF_OK;
+}
+
+bf_status bf_batch_set_spin_limit(bf_batch* b, long long polls)
+{
+    if (!b || polls < 1) {
+        set_error("bf_batch_set_spin_limit: NULL batch or polls < 1");
+        return BF_ERR_ARG;
+    }
+    b->bl.spin_limit = polls;
+    return BF_OK;
+}
+
+bf_status bf_batch_debug_hold(bf_batch* b, int on)
+{
+    if (!b) {
+        set_error("bf_batch_debug_hold: NULL batch");
+        return BF_ERR_ARG;
+    }
+    b->bl.wait_extra = on ? 1 : 0;
+    return BF_OK;
+}
+
+void bf_batch_destroy(bf_batch* b) { free_batch(b); }
+
+// ---------------------------------------------------------------- autotune --
+bf_status bf_autotune(bf_plan* p, int64_t m, const char* cache_path, int* mr_out)
+{
+    if (!p || m < 1) {
+        set_error("bf_autotune: NULL plan or m < 1");
+        return BF_ERR_ARG;
+    }
+    bf_status st = bf_upload(p);
+    if (st != BF_OK) return st;
+    DeviceState* ds = p->dev;
+    const Geo& g0 = ds->blocks[0].g;
+    char key[160];
+    snprintf(key, sizeof(key), "N=%lld r=%d ra=%d split=%d m=%lld", (long long)p->N, p->r, g0.ra, p->opt.split,
+             (long long)m);
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "r");
+        if (f) {
+            char line[256];
+            while (fgets(line, sizeof(line), f)) {
+                const size_t kl = strlen(key);
+                if (strncmp(line, key, kl) == 0 && line[kl] == ' ') {
+                    int mr = atoi(line + kl + 4);  // " mr=<v>"
+                    if (mr > 0) {
+                        p->tuned_mr[m] = mr;
+                        if (mr_out) *mr_out = mr;
+                        fclose(f);
+                        return BF_OK;
+                    }
+                }
+            }
+            fclose(f);
+        }
+    }
+    cudaError_t e = cudaSetDevice(ds->device);
+    if (e != cudaSuccess) return cuda_fail("bf_autotune: cudaSetDevice", e);
+    const int mr0 = fused_f32_config(g0, m, 0).mr;
+    std::vector<int> cand;
+    for (int mr = 1; mr <= 128; mr *= 2)
+        if (mr >= mr0 / 4 && mr <= mr0 * 4 && (int64_t)mr <= 2 * m && fused_f32_config(g0, m, mr).mr == mr)
+            cand.push_back(mr);
+    if (cand.empty()) cand.push_back(mr0);
+    size_t wsmax = 0;
+    for (int mr : cand)
+        for (auto& B : ds->blocks) wsmax = std::max(wsmax, fused_f32_ws_bytes(B.g, m, mr));
+    void *F = nullptr, *G = nullptr, *ws = nullptr;
+    const size_t nb = (size_t)p->N * m * sizeof(float2);
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (F) cudaFree(F);
+        if (G) cudaFree(G);
+        if (ws) cudaFree(ws);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s) cudaStreamDestroy(s);
+    };
+    if ((e = cudaMalloc(&F, nb)) != cudaSuccess || (e = cudaMalloc(&G, nb)) != cudaSuccess ||
+        (e = cudaMalloc(&ws, wsmax)) != cudaSuccess || (e = cudaMemset(F, 0, nb)) != cudaSuccess ||
+        (e = cudaStreamCreate(&s)) != cudaSuccess || (e = cudaEventCreate(&e0)) != cudaSuccess ||
+        (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cleanup();
+        return cuda_fail("bf_autotune: set-up", e);
+    }
+    int best = cand[0];
+    float best_ms = 1e30f;
+    for (int mr : cand) {
+        float tot = 0;
+        for (int rep = 0; rep < 5; ++rep) {
+            cudaEventRecord(e0, s);
+            for (size_t i = 0; i < ds->blocks.size(); ++i) {
+                const DevBlock& B = ds->blocks[i];
+                const int beta = (p->opt.split == 2 && (i % 2) == 1) ? 1 : 0;
+                e = launch_fused_f32(B, (const float2*)F + B.col0 * m, m, (float2*)G + B.row0 * m, beta,
+                                     (float2*)ws, s, mr);
+                if (e != cudaSuccess) break;
+            }
+            cudaEventRecord(e1, s);
+            if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                cleanup();
+                return cuda_fail("bf_autotune: trial", e);
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep >= 1) tot += ms;  // first run warms up
+        }
+        if (tot < best_ms) {
+            best_ms = tot;
+            best = mr;
+        }
+    }
+    cleanup();
+    p->tuned_mr[m] = best;
+    if (mr_out) *mr_out = best;
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s mr=%d ms=%.4f\n", key, best, best_ms / 4);
+            fclose(f);
+        }
+    }
+    return BF_OK;
+}
+
+}  // extern "C"

@@ -235,7 +235,7 @@ bf_status device_reserve(bf_plan* p, bf_precision prec, int64_t m, void*)
     size_t need = 0;
     for (auto& B : ds->blocks) {
         if (prec == BF_PREC_F64) need = std::max(need, 2 * plain_f64_ws_bytes(B.g, m));
-        else need = std::max(need, fused_f32_ws_bytes(B.g, m));
+        else need = std::max(need, fused_f32_ws_bytes(B.g, m, p->mr_hint(m)));
     }
     if (need == 0) need = 256;
     if (prec == BF_PREC_F64) return ensure(&ds->ws64, &ds->ws64_bytes, need);
@@ -272,7 +272,7 @@ bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, 
         } else {
             const float2* Fb = (const float2*)F + B.col0 * m;
             float2* Gb = (float2*)G + B.row0 * m;
-            e = launch_fused_f32(B, Fb, m, Gb, beta, (float2*)ds->ws32, st);
+            e = launch_fused_f32(B, Fb, m, Gb, beta, (float2*)ds->ws32, st, p->mr_hint(m));
         }
         if (e != cudaSuccess) {
             set_error("bf_apply: kernel launch failed: %s", cudaGetErrorString(e));

@@ -74,10 +74,11 @@ struct FusedCfg {
     int mr;       // right-hand sides per column slice
     int nslice;   // ceil(m / mr)
 };
-FusedCfg fused_f32_config(const Geo& g, int64_t m);
-size_t fused_f32_ws_bytes(const Geo& g, int64_t m);
+// mr_hint: column-slice width chosen by the autotuner (0 = built-in rule)
+FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint = 0);
+size_t fused_f32_ws_bytes(const Geo& g, int64_t m, int mr_hint = 0);
 cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta,
-                             float2* ws, cudaStream_t st);
+                             float2* ws, cudaStream_t st, int mr_hint = 0);
 bool fused_f32_supported(int r);
 
 // per-launch event timing (bf_profile_*); no-ops unless profiling is on

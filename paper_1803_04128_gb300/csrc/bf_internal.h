@@ -2,6 +2,7 @@
 #pragma once
 
 #include <complex>
+#include <map>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -64,6 +65,12 @@ struct bf_plan {
     bool user_kinds_lost = false;  // loaded from file with user callbacks
     std::vector<bfi::BlockFactors> blocks;  // 1 or 4
     bfi::DeviceState* dev = nullptr;
+    std::map<int64_t, int> tuned_mr;  // autotuned column-slice width per m (FP32 fused apply)
+    int mr_hint(int64_t m) const
+    {
+        auto it = tuned_mr.find(m);
+        return it == tuned_mr.end() ? 0 : it->second;
+    }
 };
 
 namespace bfi {

@@ -28,6 +28,7 @@
 #include <cstdio>
 
 #include "bf_device.h"
+#include "bf_fused.h"
 
 namespace bfi {
 namespace {
@@ -79,34 +80,6 @@ __device__ __forceinline__ void stage_matrix(float* dst, const float* src, int r
 template <int R>
 struct Pad4 {
     static constexpr int v = (R + 3) & ~3;
-};
-
-struct FrontArgs {
-    Geo g;
-    const float2* F;  // [N][m]
-    int64_t m;
-    int mr, lmr, CTp, lct, nslice;
-    const float2* bk;  // [ra][N]
-    const float* MvT;  // [nv][R]
-    const float2* EV;  // [2^l1][N]
-    const float* MHT;  // [kH][2R][R]
-    const float2* EH;  // [kH][P][2][R]
-    const float2* S;   // [P][R][R]
-    float2* W;         // [nslice][P][R][CTp]
-};
-
-struct BackArgs {
-    Geo g;
-    int64_t m;
-    int mr, lmr, CTp, lct, nslice;
-    const float2* W;
-    const float* MGT;  // [kG][2][R][R]  (pos, s, t)
-    const float2* FG;  // [kG][P][2][R]
-    const float* MU;   // [nv][R]
-    const float2* EU;  // [2^l1][N]
-    const float2* ak;  // [ra][N]
-    float2* G;         // [N][m]
-    int beta;
 };
 
 // H level (Eq. 2) on one (group, column): two inputs -> two outputs in place.
@@ -212,14 +185,13 @@ __device__ __forceinline__ void g_item(float2* x0, float2* x1, int CTp, const fl
 
 // ------------------------------------------------------------------ front --
 template <int R, int NV>
-__global__ void __launch_bounds__(kThreads, 2) front_f32(FrontArgs A)
+__device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, unsigned char* smem_raw)
 {
     constexpr int R4 = Pad4<R>::v;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geo& g = A.g;
     const int K = g.kH, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra;
-    const int slice = blockIdx.x % A.nslice;
-    const int64_t tile = blockIdx.x / A.nslice;
+    const int slice = (int)(work % A.nslice);
+    const int64_t tile = work / A.nslice;
     const int nP = 1 << g.l1;                       // x-nodes at level l1
     const int64_t p = tile & (nP - 1), c0 = tile >> g.l1;
     const int64_t nBh = (int64_t)1 << (g.L - g.h);   // T_Omega nodes at level L-h
@@ -359,14 +331,13 @@ __global__ void __launch_bounds__(kThreads, 2) front_f32(FrontArgs A)
 
 // ------------------------------------------------------------------- back --
 template <int R, int NU>
-__global__ void __launch_bounds__(kThreads, 2) back_f32(BackArgs A)
+__device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsigned char* smem_raw)
 {
     constexpr int R4 = Pad4<R>::v;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geo& g = A.g;
     const int K = g.kG, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra;
-    const int slice = blockIdx.x % A.nslice;
-    const int64_t pp = blockIdx.x / A.nslice;     // x-node at level h
+    const int slice = (int)(work % A.nslice);
+    const int64_t pp = work / A.nslice;           // x-node at level h
     const int nC = 1 << g.l1;                      // chunks c0' (= T_Omega nodes at level l1)
     const int64_t nBh = (int64_t)1 << (g.L - g.h);
     const int XN = T * NU;                         // output points of this CTA
@@ -485,6 +456,20 @@ __global__ void __launch_bounds__(kThreads, 2) back_f32(BackArgs A)
     }
 }
 
+template <int R, int NV>
+__global__ void __launch_bounds__(kThreads, 2) front_f32(FrontArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    front_tile<R, NV>(A, blockIdx.x, smem_raw);
+}
+
+template <int R, int NU>
+__global__ void __launch_bounds__(kThreads, 2) back_f32(BackArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    back_tile<R, NU>(A, blockIdx.x, smem_raw);
+}
+
 int ilog2(int v)
 {
     int l = 0;
@@ -509,60 +494,23 @@ size_t back_smem(const Geo& g, int R, int NU, int CTp, int mr)
 }
 
 template <int R>
-cudaError_t launch_r(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws,
+constexpr int nv_of() { return (R < 8) ? 8 : (R < 16 ? 16 : 32); }
+
+template <int R>
+cudaError_t launch_r(const FrontArgs& fa, const BackArgs& ba, size_t sf, size_t sb, int64_t nfront, int64_t nback,
                      cudaStream_t st)
 {
-    constexpr int NV = (R < 8) ? 8 : (R < 16 ? 16 : 32);
-    const Geo& g = B.g;
-    if (g.nv != NV) return cudaErrorNotSupported;
-    const FusedCfg cfg = fused_f32_config(g, m);
-    const int CTp = 1 << ilog2(g.ra * cfg.mr);
-    FrontArgs fa;
-    fa.g = g;
-    fa.F = F;
-    fa.m = m;
-    fa.mr = cfg.mr;
-    fa.lmr = ilog2(cfg.mr);
-    fa.CTp = CTp;
-    fa.lct = ilog2(CTp);
-    fa.nslice = cfg.nslice;
-    fa.bk = B.f32.b;
-    fa.MvT = B.f32.Mv;
-    fa.EV = B.f32.EV;
-    fa.MHT = B.f32.MH;
-    fa.EH = B.f32.EH;
-    fa.S = B.f32.S;
-    fa.W = ws;
-    const size_t sf = front_smem(g, R, NV, CTp, cfg.mr);
-    const size_t sb = back_smem(g, R, NV, CTp, cfg.mr);
+    constexpr int NV = nv_of<R>();
     cudaError_t e = cudaFuncSetAttribute(front_f32<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(back_f32<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
     if (e != cudaSuccess) return e;
-    const int64_t ntile = ((int64_t)1 << g.l1) * ((int64_t)1 << (g.L - g.h));
     {
         ProfScope ps("front_f32", st);
-        front_f32<R, NV><<<(unsigned)(ntile * cfg.nslice), kThreads, sf, st>>>(fa);
+        front_f32<R, NV><<<(unsigned)nfront, kThreads, sf, st>>>(fa);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    BackArgs ba;
-    ba.g = g;
-    ba.m = m;
-    ba.mr = cfg.mr;
-    ba.lmr = fa.lmr;
-    ba.CTp = CTp;
-    ba.lct = fa.lct;
-    ba.nslice = cfg.nslice;
-    ba.W = ws;
-    ba.MGT = B.f32.MG;
-    ba.FG = B.f32.FG;
-    ba.MU = B.f32.MU;
-    ba.EU = B.f32.EU;
-    ba.ak = B.f32.a;
-    ba.G = G;
-    ba.beta = beta;
-    const int64_t nback = ((int64_t)1 << g.h) * cfg.nslice;
     {
         ProfScope ps("back_f32", st);
         back_f32<R, NV><<<(unsigned)nback, kThreads, sb, st>>>(ba);
@@ -570,53 +518,204 @@ cudaError_t launch_r(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- batched --
+// One persistent launch over the front and back tiles of many operators.
+// Work items are handed out by an atomic counter, all front items first, so
+// every front item is claimed (by a running CTA) before any back item is; a
+// back item of operator i waits until all front items of i are done (bounded
+// spin; on time-out it sets *err and skips the tile).
+template <int R, int NV>
+__global__ void __launch_bounds__(kThreads, 2)
+    batch_f32(const BatchItem* items, int nitems, const int64_t* front_off, const int64_t* back_off,
+              int64_t total_front, int64_t total, unsigned long long* counter, int* done, int* err,
+              long long spin_limit, int wait_extra)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long s_w;
+    __shared__ int s_ok;
+    for (;;) {
+        if (threadIdx.x == 0) s_w = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long w = s_w;
+        __syncthreads();
+        if (w >= total) break;
+        if (w < total_front) {
+            int i = 0;
+            while (i + 1 < nitems && front_off[i + 1] <= w) ++i;
+            front_tile<R, NV>(items[i].fa, w - front_off[i], smem_raw);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(&done[i], 1);
+            }
+        } else {
+            const long long w2 = w - total_front;
+            int i = 0;
+            while (i + 1 < nitems && back_off[i + 1] <= w2) ++i;
+            if (threadIdx.x == 0) {
+                long long n = 0;
+                int ok = 1;
+                while (atomicAdd(&done[i], 0) < (int)items[i].nfront + wait_extra) {
+                    if (++n > spin_limit) {
+                        atomicExch(err, 2);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+                __threadfence();
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (s_ok) back_tile<R, NV>(items[i].ba, w2 - back_off[i], smem_raw);
+        }
+    }
+}
+
+template <int R>
+cudaError_t batch_launch_r(const BatchLaunch& bl, cudaStream_t st, bool set_attr, int* grid_out)
+{
+    constexpr int NV = nv_of<R>();
+    if (set_attr)  // configuration only, no launch
+        return cudaFuncSetAttribute(batch_f32<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bl.smem);
+    if (grid_out) {
+        int per_sm = 0, dev = 0, nsm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_f32<R, NV>, kThreads, bl.smem);
+        if (e != cudaSuccess) return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        *grid_out = per_sm * nsm;
+        return cudaSuccess;
+    }
+    ProfScope ps("batch_f32", st);
+    batch_f32<R, NV><<<bl.grid, kThreads, bl.smem, st>>>(bl.items, bl.nitems, bl.front_off, bl.back_off,
+                                                          bl.total_front, bl.total, bl.counter, bl.done, bl.err,
+                                                          bl.spin_limit, bl.wait_extra);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 bool fused_f32_supported(int r) { return r == 6 || r == 8 || r == 10 || r == 12 || r == 14 || r == 16; }
 
-FusedCfg fused_f32_config(const Geo& g, int64_t m)
+FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint)
 {
     const int Tmax = 1 << (g.kG > g.kH ? g.kG : g.kH);
     const int ra = g.ra > 0 ? g.ra : 1;
     const int NV = g.nv;
-    // largest power-of-two mr with at most 512 (group, column) items per level
-    // and a tile plus staged F rows within 80 KB of shared memory
-    int mr = 64;
-    while (mr > 1) {
+    auto fits = [&](int mr) {
         const int CTp = 1 << ilog2(ra * mr);
         const size_t tile = (size_t)Tmax * g.r * CTp * sizeof(float2);
         const size_t fs = (size_t)Tmax * NV * mr * sizeof(float2);
-        if ((Tmax / 2) * CTp <= 512 && tile + fs <= 80 * 1024) break;
-        mr >>= 1;
+        return CTp <= 256 && tile + fs <= 112 * 1024;
+    };
+    int mr;
+    if (mr_hint > 0 && (mr_hint & (mr_hint - 1)) == 0 && fits(mr_hint)) {
+        mr = mr_hint;
+    } else {
+        // largest power-of-two mr with at most 512 (group, column) items per level
+        // and a tile plus staged F rows within 80 KB of shared memory
+        mr = 64;
+        while (mr > 1) {
+            const int CTp = 1 << ilog2(ra * mr);
+            const size_t tile = (size_t)Tmax * g.r * CTp * sizeof(float2);
+            const size_t fs = (size_t)Tmax * NV * mr * sizeof(float2);
+            if ((Tmax / 2) * CTp <= 512 && tile + fs <= 80 * 1024) break;
+            mr >>= 1;
+        }
+        while (mr > 1 && (int64_t)(mr / 2) >= m) mr >>= 1;
     }
-    while (mr > 1 && (int64_t)(mr / 2) >= m) mr >>= 1;
     FusedCfg c;
     c.mr = mr;
     c.nslice = (int)((m + mr - 1) / mr);
     return c;
 }
 
-size_t fused_f32_ws_bytes(const Geo& g, int64_t m)
+size_t fused_f32_ws_bytes(const Geo& g, int64_t m, int mr_hint)
 {
-    const FusedCfg c = fused_f32_config(g, m);
+    const FusedCfg c = fused_f32_config(g, m, mr_hint);
     const int CTp = 1 << ilog2((g.ra > 0 ? g.ra : 1) * c.mr);
     return (size_t)c.nslice * g.P * g.r * CTp * sizeof(float2);
 }
 
+bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int mr_hint,
+                     FrontArgs* fa, BackArgs* ba, size_t* sf, size_t* sb, int64_t* nfront, int64_t* nback)
+{
+    const Geo& g = B.g;
+    if (!fused_f32_supported(g.r)) return false;
+    const int NV = (g.r < 8) ? 8 : (g.r < 16 ? 16 : 32);
+    if (g.nv != NV || g.ra < 1) return false;
+    const FusedCfg cfg = fused_f32_config(g, m, mr_hint);
+    const int CTp = 1 << ilog2(g.ra * cfg.mr);
+    fa->g = g;
+    fa->F = F;
+    fa->m = m;
+    fa->mr = cfg.mr;
+    fa->lmr = ilog2(cfg.mr);
+    fa->CTp = CTp;
+    fa->lct = ilog2(CTp);
+    fa->nslice = cfg.nslice;
+    fa->bk = B.f32.b;
+    fa->MvT = B.f32.Mv;
+    fa->EV = B.f32.EV;
+    fa->MHT = B.f32.MH;
+    fa->EH = B.f32.EH;
+    fa->S = B.f32.S;
+    fa->W = ws;
+    ba->g = g;
+    ba->m = m;
+    ba->mr = cfg.mr;
+    ba->lmr = fa->lmr;
+    ba->CTp = CTp;
+    ba->lct = fa->lct;
+    ba->nslice = cfg.nslice;
+    ba->W = ws;
+    ba->MGT = B.f32.MG;
+    ba->FG = B.f32.FG;
+    ba->MU = B.f32.MU;
+    ba->EU = B.f32.EU;
+    ba->ak = B.f32.a;
+    ba->G = G;
+    ba->beta = beta;
+    *sf = front_smem(g, g.r, NV, CTp, cfg.mr);
+    *sb = back_smem(g, g.r, NV, CTp, cfg.mr);
+    *nfront = ((int64_t)1 << g.l1) * ((int64_t)1 << (g.L - g.h)) * cfg.nslice;
+    *nback = ((int64_t)1 << g.h) * cfg.nslice;
+    return true;
+}
+
 cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws,
-                             cudaStream_t st)
+                             cudaStream_t st, int mr_hint)
 {
     if (B.g.ra == 0) {
         if (!beta) return cudaMemsetAsync(G, 0, (size_t)B.g.N * m * sizeof(float2), st);
         return cudaSuccess;
     }
+    FrontArgs fa;
+    BackArgs ba;
+    size_t sf, sb;
+    int64_t nf, nb;
+    if (!fused_make_args(B, F, m, G, beta, ws, mr_hint, &fa, &ba, &sf, &sb, &nf, &nb)) return cudaErrorNotSupported;
     switch (B.g.r) {
-    case 6: return launch_r<6>(B, F, m, G, beta, ws, st);
-    case 8: return launch_r<8>(B, F, m, G, beta, ws, st);
-    case 10: return launch_r<10>(B, F, m, G, beta, ws, st);
-    case 12: return launch_r<12>(B, F, m, G, beta, ws, st);
-    case 14: return launch_r<14>(B, F, m, G, beta, ws, st);
-    case 16: return launch_r<16>(B, F, m, G, beta, ws, st);
+    case 6: return launch_r<6>(fa, ba, sf, sb, nf, nb, st);
+    case 8: return launch_r<8>(fa, ba, sf, sb, nf, nb, st);
+    case 10: return launch_r<10>(fa, ba, sf, sb, nf, nb, st);
+    case 12: return launch_r<12>(fa, ba, sf, sb, nf, nb, st);
+    case 14: return launch_r<14>(fa, ba, sf, sb, nf, nb, st);
+    case 16: return launch_r<16>(fa, ba, sf, sb, nf, nb, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t batch_launch_f32(int r, const BatchLaunch& bl, cudaStream_t st, bool set_attr, int* grid_out)
+{
+    switch (r) {
+    case 6: return batch_launch_r<6>(bl, st, set_attr, grid_out);
+    case 8: return batch_launch_r<8>(bl, st, set_attr, grid_out);
+    case 10: return batch_launch_r<10>(bl, st, set_attr, grid_out);
+    case 12: return batch_launch_r<12>(bl, st, set_attr, grid_out);
+    case 14: return batch_launch_r<14>(bl, st, set_attr, grid_out);
+    case 16: return batch_launch_r<16>(bl, st, set_attr, grid_out);
     default: return cudaErrorNotSupported;
     }
 }
