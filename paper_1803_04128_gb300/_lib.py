@@ -40,6 +40,18 @@ class BatchItem(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("F", ctypes.c_void_p), ("G", ctypes.c_void_p), ("m", ctypes.c_int64)]
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int), ("hbm_budget", ctypes.c_int64), ("max_batch_rhs", ctypes.c_int64),
+                ("precision", ctypes.c_int), ("per_request", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("launches", ctypes.c_int64), ("mean_batch_rhs", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("units_per_s", ctypes.c_double), ("wall_s", ctypes.c_double)]
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("r", ctypes.c_int), ("n0", ctypes.c_int), ("L", ctypes.c_int),
                 ("h", ctypes.c_int), ("l1", ctypes.c_int), ("r_alpha", ctypes.c_int), ("split", ctypes.c_int),
@@ -86,6 +98,16 @@ _SIGS = {
     "bf_batch_debug_hold": (ctypes.c_int, [_P, ctypes.c_int]),
     "bf_batch_destroy": (None, [_P]),
     "bf_autotune": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
+    "bf_server_default_options": (ctypes.c_int, [ctypes.POINTER(ServerOptions)]),
+    "bf_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOptions), ctypes.POINTER(_P)]),
+    "bf_server_add_operator": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "bf_server_start": (ctypes.c_int, [_P]),
+    "bf_server_submit": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "bf_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "bf_server_drain": (ctypes.c_int, [_P, ctypes.c_double]),
+    "bf_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "bf_server_reset_stats": (ctypes.c_int, [_P]),
+    "bf_server_destroy": (None, [_P]),
 }
 
 _lock = threading.Lock()

@@ -224,6 +224,69 @@ class Batch:
             pass
 
 
+class Server:
+    """Continuous-batching request loop over resident operators (bf_server_*)."""
+
+    def __init__(self, n_slots=4, hbm_budget=0, max_batch_rhs=256, precision=F32, per_request=False, device=0):
+        self._lib = L.lib()
+        o = L.ServerOptions()
+        L.check(self._lib.bf_server_default_options(ctypes.byref(o)), "bf_server_default_options")
+        o.n_slots, o.hbm_budget, o.max_batch_rhs = n_slots, hbm_budget, max_batch_rhs
+        o.precision, o.per_request, o.device = precision, int(per_request), device
+        self._h = ctypes.c_void_p()
+        L.check(self._lib.bf_server_create(ctypes.byref(o), ctypes.byref(self._h)), "bf_server_create")
+        self._plans = []
+
+    def add(self, plan):
+        i = ctypes.c_int()
+        L.check(self._lib.bf_server_add_operator(self._h, plan._h, ctypes.byref(i)), "bf_server_add_operator")
+        self._plans.append(plan)
+        return i.value
+
+    def start(self):
+        L.check(self._lib.bf_server_start(self._h), "bf_server_start")
+
+    def submit(self, op, F, G):
+        """F, G: C-contiguous host arrays (numpy or pinned CPU tensors) of shape (N, m)."""
+        if isinstance(F, np.ndarray):
+            m = 1 if F.ndim == 1 else F.shape[1]
+            fp, gp = F.ctypes.data, G.ctypes.data
+        else:
+            m = 1 if F.dim() == 1 else F.shape[1]
+            fp, gp = F.data_ptr(), G.data_ptr()
+        rid = ctypes.c_uint64()
+        L.check(self._lib.bf_server_submit(self._h, op, ctypes.c_void_p(fp), m, ctypes.c_void_p(gp),
+                                           ctypes.byref(rid)), "bf_server_submit")
+        return rid.value
+
+    def wait(self, rid, timeout_ms=-1.0):
+        lat = ctypes.c_double()
+        L.check(self._lib.bf_server_wait(self._h, rid, timeout_ms, ctypes.byref(lat)), "bf_server_wait")
+        return lat.value
+
+    def drain(self, timeout_ms=-1.0):
+        L.check(self._lib.bf_server_drain(self._h, timeout_ms), "bf_server_drain")
+
+    def stats(self):
+        st = L.ServerStats()
+        L.check(self._lib.bf_server_get_stats(self._h, ctypes.byref(st)), "bf_server_get_stats")
+        return {k: getattr(st, k) for k, _ in L.ServerStats._fields_}
+
+    def reset_stats(self):
+        L.check(self._lib.bf_server_reset_stats(self._h), "bf_server_reset_stats")
+
+    def close(self):
+        if self._h:
+            self._lib.bf_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class KernelTimer:
     """Context manager: CUDA-event times of every library kernel launched inside
     (bf_profile_begin/end).  ``.result`` maps kernel name -> (launches, total_ms)."""

@@ -29,6 +29,8 @@ struct bf_batch {
 
 namespace {
 
+constexpr size_t kTwoCtaSmem = 113 * 1024;
+
 bf_status cuda_fail(const char* where, cudaError_t e)
 {
     set_error("%s: %s", where, cudaGetErrorString(e));
@@ -118,7 +120,8 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
     for (int i = 0; i < n; ++i) {
         const DevBlock& B = in[i].plan->dev->blocks[0];
         ws_off[(size_t)i] = ws_total;
-        ws_total += (fused_f32_ws_bytes(B.g, in[i].m, in[i].plan->mr_hint(in[i].m)) + 255) & ~(size_t)255;
+        ws_total += (std::max(fused_f32_ws_bytes(B.g, in[i].m, in[i].plan->mr_hint(in[i].m)),
+                              fused_f32_ws_bytes(B.g, in[i].m, 0)) + 255) & ~(size_t)255;
     }
     if ((e = cudaMalloc(&b->ws, std::max<size_t>(ws_total, 256))) != cudaSuccess) {
         free_batch(b);
@@ -133,9 +136,17 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
         const DevBlock& B = in[i].plan->dev->blocks[0];
         BatchItem& bi = b->items[(size_t)i];
         size_t sf, sb;
-        if (!fused_make_args(B, (const float2*)in[i].F, in[i].m, (float2*)in[i].G, 0,
-                             (float2*)((unsigned char*)b->ws + ws_off[(size_t)i]), in[i].plan->mr_hint(in[i].m),
-                             &bi.fa, &bi.ba, &sf, &sb, &bi.nfront, &bi.nback)) {
+        // keep every item within the shared memory of two resident CTAs per SM: the
+        // persistent launch runs all items at the occupancy of the largest one
+        int hint = in[i].plan->mr_hint(in[i].m);
+        bool ok = fused_make_args(B, (const float2*)in[i].F, in[i].m, (float2*)in[i].G, 0,
+                                  (float2*)((unsigned char*)b->ws + ws_off[(size_t)i]), hint, &bi.fa, &bi.ba, &sf,
+                                  &sb, &bi.nfront, &bi.nback);
+        if (ok && hint != 0 && std::max(sf, sb) > kTwoCtaSmem)
+            ok = fused_make_args(B, (const float2*)in[i].F, in[i].m, (float2*)in[i].G, 0,
+                                 (float2*)((unsigned char*)b->ws + ws_off[(size_t)i]), 0, &bi.fa, &bi.ba, &sf, &sb,
+                                 &bi.nfront, &bi.nback);
+        if (!ok) {
             free_batch(b);
             set_error("bf_batch_create: item %d: no fused FP32 kernels for r=%d", i, B.g.r);
             return BF_ERR_UNSUPPORTED;

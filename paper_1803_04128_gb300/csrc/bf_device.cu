@@ -1,4 +1,5 @@
 // Device residency of the factors, workspaces and apply dispatch.
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -276,6 +277,50 @@ bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, 
         }
         if (e != cudaSuccess) {
             set_error("bf_apply: kernel launch failed: %s", cudaGetErrorString(e));
+            return BF_ERR_CUDA;
+        }
+    }
+    return BF_OK;
+}
+
+size_t device_ws_bytes(const bf_plan* p, bf_precision prec, int64_t m)
+{
+    size_t need = 0;
+    for (auto& B : p->dev->blocks) {
+        if (prec == BF_PREC_F64) need = std::max(need, 2 * plain_f64_ws_bytes(B.g, m));
+        else need = std::max(need, fused_f32_ws_bytes(B.g, m, p->mr_hint(m)));
+    }
+    return need == 0 ? 256 : need;
+}
+
+bf_status device_apply_ws(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G, void* stream, void* ws,
+                          size_t ws_bytes)
+{
+    DeviceState* ds = p->dev;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == BF_PREC_BF16X3) {
+        set_error("BF_PREC_BF16X3 not available in this build");
+        return BF_ERR_UNSUPPORTED;
+    }
+    if (ws_bytes < device_ws_bytes(p, prec, m)) {
+        set_error("workspace of %zu bytes too small (%zu needed)", ws_bytes, device_ws_bytes(p, prec, m));
+        return BF_ERR_ARG;
+    }
+    const int sp = p->opt.split;
+    for (size_t i = 0; i < ds->blocks.size(); ++i) {
+        const DevBlock& B = ds->blocks[i];
+        const int beta = (sp == 2 && (i % 2) == 1) ? 1 : 0;
+        cudaError_t e;
+        if (prec == BF_PREC_F64) {
+            const size_t half = ws_bytes / 2 / sizeof(double2);
+            e = launch_plain_f64(B, (const double2*)F + B.col0 * m, m, (double2*)G + B.row0 * m, beta, (double2*)ws,
+                                 (double2*)ws + half, st);
+        } else {
+            e = launch_fused_f32(B, (const float2*)F + B.col0 * m, m, (float2*)G + B.row0 * m, beta, (float2*)ws, st,
+                                 p->mr_hint(m));
+        }
+        if (e != cudaSuccess) {
+            set_error("kernel launch failed: %s", cudaGetErrorString(e));
             return BF_ERR_CUDA;
         }
     }

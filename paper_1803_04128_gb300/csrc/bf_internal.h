@@ -114,6 +114,10 @@ bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, 
 bf_status device_apply_host(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G,
                             void* stream);
 bf_status device_sync_status(bf_plan* p, void* stream);
+// apply with a caller-owned workspace (ws_bytes >= device_ws_bytes(p, prec, m))
+size_t device_ws_bytes(const bf_plan* p, bf_precision prec, int64_t m);
+bf_status device_apply_ws(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G, void* stream, void* ws,
+                          size_t ws_bytes);
 void device_free(bf_plan* p);
 void device_info(const bf_plan* p, bf_plan_info* info);
 

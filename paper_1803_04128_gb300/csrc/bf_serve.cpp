@@ -1,0 +1,520 @@
+// Continuous-batching request loop (host runtime) over resident operators.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bf_internal.h"
+#include "bf_serve.h"
+
+using namespace bfi;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point a, Clock::time_point b)
+{
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Req {
+    int op = 0;
+    const void* F = nullptr;
+    void* G = nullptr;
+    int64_t m = 0;
+    Clock::time_point t_submit, t_done;
+    bool done = false;
+    bf_status status = BF_OK;
+};
+
+struct Op {
+    bf_plan* plan = nullptr;
+    int64_t N = 0;
+    int64_t cap = 0;  // right-hand sides per batch
+    std::deque<uint64_t> pending;
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    void* F = nullptr;
+    void* G = nullptr;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool busy = false;
+    std::vector<uint64_t> reqs;
+    int op = -1;
+    int64_t cols = 0;
+};
+
+}  // namespace
+
+struct bf_server {
+    bf_server_options opt{};
+    size_t elt = sizeof(float2);
+    std::vector<Op> ops;
+    std::vector<Slot> slots;
+    int64_t factor_bytes = 0;
+    std::mutex mu;
+    std::condition_variable cv_sched, cv_done;
+    std::unordered_map<uint64_t, Req> reqs;
+    uint64_t next_id = 1;
+    std::thread thr;
+    bool started = false, stop = false;
+    // statistics
+    std::vector<double> lat;
+    int64_t submitted = 0, completed = 0, launches = 0, batch_cols = 0;
+    double units_done = 0;
+    Clock::time_point t0 = Clock::now();
+};
+
+namespace {
+
+void reap(bf_server* s)
+{
+    for (auto& sl : s->slots) {
+        if (!sl.busy) continue;
+        cudaError_t e = cudaEventQuery(sl.ev);
+        if (e == cudaErrorNotReady) continue;
+        const auto now = Clock::now();
+        for (uint64_t id : sl.reqs) {
+            auto it = s->reqs.find(id);
+            if (it == s->reqs.end()) continue;
+            Req& r = it->second;
+            r.done = true;
+            r.t_done = now;
+            r.status = e == cudaSuccess ? BF_OK : BF_ERR_CUDA;
+            if (e == cudaSuccess) {
+                s->lat.push_back(ms_since(r.t_submit, now));
+                s->completed += 1;
+                s->units_done += (double)s->ops[(size_t)r.op].N * (double)r.m;
+            }
+        }
+        sl.reqs.clear();
+        sl.busy = false;
+        s->cv_done.notify_all();
+    }
+}
+
+// Enqueue one batch on a slot (called without the lock; the slot is owned).
+bf_status enqueue_batch(bf_server* s, Slot& sl, Op& op, std::vector<Req*>& rs)
+{
+    const int64_t N = op.N, M = sl.cols;
+    const size_t elt = s->elt;
+    cudaError_t e = cudaSuccess;
+    int64_t c = 0;
+    for (Req* r : rs) {
+        e = cudaMemcpy2DAsync((unsigned char*)sl.F + c * elt, (size_t)M * elt, r->F, (size_t)r->m * elt,
+                              (size_t)r->m * elt, (size_t)N, cudaMemcpyHostToDevice, sl.st);
+        if (e != cudaSuccess) return BF_ERR_CUDA;
+        c += r->m;
+    }
+    bf_status st = device_apply_ws(op.plan, (bf_precision)s->opt.precision, sl.F, M, sl.G, sl.st, sl.ws, sl.ws_bytes);
+    if (st != BF_OK) return st;
+    c = 0;
+    for (Req* r : rs) {
+        e = cudaMemcpy2DAsync(r->G, (size_t)r->m * elt, (unsigned char*)sl.G + c * elt, (size_t)M * elt,
+                              (size_t)r->m * elt, (size_t)N, cudaMemcpyDeviceToHost, sl.st);
+        if (e != cudaSuccess) return BF_ERR_CUDA;
+        c += r->m;
+    }
+    e = cudaEventRecord(sl.ev, sl.st);
+    return e == cudaSuccess ? BF_OK : BF_ERR_CUDA;
+}
+
+void scheduler(bf_server* s)
+{
+    cudaSetDevice(s->opt.device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        reap(s);
+        bool launched = false;
+        for (auto& sl : s->slots) {
+            if (sl.busy) continue;
+            // operator of the oldest pending request
+            int best = -1;
+            Clock::time_point bt{};
+            for (size_t i = 0; i < s->ops.size(); ++i) {
+                auto& q = s->ops[i].pending;
+                if (q.empty()) continue;
+                const auto t = s->reqs[q.front()].t_submit;
+                if (best < 0 || t < bt) {
+                    best = (int)i;
+                    bt = t;
+                }
+            }
+            if (best < 0) break;
+            Op& op = s->ops[(size_t)best];
+            std::vector<Req*> rs;
+            int64_t cols = 0;
+            while (!op.pending.empty()) {
+                Req& r = s->reqs[op.pending.front()];
+                if (cols + r.m > op.cap) break;
+                cols += r.m;
+                sl.reqs.push_back(op.pending.front());
+                rs.push_back(&r);
+                op.pending.pop_front();
+                if (s->opt.per_request) break;
+            }
+            if (rs.empty()) break;
+            sl.busy = true;
+            sl.op = best;
+            sl.cols = cols;
+            s->launches += 1;
+            s->batch_cols += cols;
+            lk.unlock();  // Req objects stay put: only this thread erases them after completion
+            bf_status st = enqueue_batch(s, sl, op, rs);
+            lk.lock();
+            if (st != BF_OK) {
+                const auto now = Clock::now();
+                for (uint64_t id : sl.reqs) {
+                    auto it = s->reqs.find(id);
+                    if (it != s->reqs.end()) {
+                        it->second.done = true;
+                        it->second.t_done = now;
+                        it->second.status = st;
+                    }
+                }
+                cudaStreamSynchronize(sl.st);
+                sl.reqs.clear();
+                sl.busy = false;
+                s->cv_done.notify_all();
+            }
+            launched = true;
+        }
+        bool any_busy = false;
+        for (auto& sl : s->slots) any_busy = any_busy || sl.busy;
+        if (s->stop && !any_busy) break;
+        if (!launched) s->cv_sched.wait_for(lk, std::chrono::microseconds(any_busy ? 20 : 2000));
+    }
+}
+
+int64_t per_col_bytes(const bf_server* s, const Op& op, int64_t m)
+{
+    return (int64_t)(2 * (size_t)op.N * (size_t)m * s->elt +
+                     device_ws_bytes(op.plan, (bf_precision)s->opt.precision, m));
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_server_default_options(bf_server_options* o)
+{
+    if (!o) {
+        set_error("bf_server_default_options: NULL");
+        return BF_ERR_ARG;
+    }
+    std::memset(o, 0, sizeof(*o));
+    o->n_slots = 4;
+    o->hbm_budget = 0;
+    o->max_batch_rhs = 256;
+    o->precision = BF_PREC_F32;
+    o->per_request = 0;
+    o->device = 0;
+    return BF_OK;
+}
+
+bf_status bf_server_create(const bf_server_options* opt, bf_server** out)
+{
+    if (!out) {
+        set_error("bf_server_create: NULL output");
+        return BF_ERR_ARG;
+    }
+    *out = nullptr;
+    bf_server* s = new (std::nothrow) bf_server();
+    if (!s) {
+        set_error("bf_server_create: out of host memory");
+        return BF_ERR_NOMEM;
+    }
+    if (opt) s->opt = *opt; else bf_server_default_options(&s->opt);
+    if (s->opt.n_slots < 1) s->opt.n_slots = 1;
+    if (s->opt.max_batch_rhs < 1) s->opt.max_batch_rhs = 256;
+    if (s->opt.precision != BF_PREC_F32 && s->opt.precision != BF_PREC_F64) {
+        delete s;
+        set_error("bf_server_create: precision must be BF_PREC_F32 or BF_PREC_F64");
+        return BF_ERR_ARG;
+    }
+    s->elt = s->opt.precision == BF_PREC_F64 ? sizeof(double2) : sizeof(float2);
+    if (cudaSetDevice(s->opt.device) != cudaSuccess) {
+        delete s;
+        set_error("bf_server_create: cannot use device %d", s->opt.device);
+        return BF_ERR_CUDA;
+    }
+    if (s->opt.hbm_budget <= 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            delete s;
+            set_error("bf_server_create: cudaMemGetInfo failed");
+            return BF_ERR_CUDA;
+        }
+        s->opt.hbm_budget = (int64_t)(0.6 * (double)fr);
+    }
+    *out = s;
+    return BF_OK;
+}
+
+bf_status bf_server_add_operator(bf_server* s, bf_plan* plan, int* op_id)
+{
+    if (!s || !plan) {
+        set_error("bf_server_add_operator: NULL argument");
+        return BF_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->started) {
+        set_error("bf_server_add_operator: add operators before bf_server_start");
+        return BF_ERR_STATE;
+    }
+    if (!plan->factored) {
+        set_error("bf_server_add_operator: plan not factored");
+        return BF_ERR_STATE;
+    }
+    if (plan->opt.device != s->opt.device) {
+        set_error("bf_server_add_operator: plan is on device %d, server on %d", plan->opt.device, s->opt.device);
+        return BF_ERR_ARG;
+    }
+    bf_plan_info info;
+    const bool was_up = plan->dev != nullptr;
+    if (!was_up) {
+        // admission: estimate the device factor bytes from the host factors (both arenas)
+        int64_t est = 0;
+        for (auto& B : plan->blocks) est += (int64_t)(B.host_bytes() * 3 / 2);
+        if (s->factor_bytes + est > s->opt.hbm_budget) {
+            set_error("bf_server_add_operator: factors (%lld bytes) exceed the remaining HBM budget (%lld)",
+                      (long long)est, (long long)(s->opt.hbm_budget - s->factor_bytes));
+            return BF_ERR_NOMEM;
+        }
+    }
+    bf_status st = bf_upload(plan);
+    if (st != BF_OK) return st;
+    bf_plan_get_info(plan, &info);
+    s->factor_bytes += info.dev_bytes_f32 + info.dev_bytes_f64;
+    if (s->factor_bytes > s->opt.hbm_budget) {
+        s->factor_bytes -= info.dev_bytes_f32 + info.dev_bytes_f64;
+        set_error("bf_server_add_operator: factors exceed the HBM budget");
+        return BF_ERR_NOMEM;
+    }
+    Op op;
+    op.plan = plan;
+    op.N = plan->N;
+    s->ops.push_back(op);
+    if (op_id) *op_id = (int)s->ops.size() - 1;
+    return BF_OK;
+}
+
+bf_status bf_server_start(bf_server* s)
+{
+    if (!s) {
+        set_error("bf_server_start: NULL server");
+        return BF_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->started) return BF_OK;
+    if (s->ops.empty()) {
+        set_error("bf_server_start: no operators");
+        return BF_ERR_STATE;
+    }
+    if (cudaSetDevice(s->opt.device) != cudaSuccess) {
+        set_error("bf_server_start: cudaSetDevice failed");
+        return BF_ERR_CUDA;
+    }
+    const int64_t per_slot = (s->opt.hbm_budget - s->factor_bytes) / s->opt.n_slots;
+    size_t slab = 0, ws = 0;
+    for (auto& op : s->ops) {
+        int64_t m = s->opt.max_batch_rhs;
+        while (m > 1 && per_col_bytes(s, op, m) > per_slot) m = m * 3 / 4;
+        if (per_col_bytes(s, op, m) > per_slot) {
+            set_error("bf_server_start: one right-hand side of N=%lld does not fit a slot (%lld bytes)",
+                      (long long)op.N, (long long)per_slot);
+            return BF_ERR_NOMEM;
+        }
+        op.cap = m;
+        slab = std::max(slab, (size_t)op.N * (size_t)m * s->elt);
+        ws = std::max(ws, device_ws_bytes(op.plan, (bf_precision)s->opt.precision, m));
+    }
+    s->slots.resize((size_t)s->opt.n_slots);
+    for (auto& sl : s->slots) {
+        cudaError_t e;
+        if ((e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaMalloc(&sl.F, slab)) != cudaSuccess || (e = cudaMalloc(&sl.G, slab)) != cudaSuccess ||
+            (e = cudaMalloc(&sl.ws, ws)) != cudaSuccess) {
+            set_error("bf_server_start: slot allocation: %s", cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? BF_ERR_NOMEM : BF_ERR_CUDA;
+        }
+        sl.ws_bytes = ws;
+    }
+    s->t0 = Clock::now();
+    s->started = true;
+    s->thr = std::thread(scheduler, s);
+    return BF_OK;
+}
+
+bf_status bf_server_submit(bf_server* s, int op_id, const void* F, int64_t m, void* G, uint64_t* req_id)
+{
+    if (!s || !F || !G || m < 1) {
+        set_error("bf_server_submit: NULL argument or m < 1");
+        return BF_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->started || s->stop) {
+        set_error("bf_server_submit: server not running");
+        return BF_ERR_STATE;
+    }
+    if (op_id < 0 || op_id >= (int)s->ops.size()) {
+        set_error("bf_server_submit: unknown operator %d", op_id);
+        return BF_ERR_ARG;
+    }
+    Op& op = s->ops[(size_t)op_id];
+    if (m > op.cap) {
+        set_error("bf_server_submit: m=%lld exceeds the batch width %lld of operator %d", (long long)m,
+                  (long long)op.cap, op_id);
+        return BF_ERR_ARG;
+    }
+    const uint64_t id = s->next_id++;
+    Req r;
+    r.op = op_id;
+    r.F = F;
+    r.G = G;
+    r.m = m;
+    r.t_submit = Clock::now();
+    s->reqs.emplace(id, r);
+    op.pending.push_back(id);
+    s->submitted += 1;
+    if (req_id) *req_id = id;
+    s->cv_sched.notify_one();
+    return BF_OK;
+}
+
+bf_status bf_server_wait(bf_server* s, uint64_t id, double timeout_ms, double* latency_ms)
+{
+    if (!s) {
+        set_error("bf_server_wait: NULL server");
+        return BF_ERR_ARG;
+    }
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) {
+        set_error("bf_server_wait: unknown request %llu", (unsigned long long)id);
+        return BF_ERR_ARG;
+    }
+    auto pred = [&] { return s->reqs[id].done; };
+    if (timeout_ms < 0) {
+        s->cv_done.wait(lk, pred);
+    } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), pred)) {
+        set_error("bf_server_wait: request %llu not done after %.1f ms", (unsigned long long)id, timeout_ms);
+        return BF_ERR_TIMEOUT;
+    }
+    Req r = s->reqs[id];
+    s->reqs.erase(id);
+    if (latency_ms) *latency_ms = ms_since(r.t_submit, r.t_done);
+    if (r.status != BF_OK) set_error("bf_server_wait: request %llu failed", (unsigned long long)id);
+    return r.status;
+}
+
+bf_status bf_server_drain(bf_server* s, double timeout_ms)
+{
+    if (!s) {
+        set_error("bf_server_drain: NULL server");
+        return BF_ERR_ARG;
+    }
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto pred = [&] {
+        for (auto& kv : s->reqs)
+            if (!kv.second.done) return false;
+        return true;
+    };
+    if (timeout_ms < 0) {
+        s->cv_done.wait(lk, pred);
+        return BF_OK;
+    }
+    if (!s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), pred)) {
+        set_error("bf_server_drain: requests still pending after %.1f ms", timeout_ms);
+        return BF_ERR_TIMEOUT;
+    }
+    return BF_OK;
+}
+
+bf_status bf_server_get_stats(bf_server* s, bf_server_stats* out)
+{
+    if (!s || !out) {
+        set_error("bf_server_get_stats: NULL argument");
+        return BF_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    int64_t pend = 0, fl = 0;
+    for (auto& op : s->ops) pend += (int64_t)op.pending.size();
+    for (auto& sl : s->slots) fl += (int64_t)sl.reqs.size();
+    out->pending = pend;
+    out->in_flight = fl;
+    out->launches = s->launches;
+    out->mean_batch_rhs = s->launches ? (double)s->batch_cols / (double)s->launches : 0.0;
+    if (!s->lat.empty()) {
+        std::vector<double> v = s->lat;
+        std::sort(v.begin(), v.end());
+        auto q = [&](double p) { return v[(size_t)std::min((double)v.size() - 1, p * (double)(v.size() - 1) + 0.5)]; };
+        out->p50_ms = q(0.50);
+        out->p99_ms = q(0.99);
+        double sum = 0;
+        for (double x : v) sum += x;
+        out->mean_ms = sum / (double)v.size();
+        out->max_ms = v.back();
+    }
+    out->wall_s = ms_since(s->t0, Clock::now()) / 1e3;
+    out->units_per_s = out->wall_s > 0 ? s->units_done / out->wall_s : 0.0;
+    return BF_OK;
+}
+
+bf_status bf_server_reset_stats(bf_server* s)
+{
+    if (!s) {
+        set_error("bf_server_reset_stats: NULL server");
+        return BF_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->lat.clear();
+    s->completed = 0;
+    s->submitted = 0;
+    s->launches = 0;
+    s->batch_cols = 0;
+    s->units_done = 0;
+    s->t0 = Clock::now();
+    return BF_OK;
+}
+
+void bf_server_destroy(bf_server* s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        // pending (not yet launched) requests are dropped
+        for (auto& op : s->ops) op.pending.clear();
+        s->cv_sched.notify_all();
+    }
+    if (s->thr.joinable()) s->thr.join();
+    cudaSetDevice(s->opt.device);
+    for (auto& sl : s->slots) {
+        if (sl.st) cudaStreamSynchronize(sl.st);
+        cudaFree(sl.F);
+        cudaFree(sl.G);
+        cudaFree(sl.ws);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.st) cudaStreamDestroy(sl.st);
+    }
+    delete s;
+}
+
+}  // extern "C"
