@@ -129,8 +129,8 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
     }
     b->ws_bytes = ws_total;
     b->items.resize((size_t)n);
-    std::vector<int64_t> foff((size_t)n), boff((size_t)n);
-    int64_t tf = 0, tb = 0;
+    std::vector<int64_t> off((size_t)(2 * n));
+    int64_t tot = 0;
     size_t smem = 0;
     for (int i = 0; i < n; ++i) {
         const DevBlock& B = in[i].plan->dev->blocks[0];
@@ -152,21 +152,21 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
             return BF_ERR_UNSUPPORTED;
         }
         smem = std::max(smem, std::max(sf, sb));
-        foff[(size_t)i] = tf;
-        boff[(size_t)i] = tb;
-        tf += bi.nfront;
-        tb += bi.nback;
+        off[(size_t)(2 * i)] = tot;
+        tot += bi.nfront;
+        off[(size_t)(2 * i + 1)] = tot;
+        tot += bi.nback;
     }
     if (smem > 227 * 1024) {
         free_batch(b);
         set_error("bf_batch_create: a tile needs %zu bytes of shared memory", smem);
         return BF_ERR_UNSUPPORTED;
     }
-    // device copies: items | front_off | back_off | counter | done[n] | err
+    // device copies: items | off[2n] | counter | done[n] | err
     const size_t s_items = ((size_t)n * sizeof(BatchItem) + 255) & ~(size_t)255;
-    const size_t s_off = ((size_t)n * sizeof(int64_t) + 255) & ~(size_t)255;
+    const size_t s_off = ((size_t)(2 * n) * sizeof(int64_t) + 255) & ~(size_t)255;
     const size_t s_reset = ((sizeof(unsigned long long) + (size_t)n * sizeof(int)) + 255) & ~(size_t)255;
-    b->dmem_bytes = s_items + 2 * s_off + s_reset + 256;
+    b->dmem_bytes = s_items + s_off + s_reset + 256;
     if ((e = cudaMalloc(&b->dmem, b->dmem_bytes)) != cudaSuccess) {
         free_batch(b);
         return cuda_fail("bf_batch_create: descriptors", e);
@@ -174,23 +174,20 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
     unsigned char* base = (unsigned char*)b->dmem;
     std::vector<unsigned char> host(b->dmem_bytes, 0);
     std::memcpy(host.data(), b->items.data(), (size_t)n * sizeof(BatchItem));
-    std::memcpy(host.data() + s_items, foff.data(), (size_t)n * sizeof(int64_t));
-    std::memcpy(host.data() + s_items + s_off, boff.data(), (size_t)n * sizeof(int64_t));
+    std::memcpy(host.data() + s_items, off.data(), (size_t)(2 * n) * sizeof(int64_t));
     if ((e = cudaMemcpy(base, host.data(), b->dmem_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
         free_batch(b);
         return cuda_fail("bf_batch_create: upload", e);
     }
     b->bl.items = (const BatchItem*)base;
     b->bl.nitems = n;
-    b->bl.front_off = (const int64_t*)(base + s_items);
-    b->bl.back_off = (const int64_t*)(base + s_items + s_off);
-    b->reset_ptr = base + s_items + 2 * s_off;
+    b->bl.off = (const int64_t*)(base + s_items);
+    b->reset_ptr = base + s_items + s_off;
     b->reset_bytes = s_reset;
     b->bl.counter = (unsigned long long*)b->reset_ptr;
     b->bl.done = (int*)(b->reset_ptr + sizeof(unsigned long long));
     b->bl.err = (int*)(b->reset_ptr + s_reset);
-    b->bl.total_front = tf;
-    b->bl.total = tf + tb;
+    b->bl.total = tot;
     b->bl.smem = smem;
     e = batch_launch_f32(b->r, b->bl, nullptr, true, nullptr);
     if (e == cudaSuccess) e = batch_launch_f32(b->r, b->bl, nullptr, false, &b->bl.grid);

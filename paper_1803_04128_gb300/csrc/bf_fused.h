@@ -45,9 +45,8 @@ struct BatchItem {
 struct BatchLaunch {
     const BatchItem* items = nullptr;
     int nitems = 0;
-    const int64_t* front_off = nullptr;  // [nitems] prefix sums of nfront
-    const int64_t* back_off = nullptr;   // [nitems] prefix sums of nback
-    int64_t total_front = 0, total = 0;
+    const int64_t* off = nullptr;  // [2 nitems] start of (fronts of op i, backs of op i) in the work order
+    int64_t total = 0;
     unsigned long long* counter = nullptr;
     int* done = nullptr;  // [nitems]
     int* err = nullptr;

@@ -25,6 +25,7 @@
 //
 // Every tile input (factor phases, Lagrange matrices, the F rows, b_k) is
 // staged into shared memory with cp.async in one commit group before use.
+#include <algorithm>
 #include <cstdio>
 
 #include "bf_device.h"
@@ -61,11 +62,10 @@ __device__ __forceinline__ void cp8(void* dst, const void* src, bool valid)
     int n = valid ? 8 : 0;
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(src), "r"(n) : "memory");
 }
-__device__ __forceinline__ void cp_commit_wait()
-{
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most 0 / 1 of this thread's committed groups are still pending
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // real rows x cols matrix (row-major, global) -> shared rows padded to c4 floats, 8-byte copies
 __device__ __forceinline__ void stage_matrix(float* dst, const float* src, int rows, int cols, int c4, int tid)
@@ -184,6 +184,10 @@ __device__ __forceinline__ void g_item(float2* x0, float2* x1, int CTp, const fl
 }
 
 // ------------------------------------------------------------------ front --
+// Shared memory: X [T][R][CTp] | EH double buffer [2][T][2][R] | EV [T*NV] |
+// F rows [T*NV][mr] | Mv^T [NV][R4] | MH^T [kH][2R][R4].  The phases of level j
+// are staged (cp.async) while level j-1 is computed; b_k and the switch
+// matrices are read through the read-only cache.
 template <int R, int NV>
 __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, unsigned char* smem_raw)
 {
@@ -196,56 +200,52 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
     const int64_t p = tile & (nP - 1), c0 = tile >> g.l1;
     const int64_t nBh = (int64_t)1 << (g.L - g.h);   // T_Omega nodes at level L-h
     const int64_t xi_base = c0 * T * NV;
+    const int64_t N = g.N, P = g.P, m = A.m;
+    const int L = g.L, l1 = g.l1;
 
     float2* X = reinterpret_cast<float2*>(smem_raw);         // [T][R][CTp]
-    float2* Fs = X + (size_t)T * R * CTp;                     // [T*NV][mr]
-    float2* Bs = Fs + (size_t)T * NV * mr;                    // [ra][T*NV]
-    float2* EHs = Bs + (size_t)ra * T * NV;                   // [K][T][2][R]
-    float2* Ss = EHs + (size_t)K * T * 2 * R;                 // [T][R][R]
-    float2* EVs = Ss + (size_t)T * R * R;                     // [T*NV]
-    float* MvTs = reinterpret_cast<float*>(EVs + (size_t)T * NV);  // [NV][R4]
-    float* MHTs = MvTs + NV * R4;                                  // [K][2R][R4]
+    float2* EHb = X + (size_t)T * R * CTp;                    // [2][T][2][R]
+    float2* EVs = EHb + (size_t)2 * T * 2 * R;                // [T*NV]
+    float2* Fs = EVs + (size_t)T * NV;                        // [T*NV][mr]
+    float* MvTs = reinterpret_cast<float*>(Fs + (size_t)T * NV * mr);  // [NV][R4]
+    float* MHTs = MvTs + NV * R4;                                      // [K][2R][R4]
 
     const int tid = threadIdx.x;
-    // ---- stage every input of this tile (one cp.async group)
-    stage_matrix(MvTs, A.MvT, NV, R, R4, tid);
-    stage_matrix(MHTs, A.MHT, K * 2 * R, R, R4, tid);
-    {
-        const float2* ev = A.EV + p * g.N + xi_base;
-        for (int e = tid; e < T * NV / 2; e += kThreads) cp16(EVs + 2 * e, ev + 2 * e);
-    }
-    for (int j = 1; j <= K; ++j) {
-        const int l = g.l1 + j;
-        const int64_t nBl = (int64_t)1 << (g.L - l);
-        const float2* eh = A.EH + (size_t)(j - 1) * g.P * 2 * R;
+    const float2* EHg = A.EH;
+    auto stage_eh = [&](int j) {  // phases of level l1 + j into buffer (j - 1) & 1
+        const int64_t nBl = (int64_t)1 << (L - l1 - j);
+        const float2* eh = EHg + (size_t)(j - 1) * P * 2 * R;
+        float2* dst = EHb + (size_t)((j - 1) & 1) * T * 2 * R;
         for (int e = tid; e < T * R; e += kThreads) {  // R 16-byte chunks per pair
             const int lp = e / R, w = e - lp * R;
             const int64_t ap = (p << j) + (lp >> (K - j));
             const int64_t bp = (c0 << (K - j)) + (lp & ((1 << (K - j)) - 1));
-            cp16(EHs + ((size_t)(j - 1) * T + lp) * 2 * R + 2 * w, eh + (ap * nBl + bp) * 2 * R + 2 * w);
+            cp16(dst + (size_t)lp * 2 * R + 2 * w, eh + (ap * nBl + bp) * 2 * R + 2 * w);
         }
-    }
-    for (int e = tid; e < T * (R * R / 2); e += kThreads) {
-        const int lp = e / (R * R / 2), w = e - lp * (R * R / 2);
-        const int64_t q = ((p << K) + lp) * nBh + c0;
-        cp16(Ss + (size_t)lp * R * R + 2 * w, A.S + q * R * R + 2 * w);
-    }
+    };
+    // group 0: matrices, EV, F rows, level-1 phases; group 1: level-2 phases
+    stage_matrix(MvTs, A.MvT, NV, R, R4, tid);
+    stage_matrix(MHTs, A.MHT, K * 2 * R, R, R4, tid);
     {
+        const float2* ev = A.EV + p * N + xi_base;
+        for (int e = tid; e < T * NV / 2; e += kThreads) cp16(EVs + 2 * e, ev + 2 * e);
         const int64_t cbase = (int64_t)slice * mr;
         for (int e = tid; e < T * NV * mr; e += kThreads) {
             const int row = e >> lmr, c = e & (mr - 1);
-            const bool valid = cbase + c < A.m;
-            cp8(Fs + e, A.F + (xi_base + row) * A.m + (valid ? cbase + c : 0), valid);
+            const bool valid = cbase + c < m;
+            cp8(Fs + e, A.F + (xi_base + row) * m + (valid ? cbase + c : 0), valid);
         }
-        for (int e = tid; e < ra * T * NV; e += kThreads) {
-            const int k = e / (T * NV), x = e - k * (T * NV);
-            cp8(Bs + e, A.bk + (size_t)k * g.N + xi_base + x, true);
-        }
+    }
+    if (K >= 1) stage_eh(1);
+    cp_commit();
+    if (K >= 2) {
+        stage_eh(2);
+        cp_commit();
     }
     // padding columns of the tile start (and stay) at zero
     for (int e = tid; e < T * R * CTp; e += kThreads)
         if ((e & (CTp - 1)) >= ra * mr) X[e] = make_float2(0.f, 0.f);
-    cp_commit_wait();
+    if (K >= 2) cp_wait1(); else cp_wait0();
     __syncthreads();
 
     // ---- V (Eq. 1): item (j, c) computes mu[j][.][k*mr + c] for every k
@@ -260,10 +260,10 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
                 float2 acc[R];
 #pragma unroll
                 for (int t = 0; t < R; ++t) acc[t] = make_float2(0.f, 0.f);
-                const float2* bs = Bs + (size_t)k * T * NV + j * NV;
+                const float2* bk = A.bk + (size_t)k * N + xi_base + j * NV;
 #pragma unroll
                 for (int x = 0; x < NV; ++x) {
-                    const float2 z = cmulf(EVs[j * NV + x], cmulf(bs[x], f[x]));
+                    const float2 z = cmulf(EVs[j * NV + x], cmulf(__ldg(bk + x), f[x]));
                     const float4* mv = reinterpret_cast<const float4*>(MvTs + x * R4);
 #pragma unroll
                     for (int t4 = 0; t4 < R4 / 4; ++t4) {
@@ -285,14 +285,18 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
             }
         }
     }
+    __syncthreads();
 
     // ---- H levels (Eq. 2), in place
     const int col = tid & (CTp - 1);
     for (int j = 1; j <= K; ++j) {
-        __syncthreads();
+        if (j > 1) {
+            if (j < K) cp_wait1(); else cp_wait0();
+            __syncthreads();
+        }
         const int kj = K - j, half = 1 << kj;
         const float* Mh = MHTs + (size_t)(j - 1) * 2 * R * R4;
-        const float2* Eh = EHs + (size_t)(j - 1) * T * 2 * R;
+        const float2* Eh = EHb + (size_t)((j - 1) & 1) * T * 2 * R;
         for (int grp = tid >> lct; grp < T / 2; grp += kThreads >> lct) {
             const int a = grp >> kj, bp = grp & (half - 1);
             const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
@@ -301,26 +305,30 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
             h_item<R>(x0, x1, CTp, Eh + (size_t)((2 * a) * half + bp) * 2 * R,
                       Eh + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mh);
         }
+        __syncthreads();
+        if (j + 2 <= K) {
+            stage_eh(j + 2);
+            cp_commit();
+        }
     }
-    __syncthreads();
 
     // ---- switch (step 4) and write-out of the switch-level coefficients
-    float2* Wout = A.W + (size_t)slice * g.P * R * CTp;
+    float2* Wout = A.W + (size_t)slice * P * R * CTp;
     for (int lp = tid >> lct; lp < T; lp += kThreads >> lct) {
         const int slot = (int)brev((unsigned)lp, K);
         const float2* xs = X + (size_t)slot * R * CTp + col;
         float2 mu[R];
 #pragma unroll
         for (int s = 0; s < R; ++s) mu[s] = xs[s * CTp];
-        const float4* Sp = reinterpret_cast<const float4*>(Ss + (size_t)lp * R * R);
         const int64_t q = ((p << K) + lp) * nBh + c0;
+        const float4* Sp = reinterpret_cast<const float4*>(A.S + q * R * R);
         float2* wo = Wout + (size_t)q * R * CTp + col;
 #pragma unroll
         for (int t = 0; t < R; ++t) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int s2 = 0; s2 < R / 2; ++s2) {
-                const float4 sv = Sp[t * (R / 2) + s2];
+                const float4 sv = __ldg(Sp + t * (R / 2) + s2);
                 cfmaf(acc, make_float2(sv.x, sv.y), mu[2 * s2]);
                 cfmaf(acc, make_float2(sv.z, sv.w), mu[2 * s2 + 1]);
             }
@@ -330,6 +338,8 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
 }
 
 // ------------------------------------------------------------------- back --
+// Shared memory: X [T][R][CTp] | FG double buffer [2][T][2][R] | EU [XN] |
+// U accumulator [XN][mr] | MG^T [kG][2][R][R4] | MU [NU][R4].
 template <int R, int NU>
 __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsigned char* smem_raw)
 {
@@ -341,53 +351,62 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
     const int nC = 1 << g.l1;                      // chunks c0' (= T_Omega nodes at level l1)
     const int64_t nBh = (int64_t)1 << (g.L - g.h);
     const int XN = T * NU;                         // output points of this CTA
+    const int64_t N = g.N, P = g.P;
+    const int L = g.L, h = g.h;
 
     float2* X = reinterpret_cast<float2*>(smem_raw);    // [T][R][CTp]
-    float2* FGs = X + (size_t)T * R * CTp;               // [K][T][2][R]
-    float2* EUs = FGs + (size_t)K * T * 2 * R;           // [XN]
-    float2* AKs = EUs + XN;                              // [ra][XN]
-    float2* acc = AKs + (size_t)ra * XN;                 // [XN][mr]
+    float2* FGb = X + (size_t)T * R * CTp;               // [2][T][2][R]
+    float2* EUs = FGb + (size_t)2 * T * 2 * R;           // [XN]
+    float2* acc = EUs + XN;                              // [XN][mr]
     float* MGTs = reinterpret_cast<float*>(acc + (size_t)XN * mr);  // [K][2][R][R4]
     float* MUs = MGTs + (size_t)K * 2 * R * R4;                      // [NU][R4]
 
     const int tid = threadIdx.x;
     const int64_t x0g = pp * XN;
+    const float2* FGg = A.FG;
+    int c0 = 0;
+    auto stage_fg = [&](int j) {  // phases of level h + j into buffer (j - 1) & 1
+        const int64_t nBl = (int64_t)1 << (L - h - j);
+        const float2* fg = FGg + (size_t)(j - 1) * P * 2 * R;
+        float2* dst = FGb + (size_t)((j - 1) & 1) * T * 2 * R;
+        for (int e = tid; e < T * R; e += kThreads) {
+            const int lp = e / R, w = e - lp * R;
+            const int64_t ap = (pp << j) + (lp >> (K - j));
+            const int64_t bp = ((int64_t)c0 << (K - j)) + (lp & ((1 << (K - j)) - 1));
+            cp16(dst + (size_t)lp * 2 * R + 2 * w, fg + (ap * nBl + bp) * 2 * R + 2 * w);
+        }
+    };
     stage_matrix(MGTs, A.MGT, K * 2 * R, R, R4, tid);
     stage_matrix(MUs, A.MU, NU, R, R4, tid);
-    for (int e = tid; e < ra * XN / 2; e += kThreads) {
-        const int k = e / (XN / 2), x = e - k * (XN / 2);
-        cp16(AKs + (size_t)k * XN + 2 * x, A.ak + (size_t)k * g.N + x0g + 2 * x);
-    }
     for (int e = tid; e < XN * mr; e += kThreads) acc[e] = make_float2(0.f, 0.f);
-    const float2* Win = A.W + (size_t)slice * g.P * R * CTp;
+    const float2* Win = A.W + (size_t)slice * P * R * CTp;
     const int col = tid & (CTp - 1);
 
-    for (int c0 = 0; c0 < nC; ++c0) {
-        __syncthreads();
+    for (c0 = 0; c0 < nC; ++c0) {
+        __syncthreads();  // the previous chunk's U stage is done with X and EU
         {   // pairs (pp, c0 * T + j), j < T: one contiguous block of T*R*CTp
             const float2* src = Win + (size_t)(pp * nBh + (int64_t)c0 * T) * R * CTp;
             for (int e = tid; e < T * R * CTp / 2; e += kThreads) cp16(X + 2 * e, src + 2 * e);
+            for (int e = tid; e < XN / 2; e += kThreads) cp16(EUs + 2 * e, A.EU + (size_t)c0 * N + x0g + 2 * e);
         }
-        for (int j = 1; j <= K; ++j) {
-            const int l = g.h + j;
-            const int64_t nBl = (int64_t)1 << (g.L - l);
-            const float2* fg = A.FG + (size_t)(j - 1) * g.P * 2 * R;
-            for (int e = tid; e < T * R; e += kThreads) {
-                const int lp = e / R, w = e - lp * R;
-                const int64_t ap = (pp << j) + (lp >> (K - j));
-                const int64_t bp = ((int64_t)c0 << (K - j)) + (lp & ((1 << (K - j)) - 1));
-                cp16(FGs + ((size_t)(j - 1) * T + lp) * 2 * R + 2 * w, fg + (ap * nBl + bp) * 2 * R + 2 * w);
-            }
+        if (K >= 1) stage_fg(1);
+        cp_commit();
+        if (K >= 2) {
+            stage_fg(2);
+            cp_commit();
         }
-        for (int e = tid; e < XN / 2; e += kThreads) cp16(EUs + 2 * e, A.EU + (size_t)c0 * g.N + x0g + 2 * e);
-        cp_commit_wait();
+        if (K >= 2) cp_wait1(); else cp_wait0();
+        __syncthreads();
 
         // ---- G levels (Eq. 3), in place
         for (int j = 1; j <= K; ++j) {
-            __syncthreads();
+            if (j > 1) {
+                if (j < K) cp_wait1(); else cp_wait0();
+                __syncthreads();
+            }
             const int kj = K - j, half = 1 << kj;
             const float* Mg = MGTs + (size_t)(j - 1) * 2 * R * R4;
-            const float2* Fg = FGs + (size_t)(j - 1) * T * 2 * R;
+            const float2* Fg = FGb + (size_t)((j - 1) & 1) * T * 2 * R;
             for (int grp = tid >> lct; grp < T / 2; grp += kThreads >> lct) {
                 const int a = grp >> kj, bp = grp & (half - 1);
                 const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
@@ -396,8 +415,12 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
                 g_item<R>(x0, x1, CTp, Fg + (size_t)((2 * a) * half + bp) * 2 * R,
                           Fg + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mg);
             }
+            __syncthreads();
+            if (j + 2 <= K) {
+                stage_fg(j + 2);
+                cp_commit();
+            }
         }
-        __syncthreads();
 
         // ---- U (Eq. bf3) contribution of T_Omega node c0 to this CTA's points
         {
@@ -410,7 +433,7 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
                     float2 v[R];
 #pragma unroll
                     for (int s = 0; s < R; ++s) v[s] = xs[s * CTp + k * mr];
-                    const float2* ak = AKs + (size_t)k * XN + lp * NU;
+                    const float2* ak = A.ak + (size_t)k * N + x0g + lp * NU;
 #pragma unroll 4
                     for (int i = 0; i < NU; ++i) {
                         float2 w = make_float2(0.f, 0.f);
@@ -429,7 +452,7 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
                             }
                         }
                         float2 o = ap[i * mr];
-                        cfmaf(o, cmulf(ak[i], EUs[lp * NU + i]), w);
+                        cfmaf(o, cmulf(__ldg(ak + i), EUs[lp * NU + i]), w);
                         ap[i * mr] = o;
                     }
                 }
@@ -480,8 +503,7 @@ int ilog2(int v)
 size_t front_smem(const Geo& g, int R, int NV, int CTp, int mr)
 {
     const size_t T = (size_t)1 << g.kH, R4 = (R + 3) & ~3;
-    return sizeof(float2) * (T * R * CTp + T * NV * mr + (size_t)g.ra * T * NV + (size_t)g.kH * T * 2 * R +
-                             T * R * R + T * NV) +
+    return sizeof(float2) * (T * R * CTp + 2 * T * 2 * R + T * NV + T * NV * mr) +
            sizeof(float) * ((size_t)NV * R4 + (size_t)g.kH * 2 * R * R4);
 }
 
@@ -489,7 +511,7 @@ size_t back_smem(const Geo& g, int R, int NU, int CTp, int mr)
 {
     const size_t T = (size_t)1 << g.kG, R4 = (R + 3) & ~3;
     const size_t XN = T * NU;
-    return sizeof(float2) * (T * R * CTp + (size_t)g.kG * T * 2 * R + XN + (size_t)g.ra * XN + XN * mr) +
+    return sizeof(float2) * (T * R * CTp + 2 * T * 2 * R + XN + XN * mr) +
            sizeof(float) * ((size_t)g.kG * 2 * R * R4 + (size_t)NU * R4);
 }
 
@@ -519,16 +541,31 @@ cudaError_t launch_r(const FrontArgs& fa, const BackArgs& ba, size_t sf, size_t 
 }
 
 // ---------------------------------------------------------------- batched --
+// Out-of-line copies of the tile bodies for the persistent kernel, so that each
+// body gets its own register allocation instead of the union of both.
+template <int R, int NV>
+__device__ __noinline__ void front_tile_ool(const FrontArgs& A, int64_t work, unsigned char* smem)
+{
+    front_tile<R, NV>(A, work, smem);
+}
+template <int R, int NV>
+__device__ __noinline__ void back_tile_ool(const BackArgs& A, int64_t work, unsigned char* smem)
+{
+    back_tile<R, NV>(A, work, smem);
+}
+
 // One persistent launch over the front and back tiles of many operators.
-// Work items are handed out by an atomic counter, all front items first, so
-// every front item is claimed (by a running CTA) before any back item is; a
-// back item of operator i waits until all front items of i are done (bounded
-// spin; on time-out it sets *err and skips the tile).
+// Work items are handed out by an atomic counter in the order
+// [fronts of op 0][backs of op 0][fronts of op 1][backs of op 1]..., so an
+// operator's back tiles follow its front tiles closely (its switch-level
+// workspace is often still in L2) and every front tile is claimed, by a
+// running CTA, before any back tile of the same operator; a back tile waits
+// until all front tiles of its operator are done (bounded spin; on time-out it
+// sets *err and skips the tile).
 template <int R, int NV>
 __global__ void __launch_bounds__(kThreads, 2)
-    batch_f32(const BatchItem* items, int nitems, const int64_t* front_off, const int64_t* back_off,
-              int64_t total_front, int64_t total, unsigned long long* counter, int* done, int* err,
-              long long spin_limit, int wait_extra)
+    batch_f32(const BatchItem* items, int nitems, const int64_t* off, int64_t total, unsigned long long* counter,
+              int* done, int* err, long long spin_limit, int wait_extra)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long s_w;
@@ -539,19 +576,18 @@ __global__ void __launch_bounds__(kThreads, 2)
         const long long w = s_w;
         __syncthreads();
         if (w >= total) break;
-        if (w < total_front) {
-            int i = 0;
-            while (i + 1 < nitems && front_off[i + 1] <= w) ++i;
-            front_tile<R, NV>(items[i].fa, w - front_off[i], smem_raw);
+        int j = 0;  // segment: 2 i = fronts of op i, 2 i + 1 = backs of op i
+        while (j + 1 < 2 * nitems && off[j + 1] <= w) ++j;
+        const int i = j >> 1;
+        const long long local = w - off[j];
+        if ((j & 1) == 0) {
+            front_tile_ool<R, NV>(items[i].fa, local, smem_raw);
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
                 atomicAdd(&done[i], 1);
             }
         } else {
-            const long long w2 = w - total_front;
-            int i = 0;
-            while (i + 1 < nitems && back_off[i + 1] <= w2) ++i;
             if (threadIdx.x == 0) {
                 long long n = 0;
                 int ok = 1;
@@ -567,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 s_ok = ok;
             }
             __syncthreads();
-            if (s_ok) back_tile<R, NV>(items[i].ba, w2 - back_off[i], smem_raw);
+            if (s_ok) back_tile_ool<R, NV>(items[i].ba, local, smem_raw);
         }
     }
 }
@@ -588,9 +624,8 @@ cudaError_t batch_launch_r(const BatchLaunch& bl, cudaStream_t st, bool set_attr
         return cudaSuccess;
     }
     ProfScope ps("batch_f32", st);
-    batch_f32<R, NV><<<bl.grid, kThreads, bl.smem, st>>>(bl.items, bl.nitems, bl.front_off, bl.back_off,
-                                                          bl.total_front, bl.total, bl.counter, bl.done, bl.err,
-                                                          bl.spin_limit, bl.wait_extra);
+    batch_f32<R, NV><<<bl.grid, kThreads, bl.smem, st>>>(bl.items, bl.nitems, bl.off, bl.total, bl.counter, bl.done,
+                                                          bl.err, bl.spin_limit, bl.wait_extra);
     return cudaGetLastError();
 }
 
@@ -603,24 +638,21 @@ FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint)
     const int Tmax = 1 << (g.kG > g.kH ? g.kG : g.kH);
     const int ra = g.ra > 0 ? g.ra : 1;
     const int NV = g.nv;
-    auto fits = [&](int mr) {
+    auto smem = [&](int mr) {
         const int CTp = 1 << ilog2(ra * mr);
-        const size_t tile = (size_t)Tmax * g.r * CTp * sizeof(float2);
-        const size_t fs = (size_t)Tmax * NV * mr * sizeof(float2);
-        return CTp <= 256 && tile + fs <= 112 * 1024;
+        return std::max(front_smem(g, g.r, NV, CTp, mr), back_smem(g, g.r, NV, CTp, mr));
     };
     int mr;
-    if (mr_hint > 0 && (mr_hint & (mr_hint - 1)) == 0 && fits(mr_hint)) {
+    if (mr_hint > 0 && (mr_hint & (mr_hint - 1)) == 0 && (1 << ilog2(ra * mr_hint)) <= 256 &&
+        smem(mr_hint) <= 200 * 1024) {
         mr = mr_hint;
     } else {
         // largest power-of-two mr with at most 512 (group, column) items per level
-        // and a tile plus staged F rows within 80 KB of shared memory
+        // that keeps two CTAs resident per SM (shared memory <= 113 KB)
         mr = 64;
         while (mr > 1) {
             const int CTp = 1 << ilog2(ra * mr);
-            const size_t tile = (size_t)Tmax * g.r * CTp * sizeof(float2);
-            const size_t fs = (size_t)Tmax * NV * mr * sizeof(float2);
-            if ((Tmax / 2) * CTp <= 512 && tile + fs <= 80 * 1024) break;
+            if ((Tmax / 2) * CTp <= 512 && CTp <= 256 && smem(mr) <= 113 * 1024) break;
             mr >>= 1;
         }
         while (mr > 1 && (int64_t)(mr / 2) >= m) mr >>= 1;
