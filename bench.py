@@ -42,8 +42,9 @@ WORKLOADS = {
                    desc="serving: Poisson arrivals (mean 2000 req/s) against 4 resident operators N=2^14,2^16,2^18,2^20 "
                         "of the fio2 kernel, m uniform in {1,4,16,64}, host buffers, continuous batching on 4 slots, "
                         "complex FP32; compared with the plain per-request FP64 form"),
-    "fio3": dict(N=262144, m=256, phase=2, amp=1, eps=1e-6, prec="f32", split=2,
-                 desc="piecewise FIO (jump at x=1/2), N=262144 as four N/2 sub-BFs, m=256, complex FP32 apply"),
+    "fio3": dict(N=262144, m=256, phase=2, amp=1, eps=1e-4, prec="bf16x3", split=2,
+                 desc="piecewise FIO (jump at x=1/2), N=262144 as four N/2 sub-BFs, m=256, alpha as fio2, "
+                      "split-BF16 tensor-core apply (hi/lo operands, FP32 accumulation), BF eps=1e-4 (r=8)"),
 }
 
 FP32_LANES_PER_SM = 128
@@ -57,6 +58,27 @@ def load_peaks():
             d = json.load(f)
         return d, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def tensor_flops(info, m, N, split):
+    """Tensor-core FLOPs one launch of front_tc / back_tc issues (all sub-BFs)."""
+    r, l1, ra, L, h = info["r"], info["l1"], info["r_alpha"], info["L"], info["h"]
+    Nb = N // split
+    kH, kG = h - l1, L - l1 - h
+    D2 = 2 * r
+    SLOT = 16 if D2 <= 16 else 32
+    KS = (D2 + 7) // 8 * 8
+    KG, KP = 2 * KS, (D2 + 15) // 16 * 16
+    mr = 128 // ra
+    nslice = -(-m // mr)
+    mma = 2 * 128 * SLOT * 16
+    group = 2 * 3 * (KG // 16) * mma
+    TF, TB = 2 ** kH, 2 ** kG
+    ntile = (2 ** l1) * (2 ** (L - h)) * nslice
+    front = ntile * (kH * (TF // 2) * group + TF * 3 * (KP // 16) * mma)
+    back = (2 ** h) * nslice * (2 ** l1) * kG * (TB // 2) * group
+    nblk = split * split
+    return {"front_tc": front * nblk, "back_tc": back * nblk}
 
 
 def algorithmic(info, m, N, split):
@@ -441,7 +463,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fio2", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default=None, choices=["f32", "f64"])
+    ap.add_argument("--prec", default=None, choices=["f32", "f64", "bf16x3"])
+    ap.add_argument("--eps", type=float, default=None, help="override the BF tolerance of the workload")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -449,6 +472,8 @@ def main():
     w = dict(WORKLOADS[args.workload])
     if args.prec:
         w["prec"] = args.prec
+    if args.eps:
+        w["eps"] = args.eps
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -477,7 +502,7 @@ def main():
             dist.barrier()
 
     N, m = w["N"], w["m"]
-    prec = api.F64 if w["prec"] == "f64" else api.F32
+    prec = {"f64": api.F64, "f32": api.F32, "bf16x3": api.BF16X3}[w["prec"]]
     cdt = torch.complex128 if prec == api.F64 else torch.complex64
     t0 = time.perf_counter()
     plan = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local)
@@ -535,6 +560,20 @@ def main():
                 "kernel_ms": {k: v[1] / v[0] for k, v in kt.result.items()},
                 "share": {k: v[1] / sum(x[1] for x in kt.result.values()) for k, v in kt.result.items()}}
         _ = nblk
+    elif prec == api.BF16X3 and "front_tc" in kt.result:
+        tflops = tensor_flops(info, m, N, w["split"])
+        tot = sum(v[1] for v in kt.result.values())
+        dom = max(("front_tc", "back_tc"), key=lambda k: kt.result[k][1])
+        n_l, t_l = kt.result[dom]
+        achieved = tflops[dom] / (t_l / n_l * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
+                "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops_sustained"],
+                "traffic": ncu_traffic(dom, args.workload),
+                "note": "tensor FLOPs issued (3 BF16 products per split product, zero padding to the MMA shape); "
+                        "peak: sustained cuBLAS BF16 (%s)" % peak_src,
+                "useful_alu_frac": (front + back) / (tot / n_l * 1e-3) / 1e12 / alu_peak,
+                "kernel_ms": {k: v[1] / v[0] for k, v in kt.result.items()},
+                "share": {k: v[1] / tot for k, v in kt.result.items()}}
     elif kt.result:
         tot = sum(v[1] for v in kt.result.values())
         dom = max(kt.result, key=lambda k: kt.result[k][1])
@@ -580,7 +619,7 @@ def main():
             cfg["rel_err_rows"] = cpu.pop("rows_compared")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == api.F64 else "f32",
+                "scaling": "weak", "vs_baseline": None, "dtype": {api.F64: "f64", api.F32: "f32", api.BF16X3: "bf16x3"}[prec],
                 "data": "synthetic (seeded complex Gaussian F; analytic kernel)", "config": cfg,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary()}

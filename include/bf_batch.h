@@ -4,11 +4,11 @@
  *
  * A batch applies many operators g_i = K_i f_i (each a plan of bf.h, of its own
  * N_i, with its own m_i right-hand sides) in ONE persistent launch: every CTA
- * takes work items -- the front tiles (V, H levels, switch) and back tiles (G
- * levels, U) of all operators -- from an atomic counter; a back tile of
- * operator i waits (bounded) until all front tiles of i are finished.  Each
- * operator computes exactly what bf_apply(plan_i, BF_PREC_F32, ...) computes,
- * bit for bit.  The paper applies one operator to one vector at a time
+ * takes work items from an atomic counter in the order [front tiles of op 0]
+ * [back tiles of op 0] [front tiles of op 1] ... (front = V, H levels and
+ * switch; back = G levels and U); a back tile of operator i waits (bounded)
+ * until all front tiles of i are finished.  Each operator computes exactly
+ * what bf_apply(plan_i, BF_PREC_F32, ...) computes, bit for bit.  The paper applies one operator to one vector at a time
  * (Sec. 5); batching is this library's addition, resting on the footnote of
  * Sec. 1 that the precomputed factorisation is reused across many f.
  */

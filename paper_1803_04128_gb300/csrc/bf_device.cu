@@ -236,6 +236,7 @@ bf_status device_reserve(bf_plan* p, bf_precision prec, int64_t m, void*)
     size_t need = 0;
     for (auto& B : ds->blocks) {
         if (prec == BF_PREC_F64) need = std::max(need, 2 * plain_f64_ws_bytes(B.g, m));
+        else if (prec == BF_PREC_BF16X3) need = std::max(need, tc_ws_bytes(B.g, m));
         else need = std::max(need, fused_f32_ws_bytes(B.g, m, p->mr_hint(m)));
     }
     if (need == 0) need = 256;
@@ -248,8 +249,13 @@ bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, 
     DeviceState* ds = p->dev;
     cudaStream_t st = (cudaStream_t)stream;
     if (prec == BF_PREC_BF16X3) {
-        set_error("bf_apply: BF_PREC_BF16X3 not available in this build");
-        return BF_ERR_UNSUPPORTED;
+        for (auto& B : ds->blocks) {
+            const char* why = "";
+            if (!tc_supported(B.g, &why)) {
+                set_error("bf_apply: BF_PREC_BF16X3: %s (r=%d, kH=%d, kG=%d)", why, B.g.r, B.g.kH, B.g.kG);
+                return BF_ERR_UNSUPPORTED;
+            }
+        }
     }
     if (prec == BF_PREC_F32) {
         for (auto& B : ds->blocks)
@@ -270,6 +276,9 @@ bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, 
             double2* Gb = (double2*)G + B.row0 * m;
             const size_t half = ds->ws64_bytes / 2 / sizeof(double2);
             e = launch_plain_f64(B, Fb, m, Gb, beta, (double2*)ds->ws64, (double2*)ds->ws64 + half, st);
+        } else if (prec == BF_PREC_BF16X3) {
+            e = launch_tc(B, (const float2*)F + B.col0 * m, m, (float2*)G + B.row0 * m, beta, (float2*)ds->ws32,
+                          ds->err, st);
         } else {
             const float2* Fb = (const float2*)F + B.col0 * m;
             float2* Gb = (float2*)G + B.row0 * m;
@@ -288,6 +297,7 @@ size_t device_ws_bytes(const bf_plan* p, bf_precision prec, int64_t m)
     size_t need = 0;
     for (auto& B : p->dev->blocks) {
         if (prec == BF_PREC_F64) need = std::max(need, 2 * plain_f64_ws_bytes(B.g, m));
+        else if (prec == BF_PREC_BF16X3) need = std::max(need, tc_ws_bytes(B.g, m));
         else need = std::max(need, fused_f32_ws_bytes(B.g, m, p->mr_hint(m)));
     }
     return need == 0 ? 256 : need;
@@ -299,8 +309,13 @@ bf_status device_apply_ws(bf_plan* p, bf_precision prec, const void* F, int64_t 
     DeviceState* ds = p->dev;
     cudaStream_t st = (cudaStream_t)stream;
     if (prec == BF_PREC_BF16X3) {
-        set_error("BF_PREC_BF16X3 not available in this build");
-        return BF_ERR_UNSUPPORTED;
+        for (auto& B : ds->blocks) {
+            const char* why = "";
+            if (!tc_supported(B.g, &why)) {
+                set_error("BF_PREC_BF16X3: %s", why);
+                return BF_ERR_UNSUPPORTED;
+            }
+        }
     }
     if (ws_bytes < device_ws_bytes(p, prec, m)) {
         set_error("workspace of %zu bytes too small (%zu needed)", ws_bytes, device_ws_bytes(p, prec, m));
@@ -315,6 +330,8 @@ bf_status device_apply_ws(bf_plan* p, bf_precision prec, const void* F, int64_t 
             const size_t half = ws_bytes / 2 / sizeof(double2);
             e = launch_plain_f64(B, (const double2*)F + B.col0 * m, m, (double2*)G + B.row0 * m, beta, (double2*)ws,
                                  (double2*)ws + half, st);
+        } else if (prec == BF_PREC_BF16X3) {
+            e = launch_tc(B, (const float2*)F + B.col0 * m, m, (float2*)G + B.row0 * m, beta, (float2*)ws, ds->err, st);
         } else {
             e = launch_fused_f32(B, (const float2*)F + B.col0 * m, m, (float2*)G + B.row0 * m, beta, (float2*)ws, st,
                                  p->mr_hint(m));

@@ -81,6 +81,12 @@ cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, floa
                              float2* ws, cudaStream_t st, int mr_hint = 0);
 bool fused_f32_supported(int r);
 
+// Split-BF16 tensor-core apply (bf_kernels_tc.cu)
+bool tc_supported(const Geo& g, const char** why);
+size_t tc_ws_bytes(const Geo& g, int64_t m);
+cudaError_t launch_tc(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int* err,
+                      cudaStream_t st);
+
 // per-launch event timing (bf_profile_*); no-ops unless profiling is on
 void prof_start(const char* name, cudaStream_t st, void** tok);
 void prof_stop(void* tok, cudaStream_t st);

@@ -166,3 +166,49 @@ def test_bad_calls_return_errors():
     assert lib.bf_apply(plan._h, api.F32, ctypes.c_void_p(F.data_ptr()), 2, ctypes.c_void_p(F.data_ptr()), s) == L.BF_ERR_ARG
     assert lib.bf_apply(plan._h, 7, ctypes.c_void_p(F.data_ptr()), 2, ctypes.c_void_p(F.data_ptr() + 64), s) == L.BF_ERR_ARG
     assert lib.bf_apply(None, api.F32, ctypes.c_void_p(F.data_ptr()), 2, ctypes.c_void_p(F.data_ptr() + 64), s) == L.BF_ERR_ARG
+
+
+# ------------------------------------------------------ split-BF16 path ----
+# Tolerance: operands are split x = hi + lo in BF16 (8-bit significands), so
+# hi + lo carries x to about 2^-16 relative; the dropped lo*lo term is
+# ~2^-18; with unit-modulus phases and Lagrange weights of Lebesgue constant
+# ~3 over <= 2L+3 stages this gives ~1e-5 .. 1e-4; 3e-4 against Algorithm 4.1
+# and the stated 1e-3 against the direct oracle.
+@pytest.mark.parametrize("N,r,m", [(1024, 8, 3), (4096, 10, 5), (16384, 8, 64), (8192, 12, 2), (2048, 10, 130)])
+def test_bf16x3_matches_algorithm_4_1(N, r, m):
+    plan = api.Plan(N, r=r, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(N, m, seed=N + r)
+    cols = slice(0, min(m, 4))
+    ref = oracle_ibf(L.PHASE_FIO, N, F[:, cols], r, 1)
+    g = run(plan, F, api.BF16X3)
+    assert relerr(g[:, cols], ref) < 3e-4
+    assert relerr(g, run(plan, F, api.F32)) < 3e-4
+
+
+def test_bf16x3_full_size_config2_sampled():
+    N, m = 65536, 64
+    plan = api.Plan(N, eps=1e-6, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(N, m, seed=0)
+    g = run(plan, F, api.BF16X3)
+    rows = inputs.sample_rows(N, 64, seed=0)
+    gd = od.direct(od.FIO, N, F[:, :16], rows, amp=1)
+    assert relerr(g[rows, :16], gd) < 1e-3
+
+
+def test_bf16x3_config3_shape_r8_split():
+    # piecewise phase, N = 262144 as four N/2 sub-BFs, r = 8: back tiles of 32 pairs
+    N, m = 262144, 4
+    plan = api.Plan(N, r=8, phase_kind=L.PHASE_FIO_PW, amp_kind=L.AMP_SMOOTH, split=2)
+    F = inputs.complex_gaussian(N, m, seed=0)
+    g = run(plan, F, api.BF16X3)
+    rows = np.concatenate([inputs.sample_rows(N // 2, 16, seed=1), N // 2 + inputs.sample_rows(N // 2, 16, seed=2)])
+    gd = od.direct(od.FIOPW, N, F, rows, amp=1)
+    assert relerr(g[rows], gd) < 1e-3
+
+
+def test_bf16x3_refuses_tiles_that_do_not_fit():
+    plan = api.Plan(262144, r=10, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH, split=2)
+    F = torch.zeros((262144, 1), dtype=torch.complex64, device="cuda")
+    with pytest.raises(L.BFError) as e:
+        plan.apply(F, prec=api.BF16X3)
+    assert e.value.status == L.BF_ERR_UNSUPPORTED
