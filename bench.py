@@ -153,9 +153,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_hash():
+KERNEL_SOURCES = {"f32": ("bf_kernels_f32.cu",), "tc": ("bf_kernels_tc.cu", "bf_tc.h"), "f64": ("bf_kernels_f64.cu",)}
+
+
+def kernel_hash(kernel):
+    """Hash of the source file(s) of a kernel family ('front_f32' -> f32, 'back_tc' -> tc, ...)."""
+    fam = "tc" if kernel.endswith("_tc") else ("f64" if kernel.endswith("_f64") else "f32")
     h = hashlib.sha256()
-    for f in ("bf_kernels_f32.cu", "bf_kernels_f64.cu"):
+    for f in KERNEL_SOURCES[fam]:
         with open(os.path.join(ROOT, "paper_1803_04128_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -170,7 +175,7 @@ def ncu_traffic(kernel, workload):
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload, {}).get(kernel)
-    if not e or e.get("kernel_hash") != kernel_hash():
+    if not e or e.get("kernel_hash") != kernel_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
