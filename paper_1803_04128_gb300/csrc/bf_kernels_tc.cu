@@ -8,14 +8,20 @@
 //    holds, for each of the 128 right-hand-side rows (TMEM lanes), the 2r
 //    real components (t, re/im) in columns [s * SLOT, s * SLOT + 2r);
 //  * a level group (two input pairs -> two output pairs) is one dense complex
-//    2r x 2r block W, built on the fly in shared memory from the factored
-//    form (the real Lagrange matrix of the level times the pair's phases) as
-//    its real embedding [[Re W, -Im W], [Im W, Re W]];
+//    2r x 2r block per output pair, built on the fly in shared memory from the
+//    factored form (the real Lagrange matrix of the level times the pair's
+//    phases) as its real embedding [[Re W, -Im W], [Im W, Re W]];
+//  * the two output pairs of a group occupy adjacent slots (a "region"), so a
+//    group is one MMA chain with N = 2 SLOT.  Two groups that read the same two
+//    regions form a unit and write their outputs back over those regions (the
+//    butterfly's radix-2 crossing), so the update stays in place: after level
+//    j, logical slot s lives in region compress_{j-1}(s) (s with bit j-1
+//    removed), half bit_{j-1}(s);
 //  * operands are split x = hi + lo into BF16 (hi = bf16(x), lo = bf16(x - hi));
 //    D = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in FP32 in TMEM by
-//    tcgen05.mma (M = 128 rows, N = SLOT, K = 16 per instruction), issued by
-//    one thread and tracked by an mbarrier;
-//  * D is written in place over the two input slots it consumed.
+//    tcgen05.mma (M = 128 rows, K = 16 per instruction), issued by one thread;
+//  * 16 builder warps write operands into two double-buffered item buffers and
+//    one issuer thread runs the MMAs; ready / done mbarriers hand items over.
 //
 // Rows are right-hand-side columns interleaved with amplitude terms:
 // row = c * r_alpha + k (RHS c of the slice, amplitude term k), so the sum
@@ -29,7 +35,9 @@
 namespace bfi {
 namespace {
 
-constexpr int kTcThreads = 288;  // 8 builder warps + 1 MMA-issue warp
+constexpr int kBuilders = 512;                 // 16 builder warps
+constexpr int kTcThreads = kBuilders + 32;     // + 1 MMA-issue warp
+constexpr int NBUF = 2;                        // item buffers in flight
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b)
 {
@@ -47,11 +55,15 @@ __device__ __forceinline__ void cp8(void* dst, const void* src)
     unsigned s = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_commit_wait()
+// 8-byte copy that writes zeros instead when !valid (nothing is read then)
+__device__ __forceinline__ void cp8z(void* dst, const void* src, bool valid)
 {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(src), "r"(valid ? 8 : 0) : "memory");
 }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
 __device__ __forceinline__ void stage_matrix(float* dst, const float* src, int rows, int cols, int c4, int tid)
 {
     const int half = cols / 2;
@@ -64,18 +76,17 @@ __device__ __forceinline__ void stage_matrix(float* dst, const float* src, int r
 template <int R>
 struct Shape {
     static constexpr int D2 = 2 * R;                      // real components per pair
-    static constexpr int SLOT = D2 <= 16 ? 16 : 32;       // TMEM columns per pair = MMA N
-    static constexpr int KS = (D2 + 7) / 8 * 8;           // K rows per input pair in a group
+    static constexpr int SLOT = D2 <= 16 ? 16 : 32;       // TMEM columns per pair
+    static constexpr int NG = 2 * SLOT;                   // MMA N of a group: its two output pairs
+    static constexpr int KS = (D2 + 7) / 8 * 8;           // K rows per input pair
     static constexpr int KG = 2 * KS;                     // K of a group MMA chain
-    static constexpr int KP = (D2 + 15) / 16 * 16;        // K of a single-pair (switch) chain
     static constexpr int R4 = (R + 3) & ~3;
-    static constexpr int SBO = (KG / 8) * 128;            // 8-row-group stride of the operands
+    static constexpr int SBO = (KG / 8) * 128;            // 8-row-group stride of A and B
     static constexpr int A_BYTES = 128 * KG * 2;          // one of A_hi / A_lo
-    static constexpr int B_BYTES = SLOT * KG * 2;         // one B matrix (hi or lo, one output pair)
-    static constexpr int BUF = 2 * A_BYTES + 4 * B_BYTES; // A_hi | A_lo | B_hi0 | B_hi1 | B_lo0 | B_lo1
+    static constexpr int B_BYTES = NG * KG * 2;           // one of B_hi / B_lo
+    static constexpr int GRP = 2 * A_BYTES + 2 * B_BYTES; // A_hi | A_lo | B_hi | B_lo of one group
+    static constexpr int BUF = 2 * GRP;                   // one item: up to two groups
 };
-
-constexpr int NBUF = 4;  // operand buffers in flight between the builders and the MMA issuer
 
 struct TcArgs {
     Geo g;
@@ -105,29 +116,23 @@ __device__ __forceinline__ int opnd_off(int row, int k, int sbo)
     return (row >> 3) * sbo + (k >> 3) * 128 + (row & 7) * 16;  // byte offset of the 8-value chunk of (row, k)
 }
 
-// Warps 0..7 build operands ("builders"); warp 8 issues the MMAs.  Hand-over
-// per double-buffer b: ready[b] (256 builder arrivals: operands of the item in
-// b written) and done[b] (tcgen05.commit: its MMAs finished).
-constexpr int kBuilders = 256;
-
-__device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, 256;\n" ::: "memory"); }
+__device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, 512;\n" ::: "memory"); }
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tc::smem_u32(mbar)) : "memory");
 }
 
-// A of a level group: this thread converts its row of input slot hw (K offset hw * KS)
+// A of one group: this thread converts its row of one input pair (TMEM column
+// tcol) into K columns [c KS, c KS + KS) of A_hi and A_lo (zero padded)
 template <int R>
-__device__ __forceinline__ void build_A_group(unsigned char* buf, uint32_t tlane, int s0, int s1, int hw, int row)
+__device__ __forceinline__ void build_A(unsigned char* grp, uint32_t taddr, int c, int row)
 {
     using S = Shape<R>;
     float v[S::KS];
 #pragma unroll
     for (int d = S::D2; d < S::KS; ++d) v[d] = 0.f;
-    tc::ld_dims<S::D2>(tlane + (uint32_t)((hw ? s1 : s0) * S::SLOT), v);
+    tc::ld_dims<S::D2>(taddr, v);
     tc::wait_ld();
-    unsigned char* Ah = buf;
-    unsigned char* Al = buf + S::A_BYTES;
 #pragma unroll
     for (int ch = 0; ch < S::KS / 8; ++ch) {
         uint4 h, l;
@@ -135,41 +140,18 @@ __device__ __forceinline__ void build_A_group(unsigned char* buf, uint32_t tlane
         tc::split2(v[8 * ch + 2], v[8 * ch + 3], h.y, l.y);
         tc::split2(v[8 * ch + 4], v[8 * ch + 5], h.z, l.z);
         tc::split2(v[8 * ch + 6], v[8 * ch + 7], h.w, l.w);
-        const int off = opnd_off(row, hw * S::KS + 8 * ch, S::SBO);
-        *reinterpret_cast<uint4*>(Ah + off) = h;
-        *reinterpret_cast<uint4*>(Al + off) = l;
+        const int off = opnd_off(row, c * S::KS + 8 * ch, S::SBO);
+        *reinterpret_cast<uint4*>(grp + off) = h;
+        *reinterpret_cast<uint4*>(grp + S::A_BYTES + off) = l;
     }
 }
 
-// A of a single pair (switch), same operand layout, K = KP; builder warps of half 0
+// One 16-byte chunk of B (hi and lo): B row n of the real embedding of four
+// consecutive complex weights w[0..3] at K offset k0 (a multiple of 8).  Output
+// component rho = 2t (real part of output t) holds (Re w, -Im w) per weight,
+// rho = 2t + 1 (imaginary part) holds (Im w, Re w).
 template <int R>
-__device__ __forceinline__ void build_A_single(unsigned char* buf, uint32_t tlane, int slot, int row)
-{
-    using S = Shape<R>;
-    float v[S::KP];
-#pragma unroll
-    for (int d = S::D2; d < S::KP; ++d) v[d] = 0.f;
-    tc::ld_dims<S::D2>(tlane + (uint32_t)(slot * S::SLOT), v);
-    tc::wait_ld();
-#pragma unroll
-    for (int ch = 0; ch < S::KP / 8; ++ch) {
-        uint4 h, l;
-        tc::split2(v[8 * ch + 0], v[8 * ch + 1], h.x, l.x);
-        tc::split2(v[8 * ch + 2], v[8 * ch + 3], h.y, l.y);
-        tc::split2(v[8 * ch + 4], v[8 * ch + 5], h.z, l.z);
-        tc::split2(v[8 * ch + 6], v[8 * ch + 7], h.w, l.w);
-        const int off = opnd_off(row, 8 * ch, S::SBO);
-        *reinterpret_cast<uint4*>(buf + off) = h;
-        *reinterpret_cast<uint4*>(buf + S::A_BYTES + off) = l;
-    }
-}
-
-// One 16-byte chunk of B (hi and lo): row rho of the real embedding of four
-// consecutive complex weights w[0..3] at K offset k0 (a multiple of 8).  Row
-// 2t (real part of output t) holds (Re w, -Im w) per weight, row 2t + 1 (the
-// imaginary part) holds (Im w, Re w).
-template <int R>
-__device__ __forceinline__ void put_chunk(unsigned char* Bh, unsigned char* Bl, int rho, int k0, const float2* w)
+__device__ __forceinline__ void put_chunk(unsigned char* Bh, unsigned char* Bl, int n, int rho, int k0, const float2* w)
 {
     using S = Shape<R>;
     uint4 h, l;
@@ -184,93 +166,158 @@ __device__ __forceinline__ void put_chunk(unsigned char* Bh, unsigned char* Bl, 
         tc::split2(w[2].y, w[2].x, h.z, l.z);
         tc::split2(w[3].y, w[3].x, h.w, l.w);
     }
-    const int off = opnd_off(rho, k0, S::SBO);
+    const int off = opnd_off(n, k0, S::SBO);
     *reinterpret_cast<uint4*>(Bh + off) = h;
     *reinterpret_cast<uint4*>(Bl + off) = l;
 }
 
-// B of a level group: two matrices (output pairs s = 0, 1).  Item = (row rho,
-// input pair c, chunk q of four weights s' = 4q..4q+3, output pair s); weights
-// with s' >= r are the zero padding of K.
+// Items of the B of one group: (component rho, input pair c, chunk q, output pair s)
+template <int R>
+struct BItems {
+    static constexpr int NQ = Shape<R>::KS / 8;
+    static constexpr int N = Shape<R>::D2 * NQ * 4;
+};
+
+// B of a level group, item it of BItems: weights with s' >= r are the K padding.
 // kind 0 (H, Eq. 2): W_s[t][(c, s')] = MH[t][c r + s'] * E_s[c][s'].
 // kind 1 (G, Eq. 3): W_s[t][(c, s')] = FG_s[c][t] * MG_s[t][s'].
+// kind 2 (switch):   W_s[t][(c, s')] = [c == s] S_s[t][s']  (two pairs, block diagonal).
 template <int R, int KIND>
-__device__ __forceinline__ void build_B_group(unsigned char* buf, const float* Mt, const float2* P0, const float2* P1,
-                                              int tid)
+__device__ __forceinline__ void build_B_item(unsigned char* grp, int it, const float* Mt, const float2* P0,
+                                             const float2* P1)
 {
     using S = Shape<R>;
-    constexpr int NQ = S::KS / 8;
-    constexpr int ITEMS = S::D2 * NQ * 4;
-    unsigned char* Bh = buf + 2 * S::A_BYTES;
-    unsigned char* Bl = Bh + 2 * S::B_BYTES;
-    for (int it = tid; it < ITEMS; it += kBuilders) {
-        const int rho = it % S::D2;
-        const int rest = it / S::D2;
-        const int q = rest % NQ;
-        const int c = (rest / NQ) & 1;
-        const int s = rest / (2 * NQ);
-        const int t = rho >> 1;
-        const float2* Pp = s ? P1 : P0;
-        float2 w[4];
+    constexpr int NQ = BItems<R>::NQ;
+    const int rho = it % S::D2;
+    const int rest = it / S::D2;
+    const int q = rest % NQ;
+    const int c = (rest / NQ) & 1;
+    const int s = rest / (2 * NQ);
+    const int t = rho >> 1;
+    const float2* Pp = s ? P1 : P0;
+    float2 w[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int sp = 4 * q + e;
-            if (sp < R) {
-                float mv;
-                float2 ph;
-                if (KIND == 0) {
-                    mv = Mt[(c * R + sp) * S::R4 + t];
-                    ph = Pp[c * R + sp];
-                } else {
-                    mv = Mt[(s * R + sp) * S::R4 + t];
-                    ph = Pp[c * R + t];
-                }
+    for (int e = 0; e < 4; ++e) {
+        const int sp = 4 * q + e;
+        w[e] = make_float2(0.f, 0.f);
+        if (sp < R) {
+            if (KIND == 0) {
+                const float mv = Mt[(c * R + sp) * S::R4 + t];
+                const float2 ph = Pp[c * R + sp];
                 w[e] = make_float2(mv * ph.x, mv * ph.y);
-            } else {
-                w[e] = make_float2(0.f, 0.f);
+            } else if (KIND == 1) {
+                const float mv = Mt[(s * R + sp) * S::R4 + t];
+                const float2 ph = Pp[c * R + t];
+                w[e] = make_float2(mv * ph.x, mv * ph.y);
+            } else if (c == s) {
+                w[e] = Pp[t * R + sp];
             }
         }
-        put_chunk<R>(Bh + s * S::B_BYTES, Bl + s * S::B_BYTES, rho, c * S::KS + 8 * q, w);
     }
+    unsigned char* Bh = grp + 2 * S::A_BYTES;
+    put_chunk<R>(Bh, Bh + S::B_BYTES, s * S::SLOT + rho, rho, c * S::KS + 8 * q, w);
 }
 
-// B of the switch of one pair: W[t][s'] = S[t][s'] (complex, staged in shared memory)
-template <int R>
-__device__ __forceinline__ void build_B_switch(unsigned char* buf, const float2* Sq, int tid)
+// ----------------------------------------------------------- schedule ----
+// One pass over a tile of T = 2^K pairs: levels j = 1..K, then (front only) the
+// switch as pass j = K + 1.  A pass has T / (2 UG) items ("units") of UG groups
+// (UG = 2, or 1 when T = 2).  Physical slot of logical slot s after level j >= 1
+// (and before level 1): 2 compress_{j-1}(s) + bit_{j-1}(s); level j >= 2 unit
+// (hi, lo) reads regions R1 = (hi << (j-1)) | lo and R2 = R1 | 2^{j-2}; its
+// group g takes half g of both and writes region g ? R2 : R1.
+struct UnitGroup {
+    int src0, src1;  // physical slots of input pairs c = 0, 1
+    int dst;         // region written (physical slots 2 dst, 2 dst + 1)
+    int p0, p1;      // output pairs' phase rows (levels) or logical pairs (switch)
+};
+
+__device__ __forceinline__ UnitGroup unit_group(int K, int j, int UG, int u, int g)
 {
-    using S = Shape<R>;
-    constexpr int NQ = (R + 3) / 4;
-    unsigned char* Bh = buf + 2 * S::A_BYTES;
-    unsigned char* Bl = Bh + 2 * S::B_BYTES;
-    for (int it = tid; it < S::D2 * NQ; it += kBuilders) {
-        const int rho = it % S::D2, q = it / S::D2, t = rho >> 1;
-        float2 w[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int sp = 4 * q + e;
-            w[e] = sp < R ? Sq[t * R + sp] : make_float2(0.f, 0.f);
+    UnitGroup G;
+    if (j == 1 || j == K + 1) {
+        const int rg = UG * u + g;
+        G.src0 = 2 * rg;
+        G.src1 = 2 * rg + 1;
+        G.dst = rg;
+        if (j == 1) {
+            G.p0 = rg;
+            G.p1 = (1 << (K - 1)) + rg;
+        } else {
+            G.p0 = (int)brev((unsigned)rg, K);
+            G.p1 = G.p0 + 1;
         }
-        put_chunk<R>(Bh, Bl, rho, 8 * q, w);
+    } else {
+        const int lo = u & ((1 << (j - 2)) - 1), hi = u >> (j - 2);
+        const int R1 = (hi << (j - 1)) | lo, R2 = R1 | (1 << (j - 2));
+        G.src0 = 2 * R1 + g;
+        G.src1 = 2 * R2 + g;
+        G.dst = g ? R2 : R1;
+        const int a = (int)brev((unsigned)lo, j - 1) + g, half = 1 << (K - j);
+        G.p0 = (2 * a) * half + hi;
+        G.p1 = (2 * a + 1) * half + hi;
     }
+    return G;
 }
 
-// matrix descriptors of one buffer: A_hi, A_lo, B_hi(s = 0, 1), B_lo(s = 0, 1); k-step ks adds 256 bytes
+// unit of pass j that wrote region R
+__device__ __forceinline__ int region_writer(int j, int UG, int R)
+{
+    if (j == 1) return R / UG;
+    return ((R >> (j - 1)) << (j - 2)) | (R & ((1 << (j - 2)) - 1));
+}
+
+// latest unit of pass j - 1 whose output unit u of pass j reads (-1: none)
+__device__ __forceinline__ int unit_dep(int K, int j, int UG, int u)
+{
+    if (j == 1) return -1;
+    int dep = -1;
+    for (int g = 0; g < UG; ++g) {
+        const UnitGroup G = unit_group(K, j, UG, u, g);
+        dep = max(dep, region_writer(j - 1, UG, G.src0 >> 1));
+        dep = max(dep, region_writer(j - 1, UG, G.src1 >> 1));
+    }
+    return dep;
+}
+
+// physical slot of logical slot s after the last level K
+__device__ __forceinline__ int phys_final(int K, int s)
+{
+    return 2 * (s & ((1 << (K - 1)) - 1)) + (s >> (K - 1));
+}
+
+// ----------------------------------------------------------- hand-over ---
+// completion of item i (buffer i % NBUF, its (i / NBUF)-th use).  Callers wait
+// only for i >= n - NBUF (n = item about to be built), so the barrier is at most
+// one phase past the awaited one.
+__device__ __forceinline__ bool wait_item(uint64_t* done, int i, long long spin)
+{
+    if (i < 0) return true;
+    const bool ok = tc::mbar_wait(&done[i % NBUF], (uint32_t)((i / NBUF) & 1), spin);
+    tc::fence_after();
+    return ok;
+}
+
+__device__ __forceinline__ void publish(uint64_t* ready, int n)
+{
+    tc::fence_async_smem();
+    tc::fence_before();
+    mbar_arrive(&ready[n % NBUF]);
+}
+
 template <int R>
 struct BufDesc {
-    uint64_t ah, al, bh0, bh1, bl0, bl1;
+    uint64_t ah, al, bh, bl;  // group 0 of buffer 0; group g of buffer b adds (b BUF + g GRP) / 16
     __device__ void init(const unsigned char* buf)
     {
         using S = Shape<R>;
         ah = tc::desc(buf, 128, S::SBO);
         al = tc::desc(buf + S::A_BYTES, 128, S::SBO);
-        bh0 = tc::desc(buf + 2 * S::A_BYTES, 128, S::SBO);
-        bh1 = tc::desc(buf + 2 * S::A_BYTES + S::B_BYTES, 128, S::SBO);
-        bl0 = tc::desc(buf + 2 * S::A_BYTES + 2 * S::B_BYTES, 128, S::SBO);
-        bl1 = tc::desc(buf + 2 * S::A_BYTES + 3 * S::B_BYTES, 128, S::SBO);
+        bh = tc::desc(buf + 2 * S::A_BYTES, 128, S::SBO);
+        bl = tc::desc(buf + 2 * S::A_BYTES + S::B_BYTES, 128, S::SBO);
     }
 };
 
-// D(d_tmem) = A_hi B_hi + A_hi B_lo + A_lo B_hi over K
+// D(d_tmem) = A_hi B_hi + A_hi B_lo + A_lo B_hi over K; a k-step adds 256 bytes (16 in the address field)
 __device__ __forceinline__ void issue_chain(uint32_t d_tmem, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl, int K,
                                             uint32_t idesc)
 {
@@ -280,85 +327,74 @@ __device__ __forceinline__ void issue_chain(uint32_t d_tmem, uint64_t ah, uint64
     for (int ks = 0; ks < nks; ++ks) tc::mma_bf16(d_tmem, al + 16 * ks, bh + 16 * ks, idesc, 1);
 }
 
-__device__ __forceinline__ void group_slots(int K, int j, int grp, int& s0, int& s1, int& lo0, int& lo1)
-{
-    const int kj = K - j, half = 1 << kj;
-    const int a = grp >> kj, bp = grp & (half - 1);
-    s0 = (bp << j) + (int)brev((unsigned)a, j - 1);
-    s1 = s0 + (1 << (j - 1));
-    lo0 = (2 * a) * half + bp;      // logical output pairs (phase rows)
-    lo1 = (2 * a + 1) * half + bp;
-}
-
-// builder-side pipeline bookkeeping (identical in every builder thread)
-struct BPipe {
-    int n;       // items handed over so far
-    bool ok;
-};
-
-// completion of item i (buffer i % NBUF, its (i / NBUF)-th use); a no-op for i < 0.  The
-// barrier cannot be two phases past the awaited one: item i + NBUF is built only
-// after every builder has passed this wait.
-__device__ __forceinline__ void builders_wait_item(uint64_t* done, int item, long long spin, bool& ok)
-{
-    if (item < 0) return;
-    ok = tc::mbar_wait(&done[item % NBUF], (uint32_t)((item / NBUF) & 1), spin) && ok;
-}
-
-// builders: acquire the buffer of item n (its previous use finished) and, at a
-// level start, the previous item's outputs (one commit covers all earlier MMAs)
-__device__ __forceinline__ unsigned char* builders_begin(unsigned char* bufs, int BUF, uint64_t* done, BPipe& bp,
-                                                         bool level_start, long long spin)
-{
-    if (level_start) builders_wait_item(done, bp.n - 1, spin, bp.ok);
-    else builders_wait_item(done, bp.n - NBUF, spin, bp.ok);
-    tc::fence_after();
-    return bufs + (bp.n % NBUF) * BUF;
-}
-__device__ __forceinline__ void builders_end(uint64_t* ready, BPipe& bp)
-{
-    tc::fence_async_smem();
-    tc::fence_before();
-    mbar_arrive(&ready[bp.n % NBUF]);
-    ++bp.n;
-}
-__device__ __forceinline__ void builders_drain(uint64_t* done, BPipe& bp, long long spin)
-{
-    builders_wait_item(done, bp.n - 1, spin, bp.ok);
-    tc::fence_after();
-}
-
-// issuer: wait for the operands of item n, issue, commit; buffer b's descriptors are
-// buffer 0's plus b * BUF / 16 in the address field (shared addresses stay below 2^18)
+// issuer: for every item of passes 1..npass (shared addresses stay below 2^18,
+// so descriptor offsets add without carry)
 template <int R>
-__device__ __forceinline__ bool issuer_item(uint64_t* ready, uint64_t* done, const BufDesc<R>& bd, int n, bool pair,
-                                            uint32_t d0, uint32_t d1, long long spin)
+__device__ __forceinline__ bool issue_passes(uint64_t* ready, uint64_t* done, const BufDesc<R>& bd, int& n, int K,
+                                             int npass, int UG, uint32_t tbase, long long spin)
 {
     using S = Shape<R>;
-    const int b = n % NBUF;
-    const uint64_t o = (uint64_t)(b * (S::BUF >> 4));
-    const bool ok = tc::mbar_wait(&ready[b], (uint32_t)((n / NBUF) & 1), spin);
-    tc::fence_after();
-    constexpr uint32_t id = tc::idesc_bf16(128, S::SLOT);
-    if (pair) {
-        issue_chain(d0, bd.ah + o, bd.al + o, bd.bh0 + o, bd.bl0 + o, S::KG, id);
-        issue_chain(d1, bd.ah + o, bd.al + o, bd.bh1 + o, bd.bl1 + o, S::KG, id);
-    } else {
-        issue_chain(d0, bd.ah + o, bd.al + o, bd.bh0 + o, bd.bl0 + o, S::KP, id);
-    }
-    tc::commit(&done[b]);
+    constexpr uint32_t id = tc::idesc_bf16(128, S::NG);
+    const int nunit = (1 << K) / (2 * UG);
+    bool ok = true;
+    for (int j = 1; j <= npass; ++j)
+        for (int u = 0; u < nunit; ++u, ++n) {
+            const int b = n % NBUF;
+            ok = tc::mbar_wait(&ready[b], (uint32_t)((n / NBUF) & 1), spin) && ok;
+            tc::fence_after();
+            for (int g = 0; g < UG; ++g) {
+                const UnitGroup G = unit_group(K, j, UG, u, g);
+                const uint64_t o = (uint64_t)((b * S::BUF + g * S::GRP) >> 4);
+                issue_chain(tbase + (uint32_t)(G.dst * S::NG), bd.ah + o, bd.al + o, bd.bh + o, bd.bl + o, S::KG, id);
+            }
+            tc::commit(&done[b]);
+        }
     return ok;
 }
 
-// 8-byte copy that writes zeros instead when !valid (nothing is read then)
-__device__ __forceinline__ void cp8z(void* dst, const void* src, bool valid)
+// builders: operands of every item of passes 1..npass; KIND of levels 0 (H) / 1 (G),
+// the switch pass (j = K + 1) uses the pairs' switch matrices Ss[lp][R * R]
+template <int R, int KIND>
+__device__ __forceinline__ bool build_passes(unsigned char* bufs, uint64_t* ready, uint64_t* done, int& n, int K,
+                                             int npass, int UG, uint32_t tlane, const float* Mlev, const float2* Plev,
+                                             const float2* Ss, int tid, int row, int role, long long spin)
 {
-    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(src), "r"(valid ? 8 : 0) : "memory");
+    using S = Shape<R>;
+    constexpr int R4 = S::R4;
+    const int T = 1 << K, nunit = T / (2 * UG);
+    const int ga = role >> 1, ca = role & 1;  // this warp's A work: group ga, input pair ca
+    bool ok = true;
+    const int n0 = n;
+    for (int j = 1; j <= npass; ++j) {
+        const bool sw = j == K + 1;
+        const float* Mt = Mlev + (size_t)(j - 1) * 2 * R * R4;
+        const float2* Pl = Plev + (size_t)(j - 1) * T * S::D2;
+        for (int u = 0; u < nunit; ++u, ++n) {
+            const int dep = unit_dep(K, j, UG, u);
+            const int wi = max(dep < 0 ? -1 : n0 + (j - 2) * nunit + dep, n - NBUF);
+            ok = wait_item(done, wi, spin) && ok;
+            unsigned char* buf = bufs + (n % NBUF) * S::BUF;
+            if (ga < UG) {
+                const UnitGroup G = unit_group(K, j, UG, u, ga);
+                build_A<R>(buf + ga * S::GRP, tlane + (uint32_t)((ca ? G.src1 : G.src0) * S::SLOT), ca, row);
+            }
+            for (int it = tid; it < UG * BItems<R>::N; it += kBuilders) {
+                const int g = it / BItems<R>::N;
+                const UnitGroup G = unit_group(K, j, UG, u, g);
+                unsigned char* grp = buf + g * S::GRP;
+                if (sw)
+                    build_B_item<R, 2>(grp, it - g * BItems<R>::N, nullptr, Ss + (size_t)G.p0 * R * R,
+                                       Ss + (size_t)G.p1 * R * R);
+                else
+                    build_B_item<R, KIND>(grp, it - g * BItems<R>::N, Mt, Pl + (size_t)G.p0 * S::D2,
+                                          Pl + (size_t)G.p1 * S::D2);
+            }
+            publish(ready, n);
+        }
+    }
+    ok = wait_item(done, n - 1, spin) && ok;  // drain: one commit covers every earlier MMA
+    return ok;
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
 
 template <int R>
 size_t front_tc_smem(const Geo& g, int NV)
@@ -381,12 +417,15 @@ size_t back_tc_smem(const Geo& g, int NU)
     return std::max<size_t>(s, 120 * 1024);
 }
 
-// zero the B matrices of every operand buffer (their padding rows and K columns stay zero)
-__device__ __forceinline__ void zero_B_regions(unsigned char* bufs, int BUF, int a_bytes, int b_bytes, int tid)
+// zero the B matrices of every group of every item buffer (padding rows and K columns stay zero)
+template <int R>
+__device__ __forceinline__ void zero_B(unsigned char* bufs, int tid)
 {
-    for (int b = 0; b < NBUF; ++b) {
-        uint4* p = reinterpret_cast<uint4*>(bufs + b * BUF + 2 * a_bytes);
-        for (int i = tid; i < 4 * b_bytes / 16; i += kBuilders) p[i] = make_uint4(0, 0, 0, 0);
+    using S = Shape<R>;
+    constexpr int n16 = 2 * S::B_BYTES / 16;
+    for (int i = tid; i < NBUF * 2 * n16; i += kBuilders) {
+        const int gb = i / n16, e = i - gb * n16;
+        reinterpret_cast<uint4*>(bufs + gb * S::GRP + 2 * S::A_BYTES)[e] = make_uint4(0, 0, 0, 0);
     }
 }
 
@@ -400,9 +439,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) front_tc(TcArgs A)
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_ready[NBUF], s_done[NBUF];
     const Geo& g = A.g;
-    const int K = g.kH, T = 1 << K, ra = g.ra, mr = A.mr;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, qd = warp & 3, hw = (warp >> 2) & 1;
-    const bool builder = warp < 8;
+    const int K = g.kH, T = 1 << K, ra = g.ra, mr = A.mr, UG = T >= 4 ? 2 : 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, qd = warp & 3, role = (warp >> 2) & 3;
+    const bool builder = warp < kBuilders / 32;
     const int row = 32 * qd + lane;
     const int slice = (int)(blockIdx.x % A.nslice);
     const int64_t tile = blockIdx.x / A.nslice;
@@ -413,12 +452,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) front_tc(TcArgs A)
     const int64_t N = g.N, P = g.P;
 
     unsigned char* bufs = smem;
-    float2* EHs = reinterpret_cast<float2*>(smem + NBUF * S::BUF);  // [K][T][2R]
-    float2* EVs = EHs + (size_t)K * T * S::D2;                      // [T*NV]
-    float2* Ss = EVs + (size_t)T * NV;                              // [T][R*R] switch matrices
-    float2* bks = Ss + (size_t)T * R * R;                           // [ra][T*NV] b_k on the tile's columns
+    float2* EHs = reinterpret_cast<float2*>(smem + NBUF * S::BUF);    // [K][T][2R]
+    float2* EVs = EHs + (size_t)K * T * S::D2;                        // [T*NV]
+    float2* Ss = EVs + (size_t)T * NV;                                // [T][R*R] switch matrices
+    float2* bks = Ss + (size_t)T * R * R;                             // [ra][T*NV] b_k on the tile's columns
     float* MvTs = reinterpret_cast<float*>(bks + (size_t)ra * T * NV); // [NV][R4]
-    float* MHTs = MvTs + NV * R4;                                   // [K][2R][R4]
+    float* MHTs = MvTs + NV * R4;                                     // [K][2R][R4]
 
     if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
     if (tid == 0) {
@@ -451,12 +490,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) front_tc(TcArgs A)
         }
     }
     cp_commit();
-    // F is staged per chunk of CS slots through the (still unused) operand buffers,
+    // F is staged per chunk of CS slots through the (still unused) item buffers,
     // two chunks in flight: [CS * NV columns xi][mr right-hand sides]
     const int lmr = 31 - __clz(mr);
     const int slot_elems = NV * mr;
     int CS = T;
-    while (CS > 2 && 2 * CS * slot_elems * (int)sizeof(float2) > NBUF * S::BUF) CS >>= 1;
+    while (CS > 1 && 2 * CS * slot_elems * (int)sizeof(float2) > NBUF * S::BUF) CS >>= 1;
     const int nch = T / CS;
     float2* Fst = reinterpret_cast<float2*>(bufs);
     auto issue_chunk = [&](int ch) {
@@ -482,27 +521,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) front_tc(TcArgs A)
     const uint32_t tbase = s_tmem;
     const uint32_t tlane = tbase + ((uint32_t)(32 * qd) << 16);
     bool ok = true;
+    int n = 0;
 
     if (!builder) {
-        // ---------------- MMA issuer (one thread of warp 8)
+        // ---------------- MMA issuer (one thread of the last warp): H levels, then the switch
         if (lane == 0) {
             BufDesc<R> bd;
             bd.init(bufs);
-            int n = 0;
-            for (int j = 1; j <= K; ++j)
-                for (int grp = 0; grp < T / 2; ++grp) {
-                    int s0, s1, lo0, lo1;
-                    group_slots(K, j, grp, s0, s1, lo0, lo1);
-                    ok = issuer_item<R>(s_ready, s_done, bd, n++, true, tbase + (uint32_t)(s0 * S::SLOT),
-                                        tbase + (uint32_t)(s1 * S::SLOT), A.spin) && ok;
-                }
-            for (int lp = 0; lp < T; ++lp) {
-                const int slot = (int)brev((unsigned)lp, K);
-                ok = issuer_item<R>(s_ready, s_done, bd, n++, false, tbase + (uint32_t)(slot * S::SLOT), 0, A.spin) && ok;
-            }
+            ok = issue_passes<R>(s_ready, s_done, bd, n, K, K + 1, UG, tbase, A.spin);
         }
     } else {
-        // ---------------- builders: V (Eq. 1) into TMEM, F chunk by chunk
+        // ---------------- builders: V (Eq. 1) into TMEM slot j, F chunk by chunk
         {
             const int c = row / ra, k = row - c * ra;
             const float2* bkk = bks + k * T * NV;
@@ -515,7 +544,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) front_tc(TcArgs A)
                 }
                 builders_sync();
                 const float2* Fc = Fst + (ch & 1) * CS * slot_elems;
-                for (int jj = hw; jj < CS; jj += 2) {
+                for (int jj = role; jj < CS; jj += 4) {
                     const int j = ch * CS + jj;
                     float v[S::D2];
 #pragma unroll
@@ -537,42 +566,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) front_tc(TcArgs A)
             }
             tc::wait_st();
         }
-        zero_B_regions(bufs, S::BUF, S::A_BYTES, S::B_BYTES, tid);
+        zero_B<R>(bufs, tid);
         tc::fence_before();
         builders_sync();
         tc::fence_after();
 
-        BPipe bp;
-        bp.n = 0;
-        bp.ok = true;
-        // ---- H levels (Eq. 2)
-        for (int j = 1; j <= K; ++j) {
-            const float* Mh = MHTs + (size_t)(j - 1) * 2 * R * R4;
-            const float2* Pl = EHs + (size_t)(j - 1) * T * S::D2;
-            for (int grp = 0; grp < T / 2; ++grp) {
-                int s0, s1, lo0, lo1;
-                group_slots(K, j, grp, s0, s1, lo0, lo1);
-                unsigned char* buf = builders_begin(bufs, S::BUF, s_done, bp, grp == 0, A.spin);
-                build_A_group<R>(buf, tlane, s0, s1, hw, row);
-                build_B_group<R, 0>(buf, Mh, Pl + (size_t)lo0 * S::D2, Pl + (size_t)lo1 * S::D2, tid);
-                builders_end(s_ready, bp);
-            }
-        }
-        // ---- switch (step 4), one pair per item
-        for (int lp = 0; lp < T; ++lp) {
-            const int slot = (int)brev((unsigned)lp, K);
-            unsigned char* buf = builders_begin(bufs, S::BUF, s_done, bp, lp == 0, A.spin);
-            if (hw == 0) build_A_single<R>(buf, tlane, slot, row);
-            build_B_switch<R>(buf, Ss + (size_t)lp * R * R, tid);
-            builders_end(s_ready, bp);
-        }
-        builders_drain(s_done, bp, A.spin);
-        ok = bp.ok;
+        // ---- H levels (Eq. 2) and the switch (step 4)
+        ok = build_passes<R, 0>(bufs, s_ready, s_done, n, K, K + 1, UG, tlane, MHTs, EHs, Ss, tid, row, role, A.spin);
 
         // ---- write the switch-level coefficients: W[slice][q][row][R]
         float2* Wout = A.W + (size_t)slice * P * 128 * R;
-        for (int lp = hw; lp < T; lp += 2) {
-            const int slot = (int)brev((unsigned)lp, K);
+        for (int lp = role; lp < T; lp += 4) {
+            const int slot = phys_final(K, (int)brev((unsigned)lp, K));
             const int64_t qg = ((p << K) + lp) * nBh + c0;
             float v[S::D2];
             tc::ld_dims<S::D2>(tlane + (uint32_t)(slot * S::SLOT), v);
@@ -598,9 +603,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) back_tc(TcArgs A)
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_ready[NBUF], s_done[NBUF];
     const Geo& g = A.g;
-    const int K = g.kG, T = 1 << K, ra = g.ra, mr = A.mr;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, qd = warp & 3, hw = (warp >> 2) & 1;
-    const bool builder = warp < 8;
+    const int K = g.kG, T = 1 << K, ra = g.ra, mr = A.mr, UG = T >= 4 ? 2 : 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, qd = warp & 3, role = (warp >> 2) & 3;
+    const bool builder = warp < kBuilders / 32;
     const int row = 32 * qd + lane;
     const int slice = (int)(blockIdx.x % A.nslice);
     const int64_t pp_x = blockIdx.x / A.nslice;  // x-node at level h
@@ -623,43 +628,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) back_tc(TcArgs A)
             tc::mbar_init(&s_done[b], 1);
         }
     }
-    if (builder) zero_B_regions(bufs, S::BUF, S::A_BYTES, S::B_BYTES, tid);
+    if (builder) zero_B<R>(bufs, tid);
     stage_matrix(MGTs, A.MGT, K * 2 * R, R, R4, tid);
     stage_matrix(MUs, A.MU, NU, R, R4, tid);
     for (int k = 0; k < ra; ++k)
         for (int e = tid; e < XN / 2; e += kTcThreads) cp16(aks + k * XN + 2 * e, A.ak + k * N + x0g + 2 * e);
-    cp_commit_wait();
+    cp_commit();
+    cp_wait<0>();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = s_tmem;
     const uint32_t tlane = tbase + ((uint32_t)(32 * qd) << 16);
     bool ok = true;
+    int n = 0;
 
     if (!builder) {
         if (lane == 0) {
             BufDesc<R> bd;
             bd.init(bufs);
-            int n = 0;
-            for (int c0 = 0; c0 < nC; ++c0)
-                for (int j = 1; j <= K; ++j)
-                    for (int grp = 0; grp < T / 2; ++grp) {
-                        int s0, s1, lo0, lo1;
-                        group_slots(K, j, grp, s0, s1, lo0, lo1);
-                        ok = issuer_item<R>(s_ready, s_done, bd, n++, true, tbase + (uint32_t)(s0 * S::SLOT),
-                                            tbase + (uint32_t)(s1 * S::SLOT), A.spin) && ok;
-                    }
+            for (int c0 = 0; c0 < nC; ++c0) ok = issue_passes<R>(s_ready, s_done, bd, n, K, K, UG, tbase, A.spin) && ok;
         }
     } else {
         const int c = row / ra, k = row - c * ra;
         const int64_t cg = (int64_t)slice * mr + c;
         const bool valid = cg < A.m;
-        const bool accum_old = A.beta != 0;
         const float2* akk = aks + k * XN;
         const float2* Win = A.W + (size_t)slice * P * 128 * R;
-        BPipe bp;
-        bp.n = 0;
-        bp.ok = true;
         for (int c0 = 0; c0 < nC; ++c0) {
             // FG phases and EU of T_Omega node c0 (overlaps the W loads below)
             for (int jl = 1; jl <= K; ++jl) {
@@ -674,12 +669,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) back_tc(TcArgs A)
             }
             for (int e = tid; e < XN / 2; e += kBuilders) cp16(EUs + 2 * e, A.EU + (size_t)c0 * N + x0g + 2 * e);
             cp_commit();
-            // switch-level pairs (pp_x, c0 T + j) -> TMEM slots j, two slots' loads in flight
-            for (int j = hw; j < T; j += 4) {
-                const bool two = j + 2 < T;
+            // switch-level pairs (pp_x, c0 T + j) -> TMEM slot j, two slots' loads in flight
+            for (int j = role; j < T; j += 8) {
+                const bool two = j + 4 < T;
                 const float4* src0 =
                     reinterpret_cast<const float4*>(Win + ((size_t)(pp_x * nBh + (int64_t)c0 * T + j) * 128 + row) * R);
-                const float4* src1 = src0 + (two ? 2 * 128 * R / 2 : 0);
+                const float4* src1 = src0 + (two ? 4 * 128 * R / 2 : 0);
                 float v0[S::D2], v1[S::D2];
 #pragma unroll
                 for (int i = 0; i < S::D2 / 4; ++i) {
@@ -689,7 +684,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) back_tc(TcArgs A)
                     v1[4 * i] = b.x; v1[4 * i + 1] = b.y; v1[4 * i + 2] = b.z; v1[4 * i + 3] = b.w;
                 }
                 tc::st_dims<S::D2>(tlane + (uint32_t)(j * S::SLOT), v0);
-                if (two) tc::st_dims<S::D2>(tlane + (uint32_t)((j + 2) * S::SLOT), v1);
+                if (two) tc::st_dims<S::D2>(tlane + (uint32_t)((j + 4) * S::SLOT), v1);
             }
             cp_wait<0>();
             tc::wait_st();
@@ -697,63 +692,56 @@ __global__ void __launch_bounds__(kTcThreads, 1) back_tc(TcArgs A)
             builders_sync();
             tc::fence_after();
 
-            // ---- G levels (Eq. 3)
-            for (int j = 1; j <= K; ++j) {
-                const float* Mg = MGTs + (size_t)(j - 1) * 2 * R * R4;
-                const float2* Pl = FGs + (size_t)(j - 1) * T * S::D2;
-                for (int grp = 0; grp < T / 2; ++grp) {
-                    int s0, s1, lo0, lo1;
-                    group_slots(K, j, grp, s0, s1, lo0, lo1);
-                    unsigned char* buf = builders_begin(bufs, S::BUF, s_done, bp, grp == 0, A.spin);
-                    build_A_group<R>(buf, tlane, s0, s1, hw, row);
-                    build_B_group<R, 1>(buf, Mg, Pl + (size_t)lo0 * S::D2, Pl + (size_t)lo1 * S::D2, tid);
-                    builders_end(s_ready, bp);
-                }
-            }
-            builders_drain(s_done, bp, A.spin);
+            // ---- G levels (Eq. 3), drained
+            ok = build_passes<R, 1>(bufs, s_ready, s_done, n, K, K, UG, tlane, MGTs, FGs, nullptr, tid, row, role,
+                                    A.spin) && ok;
 
             // ---- U (Eq. bf3) of T_Omega node c0, summed over k, accumulated into this CTA's
-            // rows of G; lane k of each column writes the rows i = k (mod r_alpha), all old
-            // values loaded before any store
-            const bool add_old = c0 > 0 || accum_old;
-            for (int lp = hw; lp < T; lp += 2) {
-                const int slot = (int)brev((unsigned)lp, K);
+            // rows of G; lane k of each column writes the rows i = k (mod r_alpha); the old
+            // values are loaded before the arithmetic that hides their latency
+            const bool add_old = c0 > 0 || A.beta != 0;
+            for (int lp = role; lp < T; lp += 4) {
+                const int slot = phys_final(K, (int)brev((unsigned)lp, K));
                 float v[S::D2];
                 tc::ld_dims<S::D2>(tlane + (uint32_t)(slot * S::SLOT), v);
                 tc::wait_ld();
-                float2 ctb[NU];
+                float2* gp = A.G + (x0g + lp * NU) * A.m + cg;
 #pragma unroll
-                for (int i = 0; i < NU; ++i) {
-                    float2 w = make_float2(0.f, 0.f);
-                    const float* mu = MUs + i * R4;
+                for (int h2 = 0; h2 < NU; h2 += 8) {
+                    float2 old[8];
 #pragma unroll
-                    for (int s2 = 0; s2 < R; ++s2) {
-                        w.x = fmaf(mu[s2], v[2 * s2], w.x);
-                        w.y = fmaf(mu[s2], v[2 * s2 + 1], w.y);
+                    for (int i = 0; i < 8; ++i)
+                        old[i] = (valid && add_old && ((h2 + i) & (ra - 1)) == k) ? gp[(int64_t)(h2 + i) * A.m]
+                                                                                   : make_float2(0.f, 0.f);
+                    float2 ctb[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        float2 w = make_float2(0.f, 0.f);
+                        const float* mu = MUs + (h2 + i) * R4;
+#pragma unroll
+                        for (int s2 = 0; s2 < R; ++s2) {
+                            w.x = fmaf(mu[s2], v[2 * s2], w.x);
+                            w.y = fmaf(mu[s2], v[2 * s2 + 1], w.y);
+                        }
+                        float2 z = cmulf(cmulf(akk[lp * NU + h2 + i], EUs[lp * NU + h2 + i]), w);
+                        for (int o = 1; o < ra; o <<= 1) {
+                            z.x += __shfl_xor_sync(0xffffffffu, z.x, o);
+                            z.y += __shfl_xor_sync(0xffffffffu, z.y, o);
+                        }
+                        ctb[i] = z;
                     }
-                    float2 z = cmulf(cmulf(akk[lp * NU + i], EUs[lp * NU + i]), w);
-                    for (int o = 1; o < ra; o <<= 1) {
-                        z.x += __shfl_xor_sync(0xffffffffu, z.x, o);
-                        z.y += __shfl_xor_sync(0xffffffffu, z.y, o);
+                    if (valid) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (((h2 + i) & (ra - 1)) == k)
+                                gp[(int64_t)(h2 + i) * A.m] = make_float2(ctb[i].x + old[i].x, ctb[i].y + old[i].y);
                     }
-                    ctb[i] = z;
-                }
-                if (valid) {
-                    float2* gp = A.G + (x0g + lp * NU) * A.m + cg;
-                    float2 old[NU];
-#pragma unroll
-                    for (int i = 0; i < NU; ++i)
-                        old[i] = (add_old && (i & (ra - 1)) == k) ? gp[(int64_t)i * A.m] : make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int i = 0; i < NU; ++i)
-                        if ((i & (ra - 1)) == k) gp[(int64_t)i * A.m] = make_float2(ctb[i].x + old[i].x, ctb[i].y + old[i].y);
                 }
             }
             tc::fence_before();
             builders_sync();
             tc::fence_after();
         }
-        ok = bp.ok;
     }
     tc::fence_before();
     __syncthreads();
@@ -824,6 +812,10 @@ bool tc_supported(const Geo& g, const char** why)
     }
     if (g.ra != 1 && g.ra != 2 && g.ra != 4) {
         if (why) *why = "split-BF16 kernels need an amplitude rank of 1, 2 or 4";
+        return false;
+    }
+    if (g.kH < 1 || g.kG < 1) {
+        if (why) *why = "split-BF16 kernels need at least one H and one G level";
         return false;
     }
     const int slot = 2 * r <= 16 ? 16 : 32;
