@@ -297,11 +297,14 @@ __device__ __forceinline__ bool wait_item(uint64_t* done, int i, long long spin)
     return ok;
 }
 
+// every builder thread makes its operand writes (and its TMEM reads) visible,
+// then one lane per warp arrives: ready[] counts warps
 __device__ __forceinline__ void publish(uint64_t* ready, int n)
 {
     tc::fence_async_smem();
     tc::fence_before();
-    mbar_arrive(&ready[n % NBUF]);
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&ready[n % NBUF]);
 }
 
 template <int R>
@@ -370,16 +373,12 @@ __device__ __forceinline__ bool build_passes(unsigned char* bufs, uint64_t* read
         const float* Mt = Mlev + (size_t)(j - 1) * 2 * R * R4;
         const float2* Pl = Plev + (size_t)(j - 1) * T * S::D2;
         for (int u = 0; u < nunit; ++u, ++n) {
-            const int dep = unit_dep(K, j, UG, u);
-            const int wi = max(dep < 0 ? -1 : n0 + (j - 2) * nunit + dep, n - NBUF);
-            ok = wait_item(done, wi, spin) && ok;
+            // the weights need only a free buffer: build them while the MMAs this
+            // item's data depends on may still run
+            ok = wait_item(done, n - NBUF, spin) && ok;
             unsigned char* buf = bufs + (n % NBUF) * S::BUF;
-            if (ga < UG) {
-                const UnitGroup G = unit_group(K, j, UG, u, ga);
-                build_A<R>(buf + ga * S::GRP, tlane + (uint32_t)((ca ? G.src1 : G.src0) * S::SLOT), ca, row);
-            }
             for (int it = tid; it < UG * BItems<R>::N; it += kBuilders) {
-                const int g = it / BItems<R>::N;
+                const int g = it >= BItems<R>::N;
                 const UnitGroup G = unit_group(K, j, UG, u, g);
                 unsigned char* grp = buf + g * S::GRP;
                 if (sw)
@@ -388,6 +387,12 @@ __device__ __forceinline__ bool build_passes(unsigned char* bufs, uint64_t* read
                 else
                     build_B_item<R, KIND>(grp, it - g * BItems<R>::N, Mt, Pl + (size_t)G.p0 * S::D2,
                                           Pl + (size_t)G.p1 * S::D2);
+            }
+            const int dep = unit_dep(K, j, UG, u);
+            if (dep >= 0) ok = wait_item(done, max(n0 + (j - 2) * nunit + dep, n - NBUF), spin) && ok;
+            if (ga < UG) {
+                const UnitGroup G = unit_group(K, j, UG, u, ga);
+                build_A<R>(buf + ga * S::GRP, tlane + (uint32_t)((ca ? G.src1 : G.src0) * S::SLOT), ca, row);
             }
             publish(ready, n);
         }
@@ -462,7 +467,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) front_tc(TcArgs A)
     if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
     if (tid == 0) {
         for (int b = 0; b < NBUF; ++b) {
-            tc::mbar_init(&s_ready[b], kBuilders);
+            tc::mbar_init(&s_ready[b], kBuilders / 32);
             tc::mbar_init(&s_done[b], 1);
         }
     }
@@ -624,7 +629,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) back_tc(TcArgs A)
     if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
     if (tid == 0) {
         for (int b = 0; b < NBUF; ++b) {
-            tc::mbar_init(&s_ready[b], kBuilders);
+            tc::mbar_init(&s_ready[b], kBuilders / 32);
             tc::mbar_init(&s_done[b], 1);
         }
     }
