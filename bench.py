@@ -7,7 +7,7 @@ eps = 1e-6.  One step = one full apply G = K F (amplitude split-in, V, all H
 levels, switch, all G levels, U, amplitude split-out).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload fio2|fio1|fio3] [--prec f32|f64]
+                    [--workload fio2|fio1|fio3|fio4|serve5] [--prec f32|f64|bf16x3]
 
 Under torchrun each rank applies its own operator replica to its own m
 right-hand sides (weak scaling, no data-path collective).
@@ -51,6 +51,24 @@ FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 
 
+def max_over_ranks(x, world, device):
+    """The timing rule across ranks: each rank's value reduced with MAX (NCCL on the
+    GPU machine; gloo on CPU in the tests)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank_step, steps, ms_max):
+    """Whole-job throughput in G units/s: the units every rank processed over the
+    slowest rank's time (weak scaling: each rank applies its own replica)."""
+    return world * units_per_rank_step * steps / (ms_max * 1e-3) / 1e9
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -68,14 +86,15 @@ def tensor_flops(info, m, N, split):
     D2 = 2 * r
     SLOT = 16 if D2 <= 16 else 32
     KS = (D2 + 7) // 8 * 8
-    KG, KP = 2 * KS, (D2 + 15) // 16 * 16
+    KG = 2 * KS
     mr = 128 // ra
     nslice = -(-m // mr)
     mma = 2 * 128 * SLOT * 16
     group = 2 * 3 * (KG // 16) * mma
     TF, TB = 2 ** kH, 2 ** kG
     ntile = (2 ** l1) * (2 ** (L - h)) * nslice
-    front = ntile * (kH * (TF // 2) * group + TF * 3 * (KP // 16) * mma)
+    # the switch runs per region of two pairs: a group-shaped chain with a block-diagonal weight
+    front = ntile * (kH * (TF // 2) * group + TF * 3 * (KG // 16) * mma)
     back = (2 ** h) * nslice * (2 ** l1) * kG * (TB // 2) * group
     nblk = split * split
     return {"front_tc": front * nblk, "back_tc": back * nblk}
@@ -383,11 +402,8 @@ def run_batched(args, w, rank, world, local):
     torch.cuda.synchronize()
     assert batch.status(stream) == 0
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = world * units * args.steps / (ms_max * 1e-3) / 1e9
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = job_rate(world, units, args.steps, ms_max)
     # kernel time of the persistent launch, issued eagerly (graph replays bypass the launch hooks)
     with api.KernelTimer() as kt_eager:
         with torch.cuda.stream(stream):
@@ -540,11 +556,8 @@ def main():
     torch.cuda.synchronize()
     assert plan.sync_status() == 0
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = world * N * m * args.steps / (ms_max * 1e-3) / 1e9
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = job_rate(world, N * m, args.steps, ms_max)
 
     peaks, peak_src = load_peaks()
     front, back, bytes_apply = algorithmic(info, m, N, w["split"])
@@ -600,12 +613,9 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             plan.apply_host(Fp, Gp, prec)
-        t_e2e = time.perf_counter() - t0
-        te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world, "cuda")
         nbytes = Fp.numel() * Fp.element_size()
-        e2e = {"value": world * N * m * args.steps / float(te.item()) / 1e9, "unit": UNIT,
+        e2e = {"value": job_rate(world, N * m, args.steps, 1e3 * t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     cpu = None
