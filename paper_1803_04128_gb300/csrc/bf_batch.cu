@@ -152,21 +152,40 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
             return BF_ERR_UNSUPPORTED;
         }
         smem = std::max(smem, std::max(sf, sb));
-        off[(size_t)(2 * i)] = tot;
-        tot += bi.nfront;
-        off[(size_t)(2 * i + 1)] = tot;
-        tot += bi.nback;
+    }
+    // Work order: each operator's front segment, and its back segment once at
+    // least kBackLag work items have been queued after that front segment (or
+    // at the end), so that a back tile rarely finds its operator's fronts still
+    // running.  Every front of an operator precedes all of its backs, so a back
+    // tile's wait always ends.
+    std::vector<int> seg((size_t)(2 * n));
+    {
+        constexpr int64_t kBackLag = 1024;
+        std::vector<std::pair<int, int64_t>> pending;  // (op, position after its fronts)
+        size_t head = 0, k = 0;
+        auto put = [&](int op, bool back) {
+            off[k] = tot;
+            seg[k++] = (op << 1) | (back ? 1 : 0);
+            tot += back ? b->items[(size_t)op].nback : b->items[(size_t)op].nfront;
+        };
+        for (int i = 0; i < n; ++i) {
+            put(i, false);
+            pending.emplace_back(i, tot);
+            while (head < pending.size() && tot - pending[head].second >= kBackLag) put(pending[head++].first, true);
+        }
+        while (head < pending.size()) put(pending[head++].first, true);
     }
     if (smem > 227 * 1024) {
         free_batch(b);
         set_error("bf_batch_create: a tile needs %zu bytes of shared memory", smem);
         return BF_ERR_UNSUPPORTED;
     }
-    // device copies: items | off[2n] | counter | done[n] | err
+    // device copies: items | off[2n] | seg[2n] | counter | done[n] | err
     const size_t s_items = ((size_t)n * sizeof(BatchItem) + 255) & ~(size_t)255;
     const size_t s_off = ((size_t)(2 * n) * sizeof(int64_t) + 255) & ~(size_t)255;
+    const size_t s_seg = ((size_t)(2 * n) * sizeof(int) + 255) & ~(size_t)255;
     const size_t s_reset = ((sizeof(unsigned long long) + (size_t)n * sizeof(int)) + 255) & ~(size_t)255;
-    b->dmem_bytes = s_items + s_off + s_reset + 256;
+    b->dmem_bytes = s_items + s_off + s_seg + s_reset + 256;
     if ((e = cudaMalloc(&b->dmem, b->dmem_bytes)) != cudaSuccess) {
         free_batch(b);
         return cuda_fail("bf_batch_create: descriptors", e);
@@ -175,6 +194,7 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
     std::vector<unsigned char> host(b->dmem_bytes, 0);
     std::memcpy(host.data(), b->items.data(), (size_t)n * sizeof(BatchItem));
     std::memcpy(host.data() + s_items, off.data(), (size_t)(2 * n) * sizeof(int64_t));
+    std::memcpy(host.data() + s_items + s_off, seg.data(), (size_t)(2 * n) * sizeof(int));
     if ((e = cudaMemcpy(base, host.data(), b->dmem_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
         free_batch(b);
         return cuda_fail("bf_batch_create: upload", e);
@@ -182,7 +202,8 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
     b->bl.items = (const BatchItem*)base;
     b->bl.nitems = n;
     b->bl.off = (const int64_t*)(base + s_items);
-    b->reset_ptr = base + s_items + s_off;
+    b->bl.seg = (const int*)(base + s_items + s_off);
+    b->reset_ptr = base + s_items + s_off + s_seg;
     b->reset_bytes = s_reset;
     b->bl.counter = (unsigned long long*)b->reset_ptr;
     b->bl.done = (int*)(b->reset_ptr + sizeof(unsigned long long));

@@ -45,7 +45,8 @@ struct BatchItem {
 struct BatchLaunch {
     const BatchItem* items = nullptr;
     int nitems = 0;
-    const int64_t* off = nullptr;  // [2 nitems] start of (fronts of op i, backs of op i) in the work order
+    const int64_t* off = nullptr;  // [2 nitems] start of each segment in the work order (increasing)
+    const int* seg = nullptr;      // [2 nitems] segment -> (op << 1) | (1 for its back tiles, 0 for its fronts)
     int64_t total = 0;
     unsigned long long* counter = nullptr;
     int* done = nullptr;  // [nitems]

@@ -555,17 +555,17 @@ __device__ __noinline__ void back_tile_ool(const BackArgs& A, int64_t work, unsi
 }
 
 // One persistent launch over the front and back tiles of many operators.
-// Work items are handed out by an atomic counter in the order
-// [fronts of op 0][backs of op 0][fronts of op 1][backs of op 1]..., so an
-// operator's back tiles follow its front tiles closely (its switch-level
-// workspace is often still in L2) and every front tile is claimed, by a
-// running CTA, before any back tile of the same operator; a back tile waits
-// until all front tiles of its operator are done (bounded spin; on time-out it
-// sets *err and skips the tile).
+// Work items are handed out by an atomic counter in segment order (off[],
+// seg[]): each operator's front segment, and its back segment a little later
+// (after about a thousand more work items, so that its fronts have usually
+// finished while its switch-level workspace is still in L2).  Every front tile
+// is claimed, by a running CTA, before any back tile of the same operator; a
+// back tile waits until all front tiles of its operator are done (bounded
+// spin; on time-out it sets *err and skips the tile).
 template <int R, int NV>
 __global__ void __launch_bounds__(kThreads, 2)
-    batch_f32(const BatchItem* items, int nitems, const int64_t* off, int64_t total, unsigned long long* counter,
-              int* done, int* err, long long spin_limit, int wait_extra)
+    batch_f32(const BatchItem* items, int nitems, const int64_t* off, const int* seg, int64_t total,
+              unsigned long long* counter, int* done, int* err, long long spin_limit, int wait_extra)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long s_w;
@@ -576,11 +576,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         const long long w = s_w;
         __syncthreads();
         if (w >= total) break;
-        int j = 0;  // segment: 2 i = fronts of op i, 2 i + 1 = backs of op i
+        int j = 0;  // segment of work item w
         while (j + 1 < 2 * nitems && off[j + 1] <= w) ++j;
-        const int i = j >> 1;
+        const int i = seg[j] >> 1;
         const long long local = w - off[j];
-        if ((j & 1) == 0) {
+        if ((seg[j] & 1) == 0) {
             front_tile_ool<R, NV>(items[i].fa, local, smem_raw);
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -624,8 +624,8 @@ cudaError_t batch_launch_r(const BatchLaunch& bl, cudaStream_t st, bool set_attr
         return cudaSuccess;
     }
     ProfScope ps("batch_f32", st);
-    batch_f32<R, NV><<<bl.grid, kThreads, bl.smem, st>>>(bl.items, bl.nitems, bl.off, bl.total, bl.counter, bl.done,
-                                                          bl.err, bl.spin_limit, bl.wait_extra);
+    batch_f32<R, NV><<<bl.grid, kThreads, bl.smem, st>>>(bl.items, bl.nitems, bl.off, bl.seg, bl.total, bl.counter,
+                                                          bl.done, bl.err, bl.spin_limit, bl.wait_extra);
     return cudaGetLastError();
 }
 
