@@ -444,7 +444,7 @@ def run_batched(args, w, rank, world, local):
     if nb:
         achieved = flops / (tb / nb * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "batch_f32", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": ncu_traffic("batch_f32", args.workload),
+                "frac": achieved / alu_peak, "traffic": ncu_traffic("batch_f32", args.workload, None),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s)" % (peaks.get("sm_max_mhz", 2070.0), peak_src),
                 "kernel_ms": {k: v[1] / v[0] for k, v in kt_eager.result.items()}}
     # end to end: pinned host F in, graph replay, G out

@@ -73,6 +73,8 @@ size_t plain_f64_ws_bytes(const Geo& g, int64_t m);  // bytes of ONE of the two 
 struct FusedCfg {
     int mr;       // right-hand sides per column slice
     int nslice;   // ceil(m / mr)
+    int tpc_f;    // front tiles per CTA
+    int tpc_b;    // T_Omega chunks a back CTA processes together
 };
 // mr_hint: column-slice width chosen by the autotuner (0 = built-in rule)
 FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint = 0);

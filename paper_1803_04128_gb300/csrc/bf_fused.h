@@ -11,6 +11,7 @@ struct FrontArgs {
     const float2* F;  // [N][m]
     int64_t m;
     int mr, lmr, CTp, lct, nslice;
+    int tpc;           // tiles per CTA (consecutive work indices)
     const float2* bk;  // [ra][N]
     const float* MvT;  // [nv][R]
     const float2* EV;  // [2^l1][N]
@@ -24,6 +25,7 @@ struct BackArgs {
     Geo g;
     int64_t m;
     int mr, lmr, CTp, lct, nslice;
+    int tpc;           // T_Omega chunks processed together (divides 2^l1)
     const float2* W;
     const float* MGT;  // [kG][2][R][R]  (pos, s, t)
     const float2* FG;  // [kG][P][2][R]

@@ -184,52 +184,72 @@ __device__ __forceinline__ void g_item(float2* x0, float2* x1, int CTp, const fl
 }
 
 // ------------------------------------------------------------------ front --
-// Shared memory: X [T][R][CTp] | EH double buffer [2][T][2][R] | EV [T*NV] |
-// F rows [T*NV][mr] | Mv^T [NV][R4] | MH^T [kH][2R][R4].  The phases of level j
-// are staged (cp.async) while level j-1 is computed; b_k and the switch
-// matrices are read through the read-only cache.
+// Shared memory: Mv^T [NV][R4] | MH^T [kH][2R][R4] | per tile u < tpc:
+// X [T][R][CTp] | EH double buffer [2][T][2][R] | EV [T*NV] | F rows [T*NV][mr].
+// A CTA applies tpc consecutive tiles (work indices work * tpc + u): with few
+// columns per tile, several tiles share the CTA's threads and their loads are
+// in flight together; each tile's arithmetic is the same for any tpc.  The
+// phases of level j are staged (cp.async) while level j-1 is computed; b_k and
+// the switch matrices are read through the read-only cache.
 template <int R, int NV>
 __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, unsigned char* smem_raw)
 {
     constexpr int R4 = Pad4<R>::v;
     const Geo& g = A.g;
-    const int K = g.kH, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra;
-    const int slice = (int)(work % A.nslice);
-    const int64_t tile = work / A.nslice;
-    const int nP = 1 << g.l1;                       // x-nodes at level l1
-    const int64_t p = tile & (nP - 1), c0 = tile >> g.l1;
+    const int K = g.kH, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra, tpc = A.tpc;
+    const int nP = 1 << g.l1;                        // x-nodes at level l1
     const int64_t nBh = (int64_t)1 << (g.L - g.h);   // T_Omega nodes at level L-h
-    const int64_t xi_base = c0 * T * NV;
     const int64_t N = g.N, P = g.P, m = A.m;
     const int L = g.L, l1 = g.l1;
+    const size_t tile_f2 = (size_t)T * R * CTp + (size_t)2 * T * 2 * R + (size_t)T * NV + (size_t)T * NV * mr;
 
-    float2* X = reinterpret_cast<float2*>(smem_raw);         // [T][R][CTp]
-    float2* EHb = X + (size_t)T * R * CTp;                    // [2][T][2][R]
-    float2* EVs = EHb + (size_t)2 * T * 2 * R;                // [T*NV]
-    float2* Fs = EVs + (size_t)T * NV;                        // [T*NV][mr]
-    float* MvTs = reinterpret_cast<float*>(Fs + (size_t)T * NV * mr);  // [NV][R4]
-    float* MHTs = MvTs + NV * R4;                                      // [K][2R][R4]
-
+    float* MvTs = reinterpret_cast<float*>(smem_raw);                      // [NV][R4]
+    float* MHTs = MvTs + NV * R4;                                          // [K][2R][R4]
+    float2* tiles = reinterpret_cast<float2*>(MHTs + (size_t)K * 2 * R * R4);
+    auto Xof = [&](int u) { return tiles + (size_t)u * tile_f2; };                         // [T][R][CTp]
+    auto EHof = [&](int u) { return Xof(u) + (size_t)T * R * CTp; };                       // [2][T][2][R]
+    auto EVof = [&](int u) { return EHof(u) + (size_t)2 * T * 2 * R; };                    // [T*NV]
+    auto Fof = [&](int u) { return EVof(u) + (size_t)T * NV; };                            // [T*NV][mr]
+    // tile u: work index work * tpc + u -> (column slice, x-node p, T_Omega chunk c0)
+    __shared__ int64_t s_p[16], s_c0[16];
+    __shared__ int s_slice[16];
     const int tid = threadIdx.x;
+    if (tid < tpc) {
+        const int64_t idx = work * tpc + tid, tile = idx / A.nslice;
+        s_slice[tid] = (int)(idx - tile * A.nslice);
+        s_p[tid] = tile & (nP - 1);
+        s_c0[tid] = tile >> l1;
+    }
+    __syncthreads();
+    auto slice_of = [&](int u) { return s_slice[u]; };
+    auto p_of = [&](int u) { return s_p[u]; };
+    auto c0_of = [&](int u) { return s_c0[u]; };
+
     const float2* EHg = A.EH;
-    auto stage_eh = [&](int j) {  // phases of level l1 + j into buffer (j - 1) & 1
+    auto stage_eh = [&](int j) {  // phases of level l1 + j into buffer (j - 1) & 1 of every tile
         const int64_t nBl = (int64_t)1 << (L - l1 - j);
         const float2* eh = EHg + (size_t)(j - 1) * P * 2 * R;
-        float2* dst = EHb + (size_t)((j - 1) & 1) * T * 2 * R;
-        for (int e = tid; e < T * R; e += kThreads) {  // R 16-byte chunks per pair
-            const int lp = e / R, w = e - lp * R;
-            const int64_t ap = (p << j) + (lp >> (K - j));
-            const int64_t bp = (c0 << (K - j)) + (lp & ((1 << (K - j)) - 1));
-            cp16(dst + (size_t)lp * 2 * R + 2 * w, eh + (ap * nBl + bp) * 2 * R + 2 * w);
+        for (int u = 0; u < tpc; ++u) {
+            const int64_t p = p_of(u), c0 = c0_of(u);
+            float2* dst = EHof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
+            for (int e = tid; e < T * R; e += kThreads) {  // R 16-byte chunks per pair
+                const int lp = e / R, w = e - lp * R;
+                const int64_t ap = (p << j) + (lp >> (K - j));
+                const int64_t bp = (c0 << (K - j)) + (lp & ((1 << (K - j)) - 1));
+                cp16(dst + (size_t)lp * 2 * R + 2 * w, eh + (ap * nBl + bp) * 2 * R + 2 * w);
+            }
         }
     };
     // group 0: matrices, EV, F rows, level-1 phases; group 1: level-2 phases
     stage_matrix(MvTs, A.MvT, NV, R, R4, tid);
     stage_matrix(MHTs, A.MHT, K * 2 * R, R, R4, tid);
-    {
-        const float2* ev = A.EV + p * N + xi_base;
+    for (int u = 0; u < tpc; ++u) {
+        const int64_t xi_base = c0_of(u) * T * NV;
+        const float2* ev = A.EV + p_of(u) * N + xi_base;
+        float2* EVs = EVof(u);
         for (int e = tid; e < T * NV / 2; e += kThreads) cp16(EVs + 2 * e, ev + 2 * e);
-        const int64_t cbase = (int64_t)slice * mr;
+        const int64_t cbase = (int64_t)slice_of(u) * mr;
+        float2* Fs = Fof(u);
         for (int e = tid; e < T * NV * mr; e += kThreads) {
             const int row = e >> lmr, c = e & (mr - 1);
             const bool valid = cbase + c < m;
@@ -242,53 +262,55 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
         stage_eh(2);
         cp_commit();
     }
-    // padding columns of the tile start (and stay) at zero
-    for (int e = tid; e < T * R * CTp; e += kThreads)
-        if ((e & (CTp - 1)) >= ra * mr) X[e] = make_float2(0.f, 0.f);
+    // padding columns of the tiles start (and stay) at zero
+    for (int u = 0; u < tpc; ++u) {
+        float2* X = Xof(u);
+        for (int e = tid; e < T * R * CTp; e += kThreads)
+            if ((e & (CTp - 1)) >= ra * mr) X[e] = make_float2(0.f, 0.f);
+    }
     if (K >= 2) cp_wait1(); else cp_wait0();
     __syncthreads();
 
-    // ---- V (Eq. 1): item (j, c) computes mu[j][.][k*mr + c] for every k
-    {
-        const int c = tid & (mr - 1);
-        for (int j = tid >> lmr; j < T; j += kThreads >> lmr) {
-            const float2* fs = Fs + (size_t)j * NV * mr + c;
-            float2 f[NV];
+    // ---- V (Eq. 1): item (u, j, c) computes mu[j][.][k*mr + c] of tile u for every k
+    for (int it = tid; it < tpc * T * mr; it += kThreads) {
+        const int c = it & (mr - 1), j = (it >> lmr) & (T - 1), u = it >> (lmr + K);
+        const int64_t xi_base = c0_of(u) * T * NV;
+        const float2* fs = Fof(u) + (size_t)j * NV * mr + c;
+        const float2* EVs = EVof(u);
+        float2 f[NV];
 #pragma unroll
-            for (int x = 0; x < NV; ++x) f[x] = fs[x * mr];
-            for (int k = 0; k < ra; ++k) {
-                float2 acc[R];
+        for (int x = 0; x < NV; ++x) f[x] = fs[x * mr];
+        for (int k = 0; k < ra; ++k) {
+            float2 acc[R];
 #pragma unroll
-                for (int t = 0; t < R; ++t) acc[t] = make_float2(0.f, 0.f);
-                const float2* bk = A.bk + (size_t)k * N + xi_base + j * NV;
+            for (int t = 0; t < R; ++t) acc[t] = make_float2(0.f, 0.f);
+            const float2* bk = A.bk + (size_t)k * N + xi_base + j * NV;
 #pragma unroll
-                for (int x = 0; x < NV; ++x) {
-                    const float2 z = cmulf(EVs[j * NV + x], cmulf(__ldg(bk + x), f[x]));
-                    const float4* mv = reinterpret_cast<const float4*>(MvTs + x * R4);
+            for (int x = 0; x < NV; ++x) {
+                const float2 z = cmulf(EVs[j * NV + x], cmulf(__ldg(bk + x), f[x]));
+                const float4* mv = reinterpret_cast<const float4*>(MvTs + x * R4);
 #pragma unroll
-                    for (int t4 = 0; t4 < R4 / 4; ++t4) {
-                        const float4 w = mv[t4];
-                        const float ww[4] = {w.x, w.y, w.z, w.w};
+                for (int t4 = 0; t4 < R4 / 4; ++t4) {
+                    const float4 w = mv[t4];
+                    const float ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int t = 4 * t4 + q;
-                            if (t < R) {
-                                acc[t].x = fmaf(ww[q], z.x, acc[t].x);
-                                acc[t].y = fmaf(ww[q], z.y, acc[t].y);
-                            }
+                    for (int q = 0; q < 4; ++q) {
+                        const int t = 4 * t4 + q;
+                        if (t < R) {
+                            acc[t].x = fmaf(ww[q], z.x, acc[t].x);
+                            acc[t].y = fmaf(ww[q], z.y, acc[t].y);
                         }
                     }
                 }
-                float2* xo = X + (size_t)j * R * CTp + k * mr + c;
-#pragma unroll
-                for (int t = 0; t < R; ++t) xo[t * CTp] = acc[t];
             }
+            float2* xo = Xof(u) + (size_t)j * R * CTp + k * mr + c;
+#pragma unroll
+            for (int t = 0; t < R; ++t) xo[t * CTp] = acc[t];
         }
     }
     __syncthreads();
 
-    // ---- H levels (Eq. 2), in place
-    const int col = tid & (CTp - 1);
+    // ---- H levels (Eq. 2), in place; item (u, grp, col)
     for (int j = 1; j <= K; ++j) {
         if (j > 1) {
             if (j < K) cp_wait1(); else cp_wait0();
@@ -296,12 +318,13 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
         }
         const int kj = K - j, half = 1 << kj;
         const float* Mh = MHTs + (size_t)(j - 1) * 2 * R * R4;
-        const float2* Eh = EHb + (size_t)((j - 1) & 1) * T * 2 * R;
-        for (int grp = tid >> lct; grp < T / 2; grp += kThreads >> lct) {
+        for (int it = tid; it < tpc * (T / 2) * CTp; it += kThreads) {
+            const int col = it & (CTp - 1), grp = (it >> lct) & (T / 2 - 1), u = it >> (lct + K - 1);
             const int a = grp >> kj, bp = grp & (half - 1);
             const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
-            float2* x0 = X + (size_t)base * R * CTp + col;
+            float2* x0 = Xof(u) + (size_t)base * R * CTp + col;
             float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
+            const float2* Eh = EHof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
             h_item<R>(x0, x1, CTp, Eh + (size_t)((2 * a) * half + bp) * 2 * R,
                       Eh + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mh);
         }
@@ -312,17 +335,17 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
         }
     }
 
-    // ---- switch (step 4) and write-out of the switch-level coefficients
-    float2* Wout = A.W + (size_t)slice * P * R * CTp;
-    for (int lp = tid >> lct; lp < T; lp += kThreads >> lct) {
+    // ---- switch (step 4) and write-out of the switch-level coefficients; item (u, lp, col)
+    for (int it = tid; it < tpc * T * CTp; it += kThreads) {
+        const int col = it & (CTp - 1), lp = (it >> lct) & (T - 1), u = it >> (lct + K);
         const int slot = (int)brev((unsigned)lp, K);
-        const float2* xs = X + (size_t)slot * R * CTp + col;
+        const float2* xs = Xof(u) + (size_t)slot * R * CTp + col;
         float2 mu[R];
 #pragma unroll
         for (int s = 0; s < R; ++s) mu[s] = xs[s * CTp];
-        const int64_t q = ((p << K) + lp) * nBh + c0;
+        const int64_t q = ((p_of(u) << K) + lp) * nBh + c0_of(u);
         const float4* Sp = reinterpret_cast<const float4*>(A.S + q * R * R);
-        float2* wo = Wout + (size_t)q * R * CTp + col;
+        float2* wo = A.W + (size_t)slice_of(u) * P * R * CTp + (size_t)q * R * CTp + col;
 #pragma unroll
         for (int t = 0; t < R; ++t) {
             float2 acc = make_float2(0.f, 0.f);
@@ -338,14 +361,17 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
 }
 
 // ------------------------------------------------------------------- back --
-// Shared memory: X [T][R][CTp] | FG double buffer [2][T][2][R] | EU [XN] |
-// U accumulator [XN][mr] | MG^T [kG][2][R][R4] | MU [NU][R4].
+// Shared memory: MG^T [kG][2][R][R4] | MU [NU][R4] | U accumulator [XN][mr] |
+// per chunk u < tpc: X [T][R][CTp] | FG double buffer [2][T][2][R] | EU [XN].
+// The 2^l1 chunks c0' of T_Omega nodes are taken tpc at a time: their loads and
+// G levels run together, their U contributions are accumulated one chunk after
+// the other in increasing c0' (the same order for any tpc).
 template <int R, int NU>
 __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsigned char* smem_raw)
 {
     constexpr int R4 = Pad4<R>::v;
     const Geo& g = A.g;
-    const int K = g.kG, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra;
+    const int K = g.kG, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra, tpc = A.tpc;
     const int slice = (int)(work % A.nslice);
     const int64_t pp = work / A.nslice;           // x-node at level h
     const int nC = 1 << g.l1;                      // chunks c0' (= T_Omega nodes at level l1)
@@ -353,40 +379,46 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
     const int XN = T * NU;                         // output points of this CTA
     const int64_t N = g.N, P = g.P;
     const int L = g.L, h = g.h;
+    const size_t chunk_f2 = (size_t)T * R * CTp + (size_t)2 * T * 2 * R + XN;
 
-    float2* X = reinterpret_cast<float2*>(smem_raw);    // [T][R][CTp]
-    float2* FGb = X + (size_t)T * R * CTp;               // [2][T][2][R]
-    float2* EUs = FGb + (size_t)2 * T * 2 * R;           // [XN]
-    float2* acc = EUs + XN;                              // [XN][mr]
-    float* MGTs = reinterpret_cast<float*>(acc + (size_t)XN * mr);  // [K][2][R][R4]
-    float* MUs = MGTs + (size_t)K * 2 * R * R4;                      // [NU][R4]
+    float* MGTs = reinterpret_cast<float*>(smem_raw);                 // [K][2][R][R4]
+    float* MUs = MGTs + (size_t)K * 2 * R * R4;                       // [NU][R4]
+    float2* acc = reinterpret_cast<float2*>(MUs + (size_t)NU * R4);   // [XN][mr]
+    float2* chunks = acc + (size_t)XN * mr;
+    auto Xof = [&](int u) { return chunks + (size_t)u * chunk_f2; };             // [T][R][CTp]
+    auto FGof = [&](int u) { return Xof(u) + (size_t)T * R * CTp; };             // [2][T][2][R]
+    auto EUof = [&](int u) { return FGof(u) + (size_t)2 * T * 2 * R; };          // [XN]
 
     const int tid = threadIdx.x;
     const int64_t x0g = pp * XN;
     const float2* FGg = A.FG;
-    int c0 = 0;
-    auto stage_fg = [&](int j) {  // phases of level h + j into buffer (j - 1) & 1
+    int c0b = 0;
+    auto stage_fg = [&](int j) {  // phases of level h + j into buffer (j - 1) & 1 of every chunk
         const int64_t nBl = (int64_t)1 << (L - h - j);
         const float2* fg = FGg + (size_t)(j - 1) * P * 2 * R;
-        float2* dst = FGb + (size_t)((j - 1) & 1) * T * 2 * R;
-        for (int e = tid; e < T * R; e += kThreads) {
-            const int lp = e / R, w = e - lp * R;
-            const int64_t ap = (pp << j) + (lp >> (K - j));
-            const int64_t bp = ((int64_t)c0 << (K - j)) + (lp & ((1 << (K - j)) - 1));
-            cp16(dst + (size_t)lp * 2 * R + 2 * w, fg + (ap * nBl + bp) * 2 * R + 2 * w);
+        for (int u = 0; u < tpc; ++u) {
+            float2* dst = FGof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
+            for (int e = tid; e < T * R; e += kThreads) {
+                const int lp = e / R, w = e - lp * R;
+                const int64_t ap = (pp << j) + (lp >> (K - j));
+                const int64_t bp = ((int64_t)(c0b + u) << (K - j)) + (lp & ((1 << (K - j)) - 1));
+                cp16(dst + (size_t)lp * 2 * R + 2 * w, fg + (ap * nBl + bp) * 2 * R + 2 * w);
+            }
         }
     };
     stage_matrix(MGTs, A.MGT, K * 2 * R, R, R4, tid);
     stage_matrix(MUs, A.MU, NU, R, R4, tid);
     for (int e = tid; e < XN * mr; e += kThreads) acc[e] = make_float2(0.f, 0.f);
     const float2* Win = A.W + (size_t)slice * P * R * CTp;
-    const int col = tid & (CTp - 1);
 
-    for (c0 = 0; c0 < nC; ++c0) {
-        __syncthreads();  // the previous chunk's U stage is done with X and EU
-        {   // pairs (pp, c0 * T + j), j < T: one contiguous block of T*R*CTp
+    for (c0b = 0; c0b < nC; c0b += tpc) {
+        __syncthreads();  // the previous chunks' U stage is done with X and EU
+        for (int u = 0; u < tpc; ++u) {  // pairs (pp, c0 * T + j), j < T: one contiguous block of T*R*CTp
+            const int c0 = c0b + u;
             const float2* src = Win + (size_t)(pp * nBh + (int64_t)c0 * T) * R * CTp;
+            float2* X = Xof(u);
             for (int e = tid; e < T * R * CTp / 2; e += kThreads) cp16(X + 2 * e, src + 2 * e);
+            float2* EUs = EUof(u);
             for (int e = tid; e < XN / 2; e += kThreads) cp16(EUs + 2 * e, A.EU + (size_t)c0 * N + x0g + 2 * e);
         }
         if (K >= 1) stage_fg(1);
@@ -398,7 +430,7 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
         if (K >= 2) cp_wait1(); else cp_wait0();
         __syncthreads();
 
-        // ---- G levels (Eq. 3), in place
+        // ---- G levels (Eq. 3), in place; item (u, grp, col)
         for (int j = 1; j <= K; ++j) {
             if (j > 1) {
                 if (j < K) cp_wait1(); else cp_wait0();
@@ -406,12 +438,13 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
             }
             const int kj = K - j, half = 1 << kj;
             const float* Mg = MGTs + (size_t)(j - 1) * 2 * R * R4;
-            const float2* Fg = FGb + (size_t)((j - 1) & 1) * T * 2 * R;
-            for (int grp = tid >> lct; grp < T / 2; grp += kThreads >> lct) {
+            for (int it = tid; it < tpc * (T / 2) * CTp; it += kThreads) {
+                const int col = it & (CTp - 1), grp = (it >> lct) & (T / 2 - 1), u = it >> (lct + K - 1);
                 const int a = grp >> kj, bp = grp & (half - 1);
                 const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
-                float2* x0 = X + (size_t)base * R * CTp + col;
+                float2* x0 = Xof(u) + (size_t)base * R * CTp + col;
                 float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
+                const float2* Fg = FGof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
                 g_item<R>(x0, x1, CTp, Fg + (size_t)((2 * a) * half + bp) * 2 * R,
                           Fg + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mg);
             }
@@ -422,38 +455,42 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
             }
         }
 
-        // ---- U (Eq. bf3) contribution of T_Omega node c0 to this CTA's points
+        // ---- U (Eq. bf3) contributions of T_Omega nodes c0b .. c0b + tpc - 1, in that order;
+        // each accumulator entry (lp, i, c) belongs to one thread
         {
             const int c = tid & (mr - 1);
             for (int lp = tid >> lmr; lp < T; lp += kThreads >> lmr) {
                 const int slot = (int)brev((unsigned)lp, K);
-                const float2* xs = X + (size_t)slot * R * CTp + c;
                 float2* ap = acc + (size_t)lp * NU * mr + c;
-                for (int k = 0; k < ra; ++k) {
-                    float2 v[R];
+                for (int u = 0; u < tpc; ++u) {
+                    const float2* xs = Xof(u) + (size_t)slot * R * CTp + c;
+                    const float2* EUs = EUof(u);
+                    for (int k = 0; k < ra; ++k) {
+                        float2 v[R];
 #pragma unroll
-                    for (int s = 0; s < R; ++s) v[s] = xs[s * CTp + k * mr];
-                    const float2* ak = A.ak + (size_t)k * N + x0g + lp * NU;
+                        for (int s = 0; s < R; ++s) v[s] = xs[s * CTp + k * mr];
+                        const float2* ak = A.ak + (size_t)k * N + x0g + lp * NU;
 #pragma unroll 4
-                    for (int i = 0; i < NU; ++i) {
-                        float2 w = make_float2(0.f, 0.f);
-                        const float4* mu = reinterpret_cast<const float4*>(MUs + i * R4);
+                        for (int i = 0; i < NU; ++i) {
+                            float2 w = make_float2(0.f, 0.f);
+                            const float4* mu = reinterpret_cast<const float4*>(MUs + i * R4);
 #pragma unroll
-                        for (int s4 = 0; s4 < R4 / 4; ++s4) {
-                            const float4 m4 = mu[s4];
-                            const float mm[4] = {m4.x, m4.y, m4.z, m4.w};
+                            for (int s4 = 0; s4 < R4 / 4; ++s4) {
+                                const float4 m4 = mu[s4];
+                                const float mm[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const int s = 4 * s4 + q;
-                                if (s < R) {
-                                    w.x = fmaf(mm[q], v[s].x, w.x);
-                                    w.y = fmaf(mm[q], v[s].y, w.y);
+                                for (int q = 0; q < 4; ++q) {
+                                    const int s = 4 * s4 + q;
+                                    if (s < R) {
+                                        w.x = fmaf(mm[q], v[s].x, w.x);
+                                        w.y = fmaf(mm[q], v[s].y, w.y);
+                                    }
                                 }
                             }
+                            float2 o = ap[i * mr];
+                            cfmaf(o, cmulf(__ldg(ak + i), EUs[lp * NU + i]), w);
+                            ap[i * mr] = o;
                         }
-                        float2 o = ap[i * mr];
-                        cfmaf(o, cmulf(__ldg(ak + i), EUs[lp * NU + i]), w);
-                        ap[i * mr] = o;
                     }
                 }
             }
@@ -500,18 +537,18 @@ int ilog2(int v)
     return l;
 }
 
-size_t front_smem(const Geo& g, int R, int NV, int CTp, int mr)
+size_t front_smem(const Geo& g, int R, int NV, int CTp, int mr, int tpc)
 {
     const size_t T = (size_t)1 << g.kH, R4 = (R + 3) & ~3;
-    return sizeof(float2) * (T * R * CTp + 2 * T * 2 * R + T * NV + T * NV * mr) +
+    return sizeof(float2) * (size_t)tpc * (T * R * CTp + 2 * T * 2 * R + T * NV + T * NV * mr) +
            sizeof(float) * ((size_t)NV * R4 + (size_t)g.kH * 2 * R * R4);
 }
 
-size_t back_smem(const Geo& g, int R, int NU, int CTp, int mr)
+size_t back_smem(const Geo& g, int R, int NU, int CTp, int mr, int tpc)
 {
     const size_t T = (size_t)1 << g.kG, R4 = (R + 3) & ~3;
     const size_t XN = T * NU;
-    return sizeof(float2) * (T * R * CTp + 2 * T * 2 * R + XN + XN * mr) +
+    return sizeof(float2) * (XN * mr + (size_t)tpc * (T * R * CTp + 2 * T * 2 * R + XN)) +
            sizeof(float) * ((size_t)g.kG * 2 * R * R4 + (size_t)NU * R4);
 }
 
@@ -640,7 +677,7 @@ FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint)
     const int NV = g.nv;
     auto smem = [&](int mr) {
         const int CTp = 1 << ilog2(ra * mr);
-        return std::max(front_smem(g, g.r, NV, CTp, mr), back_smem(g, g.r, NV, CTp, mr));
+        return std::max(front_smem(g, g.r, NV, CTp, mr, 1), back_smem(g, g.r, NV, CTp, mr, 1));
     };
     int mr;
     if (mr_hint > 0 && (mr_hint & (mr_hint - 1)) == 0 && (1 << ilog2(ra * mr_hint)) <= 256 &&
@@ -660,6 +697,19 @@ FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint)
     FusedCfg c;
     c.mr = mr;
     c.nslice = (int)((m + mr - 1) / mr);
+    // with few columns per tile, several front tiles (back chunks) per CTA: up to one
+    // (tile, group, column) item per thread and level, two CTAs per SM
+    const int CTp = 1 << ilog2(ra * mr);
+    const int itemsH = std::max(1, (1 << g.kH) / 2) * CTp, itemsG = std::max(1, (1 << g.kG) / 2) * CTp;
+    const int64_t maxf = (int64_t)1 << (g.l1 + g.L - g.h), maxb = (int64_t)1 << g.l1;
+    c.tpc_f = 1;
+    while (c.tpc_f < 16 && 2 * c.tpc_f <= maxf && 2 * c.tpc_f * itemsH <= kThreads &&
+           front_smem(g, g.r, NV, CTp, mr, 2 * c.tpc_f) <= 113 * 1024)
+        c.tpc_f *= 2;
+    c.tpc_b = 1;
+    while (c.tpc_b < 16 && 2 * c.tpc_b <= maxb && 2 * c.tpc_b * itemsG <= kThreads &&
+           back_smem(g, g.r, NV, CTp, mr, 2 * c.tpc_b) <= 113 * 1024)
+        c.tpc_b *= 2;
     return c;
 }
 
@@ -687,6 +737,7 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     fa->CTp = CTp;
     fa->lct = ilog2(CTp);
     fa->nslice = cfg.nslice;
+    fa->tpc = cfg.tpc_f;
     fa->bk = B.f32.b;
     fa->MvT = B.f32.Mv;
     fa->EV = B.f32.EV;
@@ -701,6 +752,7 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     ba->CTp = CTp;
     ba->lct = fa->lct;
     ba->nslice = cfg.nslice;
+    ba->tpc = cfg.tpc_b;
     ba->W = ws;
     ba->MGT = B.f32.MG;
     ba->FG = B.f32.FG;
@@ -709,9 +761,9 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     ba->ak = B.f32.a;
     ba->G = G;
     ba->beta = beta;
-    *sf = front_smem(g, g.r, NV, CTp, cfg.mr);
-    *sb = back_smem(g, g.r, NV, CTp, cfg.mr);
-    *nfront = ((int64_t)1 << g.l1) * ((int64_t)1 << (g.L - g.h)) * cfg.nslice;
+    *sf = front_smem(g, g.r, NV, CTp, cfg.mr, cfg.tpc_f);
+    *sb = back_smem(g, g.r, NV, CTp, cfg.mr, cfg.tpc_b);
+    *nfront = ((int64_t)1 << g.l1) * ((int64_t)1 << (g.L - g.h)) * cfg.nslice / cfg.tpc_f;
     *nback = ((int64_t)1 << g.h) * cfg.nslice;
     return true;
 }
