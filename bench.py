@@ -208,7 +208,7 @@ def cpu_oracle_rate(w, F, G_gpu, budget_s, max_rows=None):
     from paper_1803_04128_gb300 import inputs
     N, m = w["N"], w["m"]
     kind = w["phase"]
-    probe = inputs.sample_rows(N, 8, seed=11)
+    probe = inputs.sample_rows(N, min(N, 64), seed=11)   # enough rows to keep every host thread busy
     t0 = time.perf_counter()
     od.direct(kind, N, F, probe, amp=w["amp"])
     per_row = (time.perf_counter() - t0) / probe.size
