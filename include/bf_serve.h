@@ -8,7 +8,8 @@
  * stream with its own staging buffers and workspace) is free, it takes the
  * oldest pending request's operator and packs as many of that operator's
  * pending requests as fit (column-concatenated right-hand sides) into one
- * apply; requests that arrive while slots are busy wait for the next free
+ * apply (a priority slot takes the oldest small request and packs up to the
+ * small-batch size); requests that arrive while slots are busy wait for the next free
  * slot; the S slots' batches run concurrently on the device.  Each request's
  * result is bit-identical to applying its operator to that request alone
  * (columns never mix).  The paper has no serving component: this rests on its
@@ -33,6 +34,12 @@ typedef struct {
     int precision;          /* BF_PREC_F32 (default) or BF_PREC_F64                              */
     int per_request;        /* 1: no batching, one request per apply (the plain per-request form) */
     int device;             /* CUDA device (default 0)                                           */
+    int n_priority_slots;   /* slots on highest-priority streams that take only small batches
+                               (default n_slots / 2; 0: none).  Their kernels' CTAs are
+                               scheduled ahead of the other slots', so small requests do not
+                               queue behind large applies                                       */
+    int64_t small_units;    /* a batch is small if N * (its right-hand sides) <= this
+                               (default 2^21)                                                   */
 } bf_server_options;
 
 typedef struct {

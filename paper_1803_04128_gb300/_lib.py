@@ -42,7 +42,8 @@ class BatchItem(ctypes.Structure):
 
 class ServerOptions(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int), ("hbm_budget", ctypes.c_int64), ("max_batch_rhs", ctypes.c_int64),
-                ("precision", ctypes.c_int), ("per_request", ctypes.c_int), ("device", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("per_request", ctypes.c_int), ("device", ctypes.c_int),
+                ("n_priority_slots", ctypes.c_int), ("small_units", ctypes.c_int64)]
 
 
 class ServerStats(ctypes.Structure):

@@ -45,6 +45,7 @@ struct Op {
 
 struct Slot {
     cudaStream_t st = nullptr;
+    bool hi = false;  // highest-priority stream, small batches only
     cudaEvent_t ev = nullptr;
     void* F = nullptr;
     void* G = nullptr;
@@ -140,24 +141,28 @@ void scheduler(bf_server* s)
         bool launched = false;
         for (auto& sl : s->slots) {
             if (sl.busy) continue;
-            // operator of the oldest pending request
+            // operator of the oldest pending request (a priority slot: of the oldest small one)
+            const int64_t small = s->opt.small_units > 0 ? s->opt.small_units : ((int64_t)1 << 21);
             int best = -1;
             Clock::time_point bt{};
             for (size_t i = 0; i < s->ops.size(); ++i) {
                 auto& q = s->ops[i].pending;
                 if (q.empty()) continue;
-                const auto t = s->reqs[q.front()].t_submit;
-                if (best < 0 || t < bt) {
+                const Req& fr = s->reqs[q.front()];
+                if (sl.hi && s->ops[i].N * fr.m > small) continue;
+                if (best < 0 || fr.t_submit < bt) {
                     best = (int)i;
-                    bt = t;
+                    bt = fr.t_submit;
                 }
             }
-            if (best < 0) break;
+            if (best < 0) continue;
             Op& op = s->ops[(size_t)best];
+            const int64_t cap = sl.hi ? std::max<int64_t>(1, std::min(op.cap, small / op.N)) : op.cap;
             std::vector<Req*> rs;
             int64_t cols = 0;
             while (!op.pending.empty()) {
                 Req& r = s->reqs[op.pending.front()];
+                if (cols + r.m > cap && !rs.empty()) break;
                 if (cols + r.m > op.cap) break;
                 cols += r.m;
                 sl.reqs.push_back(op.pending.front());
@@ -221,6 +226,8 @@ bf_status bf_server_default_options(bf_server_options* o)
     o->precision = BF_PREC_F32;
     o->per_request = 0;
     o->device = 0;
+    o->n_priority_slots = -1;  // n_slots / 2
+    o->small_units = 0;        // 2^21
     return BF_OK;
 }
 
@@ -342,9 +349,14 @@ bf_status bf_server_start(bf_server* s)
         ws = std::max(ws, device_ws_bytes(op.plan, (bf_precision)s->opt.precision, m));
     }
     s->slots.resize((size_t)s->opt.n_slots);
-    for (auto& sl : s->slots) {
+    int pri_lo = 0, pri_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&pri_lo, &pri_hi);
+    const int nhi = s->opt.n_priority_slots < 0 ? s->opt.n_slots / 2 : std::min(s->opt.n_priority_slots, s->opt.n_slots);
+    for (size_t i = 0; i < s->slots.size(); ++i) {
+        Slot& sl = s->slots[i];
+        sl.hi = (int)i < nhi;
         cudaError_t e;
-        if ((e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking)) != cudaSuccess ||
+        if ((e = cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.hi ? pri_hi : pri_lo)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaMalloc(&sl.F, slab)) != cudaSuccess || (e = cudaMalloc(&sl.G, slab)) != cudaSuccess ||
             (e = cudaMalloc(&sl.ws, ws)) != cudaSuccess) {
