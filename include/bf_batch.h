@@ -74,6 +74,31 @@ void bf_batch_destroy(bf_batch* batch); /* NULL-safe */
  * *mr_out (nullable) receives the choice.  Allocates temporaries. */
 bf_status bf_autotune(bf_plan* plan, int64_t m, const char* cache_path, int* mr_out);
 
+/* One right-hand-side block of bf_apply_batched: G = K F, device [N][m] c64,
+ * caller-owned, G not aliasing F. */
+typedef struct {
+    const void* F;
+    void* G;
+    int64_t m;
+} bf_apply_item;
+
+/* One-call batched apply: G_i = K_{plans[i]} F_i for every i < n_items, in one
+ * persistent launch on `stream` (FP32 fused apply; the many-vector apply of the
+ * precomputed factorisation, Sec. 1 and Sec. 4, for operators of different N).
+ * Asynchronous.  The calling thread keeps the batch it built for the last
+ * (plans, m) list: a call with the same list reuses its workspace and work list,
+ * replacing only the F and G pointers (uploaded on `stream`), so it allocates
+ * nothing; a different list rebuilds it (freeing the old one synchronizes the
+ * device).  Calls that reuse the kept batch are ordered by the caller (same
+ * stream, or the previous call's stream waited on).  Same restrictions as
+ * bf_batch_create.  Errors: BF_ERR_ARG (NULL pointers, n_items < 1, m < 1), and
+ * those of bf_batch_create and bf_batch_run. */
+bf_status bf_apply_batched(bf_plan* const* plans, const bf_apply_item* items, int n_items, void* stream);
+
+/* Free the batch bf_apply_batched keeps for the calling thread (synchronizes the
+ * device).  NULL-safe to call when there is none. */
+void bf_apply_batched_release(void);
+
 #ifdef __cplusplus
 }
 #endif

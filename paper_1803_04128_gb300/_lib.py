@@ -40,6 +40,10 @@ class BatchItem(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("F", ctypes.c_void_p), ("G", ctypes.c_void_p), ("m", ctypes.c_int64)]
 
 
+class ApplyItem(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_void_p), ("G", ctypes.c_void_p), ("m", ctypes.c_int64)]
+
+
 class ServerOptions(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int), ("hbm_budget", ctypes.c_int64), ("max_batch_rhs", ctypes.c_int64),
                 ("precision", ctypes.c_int), ("per_request", ctypes.c_int), ("device", ctypes.c_int),
@@ -98,6 +102,8 @@ _SIGS = {
     "bf_batch_set_spin_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
     "bf_batch_debug_hold": (ctypes.c_int, [_P, ctypes.c_int]),
     "bf_batch_destroy": (None, [_P]),
+    "bf_apply_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _P]),
+    "bf_apply_batched_release": (None, []),
     "bf_autotune": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
     "bf_server_default_options": (ctypes.c_int, [ctypes.POINTER(ServerOptions)]),
     "bf_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOptions), ctypes.POINTER(_P)]),

@@ -172,6 +172,27 @@ def autotune(plan, m, cache_path=None):
     return mr.value
 
 
+def apply_batched(items, stream=None):
+    """One-call batched FP32 apply (bf_apply_batched): ``items`` is a list of
+    (plan, F, G), F and G contiguous CUDA complex64 tensors of shape (N, m).
+    Asynchronous on ``stream``; repeated calls with the same plans and m reuse
+    the thread's kept batch (no allocation)."""
+    lib = L.lib()
+    n = len(items)
+    plans = (ctypes.c_void_p * n)()
+    arr = (L.ApplyItem * n)()
+    for i, (plan, F, G) in enumerate(items):
+        plans[i] = plan._h.value
+        arr[i].F, arr[i].G, arr[i].m = F.data_ptr(), G.data_ptr(), 1 if F.dim() == 1 else F.shape[1]
+    L.check(lib.bf_apply_batched(ctypes.cast(plans, ctypes.c_void_p), ctypes.cast(arr, ctypes.c_void_p), n,
+                                 _stream_ptr(stream)), "bf_apply_batched")
+
+
+def apply_batched_release():
+    """Free the calling thread's kept batch (bf_apply_batched_release)."""
+    L.lib().bf_apply_batched_release()
+
+
 class Batch:
     """Many operators of different N and m applied in one persistent launch
     (bf_batch_*).  ``items``: list of (plan, F, G) with F, G contiguous CUDA

@@ -328,6 +328,65 @@ bf_status bf_batch_debug_hold(bf_batch* b, int on)
 
 void bf_batch_destroy(bf_batch* b) { free_batch(b); }
 
+// ---------------------------------------------------------- one-call form --
+namespace {
+struct KeptBatch {
+    std::vector<const bf_plan*> plans;
+    std::vector<int64_t> ms;
+    bf_batch* b = nullptr;  // not freed at thread exit (the CUDA context may be gone)
+};
+thread_local KeptBatch tl_kept;
+}  // namespace
+
+bf_status bf_apply_batched(bf_plan* const* plans, const bf_apply_item* items, int n, void* stream)
+{
+    if (!plans || !items || n < 1) {
+        set_error("bf_apply_batched: NULL arguments or n_items < 1");
+        return BF_ERR_ARG;
+    }
+    for (int i = 0; i < n; ++i)
+        if (!plans[i] || !items[i].F || !items[i].G || items[i].m < 1) {
+            set_error("bf_apply_batched: item %d: NULL plan/F/G or m < 1", i);
+            return BF_ERR_ARG;
+        }
+    KeptBatch& k = tl_kept;
+    bool same = k.b && (int)k.plans.size() == n;
+    for (int i = 0; same && i < n; ++i) same = k.plans[(size_t)i] == plans[i] && k.ms[(size_t)i] == items[i].m;
+    if (same) {
+        bf_batch* b = k.b;
+        for (int i = 0; i < n; ++i) {
+            b->items[(size_t)i].fa.F = (const float2*)items[i].F;
+            b->items[(size_t)i].ba.G = (float2*)items[i].G;
+        }
+        cudaError_t e = cudaSetDevice(b->device);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->dmem, b->items.data(), (size_t)n * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                                (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail("bf_apply_batched: descriptor upload", e);
+        return enqueue(b, (cudaStream_t)stream);
+    }
+    bf_apply_batched_release();
+    std::vector<bf_batch_item> in((size_t)n);
+    for (int i = 0; i < n; ++i) in[(size_t)i] = bf_batch_item{plans[i], items[i].F, items[i].G, items[i].m};
+    bf_batch* b = nullptr;
+    bf_status st = bf_batch_create(in.data(), n, &b);
+    if (st != BF_OK) return st;
+    k.b = b;
+    k.plans.assign(plans, plans + n);
+    k.ms.resize((size_t)n);
+    for (int i = 0; i < n; ++i) k.ms[(size_t)i] = items[i].m;
+    return bf_batch_run(b, stream);
+}
+
+void bf_apply_batched_release(void)
+{
+    KeptBatch& k = tl_kept;
+    if (k.b) free_batch(k.b);
+    k.b = nullptr;
+    k.plans.clear();
+    k.ms.clear();
+}
+
 // ---------------------------------------------------------------- autotune --
 bf_status bf_autotune(bf_plan* p, int64_t m, const char* cache_path, int* mr_out)
 {

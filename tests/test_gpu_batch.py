@@ -114,3 +114,39 @@ def test_batch_rejects_mixed_rank_and_split():
     F2 = torch.zeros((2048, 1), dtype=torch.complex64, device="cuda")
     with pytest.raises(L.BFError):
         api.Batch([(ps, F2, torch.empty_like(F2))])
+
+
+def test_apply_batched_one_call_reuses_kept_batch():
+    ops = make_ops(SHAPES[:4], seed=30)
+    s = torch.cuda.current_stream()
+    api.apply_batched(ops, s)                    # builds and keeps the batch
+    torch.cuda.synchronize()
+    for plan, F, G in ops:
+        assert torch.equal(G, plan.apply(F, prec=api.F32))
+    # same plans and m, new buffers: only the F/G pointers change
+    ops2 = [(plan, torch.from_numpy(inputs.complex_gaussian(F.shape[0], F.shape[1], seed=40 + k))
+             .to(torch.complex64).cuda(), torch.full_like(G, float("nan"))) for k, (plan, F, G) in enumerate(ops)]
+    api.apply_batched(ops2, s)
+    torch.cuda.synchronize()
+    for plan, F, G in ops2:
+        assert torch.equal(G, plan.apply(F, prec=api.F32))
+    # a different m list rebuilds
+    plan0, F0, _ = ops[0]
+    F3 = torch.cat([F0, F0], dim=1).contiguous()
+    G3 = torch.empty_like(F3)
+    api.apply_batched([(plan0, F3, G3)], s)
+    torch.cuda.synchronize()
+    assert torch.equal(G3, plan0.apply(F3, prec=api.F32))
+    api.apply_batched_release()
+
+
+def test_apply_batched_rejects_bad_items():
+    plan, F, G = make_ops([(1024, 2)])[0]
+    lib = L.lib()
+    import ctypes
+    plans = (ctypes.c_void_p * 1)(plan._h.value)
+    arr = (L.ApplyItem * 1)()
+    arr[0].F, arr[0].G, arr[0].m = F.data_ptr(), G.data_ptr(), 0
+    assert lib.bf_apply_batched(ctypes.cast(plans, ctypes.c_void_p), ctypes.cast(arr, ctypes.c_void_p), 1,
+                                None) == L.BF_ERR_ARG
+    assert lib.bf_apply_batched(None, ctypes.cast(arr, ctypes.c_void_p), 1, None) == L.BF_ERR_ARG
