@@ -104,6 +104,9 @@ _SIGS = {
     "bf_batch_destroy": (None, [_P]),
     "bf_apply_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _P]),
     "bf_apply_batched_release": (None, []),
+    "bf_shard_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "bf_apply_shard_front": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int64, _P, _P]),
+    "bf_apply_shard_back": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int64, _P, _P]),
     "bf_autotune": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
     "bf_server_default_options": (ctypes.c_int, [ctypes.POINTER(ServerOptions)]),
     "bf_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOptions), ctypes.POINTER(_P)]),

@@ -193,6 +193,53 @@ def apply_batched_release():
     L.lib().bf_apply_batched_release()
 
 
+class ShardedApply:
+    """One operator applied by ``nshard`` shards (bf_shard.h): shard s holds the
+    rows [s N/G, (s+1) N/G) of F and of G, applies the xi-side half (front) to
+    its rows, the switch-level coefficients are exchanged all-to-all, and it
+    applies the x-side half (back).  ``apply_distributed`` runs one shard per
+    rank of a torch.distributed group; ``apply_local`` runs every shard in this
+    process on one device (the exchange becomes a block transpose)."""
+
+    def __init__(self, plan, nshard, m):
+        self.plan, self.G, self.m = plan, int(nshard), int(m)
+        c = ctypes.c_int64()
+        L.check(L.lib().bf_shard_info(plan._h, self.G, self.m, ctypes.byref(c)), "bf_shard_info")
+        self.chunk = c.value                      # c64 elements per peer block
+        self.rows = plan.info()["N"] // self.G
+
+    def front(self, shard, F_rows, W_send, stream=None):
+        L.check(L.lib().bf_apply_shard_front(self.plan._h, self.G, int(shard), ctypes.c_void_p(F_rows.data_ptr()),
+                                             self.m, ctypes.c_void_p(W_send.data_ptr()), _stream_ptr(stream)),
+                "bf_apply_shard_front")
+
+    def back(self, shard, W_recv, G_rows, stream=None):
+        L.check(L.lib().bf_apply_shard_back(self.plan._h, self.G, int(shard), ctypes.c_void_p(W_recv.data_ptr()),
+                                            self.m, ctypes.c_void_p(G_rows.data_ptr()), _stream_ptr(stream)),
+                "bf_apply_shard_back")
+
+    def apply_distributed(self, F_rows, G_rows, group=None, stream=None):
+        """This rank's shard: front, one all-to-all of equal blocks, back."""
+        import torch
+        import torch.distributed as dist
+        rank = dist.get_rank(group)
+        send = torch.empty(self.G * self.chunk, dtype=torch.complex64, device=F_rows.device)
+        recv = torch.empty_like(send)
+        self.front(rank, F_rows, send, stream)
+        dist.all_to_all_single(torch.view_as_real(recv), torch.view_as_real(send), group=group)
+        self.back(rank, recv, G_rows, stream)
+
+    def apply_local(self, F, G):
+        """All shards in this process: F, G (N, m) complex64 on one device."""
+        import torch
+        send = torch.empty((self.G, self.G * self.chunk), dtype=torch.complex64, device=F.device)
+        for s in range(self.G):
+            self.front(s, F[s * self.rows:(s + 1) * self.rows], send[s])
+        recv = send.view(self.G, self.G, self.chunk).transpose(0, 1).contiguous().view(self.G, -1)
+        for d in range(self.G):
+            self.back(d, recv[d], G[d * self.rows:(d + 1) * self.rows])
+
+
 class Batch:
     """Many operators of different N and m applied in one persistent launch
     (bf_batch_*).  ``items``: list of (plan, F, G) with F, G contiguous CUDA

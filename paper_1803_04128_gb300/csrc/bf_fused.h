@@ -6,6 +6,18 @@
 
 namespace bfi {
 
+// Layout of the switch-level workspace W, in units of pairs (each R x CTp c64).
+// Pair (a, b) of column slice sl (a: x-node at level h, b: T_Omega node at level
+// L-h) is at  d * sD + s * sS + sl * slice + (a_loc << lb) + b_loc  with
+// d = a >> la, a_loc = a mod 2^la, s = b >> lb, b_loc = b mod 2^lb.  One shard
+// (the default): la = h, lb = L-h, sD = sS = 0, slice = P, i.e. a * 2^(L-h) + b.
+// G shards: la = h - log2 G, lb = L-h - log2 G; a front's send buffer has
+// sD = nslice * 2^(la+lb), sS = 0; a back's receive buffer sS = that, sD = 0.
+struct WLayout {
+    int la, lb;
+    int64_t sD, sS, slice;
+};
+
 struct FrontArgs {
     Geo g;
     const float2* F;  // [N][m]
@@ -18,7 +30,10 @@ struct FrontArgs {
     const float* MHT;  // [kH][2R][R]
     const float2* EH;  // [kH][P][2][R]
     const float2* S;   // [P][R][R]
-    float2* W;         // [nslice][P][R][CTp]
+    float2* W;         // switch-level coefficients, layout wl
+    WLayout wl;
+    int64_t c0_lo;     // first T_Omega node (level L-h) of this shard's tiles
+    int64_t xi_lo;     // F holds rows xi_lo ..: row xi at F + (xi - xi_lo) * m
 };
 
 struct BackArgs {
@@ -26,7 +41,10 @@ struct BackArgs {
     int64_t m;
     int mr, lmr, CTp, lct, nslice;
     int tpc;           // T_Omega chunks processed together (divides 2^l1)
-    const float2* W;
+    const float2* W;   // layout wl
+    WLayout wl;
+    int64_t pp_lo;     // first x-node (level h) of this shard
+    int64_t x_lo;      // G holds rows x_lo ..: row x at G + (x - x_lo) * m
     const float* MGT;  // [kG][2][R][R]  (pos, s, t)
     const float2* FG;  // [kG][P][2][R]
     const float* MU;   // [nv][R]
@@ -61,6 +79,9 @@ struct BatchLaunch {
 
 bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int mr_hint,
                      FrontArgs* fa, BackArgs* ba, size_t* sf, size_t* sb, int64_t* nfront, int64_t* nback);
+// one of the two fused FP32 kernels with prepared arguments (nblocks CTAs)
+cudaError_t launch_f32_front(int r, const FrontArgs& fa, size_t smem, int64_t nblocks, cudaStream_t st);
+cudaError_t launch_f32_back(int r, const BackArgs& ba, size_t smem, int64_t nblocks, cudaStream_t st);
 // set_attr: only set the kernel's shared-memory limit to bl.smem (no launch);
 // grid_out != NULL: only compute the persistent grid (occupancy x SMs) for bl.smem;
 // otherwise launch (bl.grid CTAs).

@@ -77,6 +77,13 @@ __device__ __forceinline__ void stage_matrix(float* dst, const float* src, int r
     }
 }
 
+// pair index of (a, b) of column slice sl in the workspace layout w
+__device__ __forceinline__ int64_t w_pair(const WLayout& w, int64_t a, int64_t b, int sl)
+{
+    const int64_t d = a >> w.la, s = b >> w.lb;
+    return d * w.sD + s * w.sS + sl * w.slice + ((a - (d << w.la)) << w.lb) + (b - (s << w.lb));
+}
+
 template <int R>
 struct Pad4 {
     static constexpr int v = (R + 3) & ~3;
@@ -218,7 +225,7 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
         const int64_t idx = work * tpc + tid, tile = idx / A.nslice;
         s_slice[tid] = (int)(idx - tile * A.nslice);
         s_p[tid] = tile & (nP - 1);
-        s_c0[tid] = tile >> l1;
+        s_c0[tid] = A.c0_lo + (tile >> l1);
     }
     __syncthreads();
     auto slice_of = [&](int u) { return s_slice[u]; };
@@ -253,7 +260,7 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
         for (int e = tid; e < T * NV * mr; e += kThreads) {
             const int row = e >> lmr, c = e & (mr - 1);
             const bool valid = cbase + c < m;
-            cp8(Fs + e, A.F + (xi_base + row) * m + (valid ? cbase + c : 0), valid);
+            cp8(Fs + e, A.F + (xi_base - A.xi_lo + row) * m + (valid ? cbase + c : 0), valid);
         }
     }
     if (K >= 1) stage_eh(1);
@@ -345,7 +352,7 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
         for (int s = 0; s < R; ++s) mu[s] = xs[s * CTp];
         const int64_t q = ((p_of(u) << K) + lp) * nBh + c0_of(u);
         const float4* Sp = reinterpret_cast<const float4*>(A.S + q * R * R);
-        float2* wo = A.W + (size_t)slice_of(u) * P * R * CTp + (size_t)q * R * CTp + col;
+        float2* wo = A.W + (size_t)w_pair(A.wl, (p_of(u) << K) + lp, c0_of(u), slice_of(u)) * R * CTp + col;
 #pragma unroll
         for (int t = 0; t < R; ++t) {
             float2 acc = make_float2(0.f, 0.f);
@@ -373,9 +380,8 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
     const Geo& g = A.g;
     const int K = g.kG, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra, tpc = A.tpc;
     const int slice = (int)(work % A.nslice);
-    const int64_t pp = work / A.nslice;           // x-node at level h
+    const int64_t pp = A.pp_lo + work / A.nslice;  // x-node at level h
     const int nC = 1 << g.l1;                      // chunks c0' (= T_Omega nodes at level l1)
-    const int64_t nBh = (int64_t)1 << (g.L - g.h);
     const int XN = T * NU;                         // output points of this CTA
     const int64_t N = g.N, P = g.P;
     const int L = g.L, h = g.h;
@@ -409,13 +415,12 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
     stage_matrix(MGTs, A.MGT, K * 2 * R, R, R4, tid);
     stage_matrix(MUs, A.MU, NU, R, R4, tid);
     for (int e = tid; e < XN * mr; e += kThreads) acc[e] = make_float2(0.f, 0.f);
-    const float2* Win = A.W + (size_t)slice * P * R * CTp;
 
     for (c0b = 0; c0b < nC; c0b += tpc) {
         __syncthreads();  // the previous chunks' U stage is done with X and EU
         for (int u = 0; u < tpc; ++u) {  // pairs (pp, c0 * T + j), j < T: one contiguous block of T*R*CTp
             const int c0 = c0b + u;
-            const float2* src = Win + (size_t)(pp * nBh + (int64_t)c0 * T) * R * CTp;
+            const float2* src = A.W + (size_t)w_pair(A.wl, pp, (int64_t)c0 * T, slice) * R * CTp;
             float2* X = Xof(u);
             for (int e = tid; e < T * R * CTp / 2; e += kThreads) cp16(X + 2 * e, src + 2 * e);
             float2* EUs = EUof(u);
@@ -503,7 +508,7 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
         const int64_t cg = (int64_t)slice * mr + c;
         if (cg < A.m) {
             for (int x = tid >> lmr; x < XN; x += kThreads >> lmr) {
-                float2* gp = A.G + (x0g + x) * A.m + cg;
+                float2* gp = A.G + (x0g - A.x_lo + x) * A.m + cg;
                 float2 v = acc[x * mr + c];
                 if (A.beta) {
                     const float2 o = *gp;
@@ -745,6 +750,9 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     fa->EH = B.f32.EH;
     fa->S = B.f32.S;
     fa->W = ws;
+    fa->wl = WLayout{g.h, g.L - g.h, 0, 0, g.P};
+    fa->c0_lo = 0;
+    fa->xi_lo = 0;
     ba->g = g;
     ba->m = m;
     ba->mr = cfg.mr;
@@ -754,6 +762,9 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     ba->nslice = cfg.nslice;
     ba->tpc = cfg.tpc_b;
     ba->W = ws;
+    ba->wl = fa->wl;
+    ba->pp_lo = 0;
+    ba->x_lo = 0;
     ba->MGT = B.f32.MG;
     ba->FG = B.f32.FG;
     ba->MU = B.f32.MU;
@@ -766,6 +777,50 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     *nfront = ((int64_t)1 << g.l1) * ((int64_t)1 << (g.L - g.h)) * cfg.nslice / cfg.tpc_f;
     *nback = ((int64_t)1 << g.h) * cfg.nslice;
     return true;
+}
+
+template <int R>
+cudaError_t launch_part_r(const FrontArgs* fa, const BackArgs* ba, size_t smem, int64_t nblocks, cudaStream_t st)
+{
+    constexpr int NV = nv_of<R>();
+    cudaError_t e;
+    if (fa) {
+        if ((e = cudaFuncSetAttribute(front_f32<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        ProfScope ps("front_f32", st);
+        front_f32<R, NV><<<(unsigned)nblocks, kThreads, smem, st>>>(*fa);
+    } else {
+        if ((e = cudaFuncSetAttribute(back_f32<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        ProfScope ps("back_f32", st);
+        back_f32<R, NV><<<(unsigned)nblocks, kThreads, smem, st>>>(*ba);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_part(int r, const FrontArgs* fa, const BackArgs* ba, size_t smem, int64_t nblocks, cudaStream_t st)
+{
+    if (nblocks < 1) return cudaSuccess;
+    switch (r) {
+    case 6: return launch_part_r<6>(fa, ba, smem, nblocks, st);
+    case 8: return launch_part_r<8>(fa, ba, smem, nblocks, st);
+    case 10: return launch_part_r<10>(fa, ba, smem, nblocks, st);
+    case 12: return launch_part_r<12>(fa, ba, smem, nblocks, st);
+    case 14: return launch_part_r<14>(fa, ba, smem, nblocks, st);
+    case 16: return launch_part_r<16>(fa, ba, smem, nblocks, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t launch_f32_front(int r, const FrontArgs& fa, size_t smem, int64_t nblocks, cudaStream_t st)
+{
+    return launch_part(r, &fa, nullptr, smem, nblocks, st);
+}
+cudaError_t launch_f32_back(int r, const BackArgs& ba, size_t smem, int64_t nblocks, cudaStream_t st)
+{
+    return launch_part(r, nullptr, &ba, smem, nblocks, st);
 }
 
 cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws,
