@@ -542,6 +542,13 @@ def main():
     t0 = time.perf_counter()
     plan = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local)
     t_factor = time.perf_counter() - t0
+    # the same operator with its phase tables built on the GPU (bf_factor_device), for the record
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
+             factor_on_device=True).close()
+    torch.cuda.synchronize()
+    t_factor_dev = time.perf_counter() - t0
     info = plan.info()
     plan.reserve(prec, m)
     Fh = inputs.complex_gaussian(N, m, seed=rank)
@@ -640,7 +647,8 @@ def main():
     if rank == 0:
         cfg = {"workload": w["desc"], "N": N, "m": m, "r": info["r"], "r_alpha": info["r_alpha"],
                "eps": w["eps"], "L": info["L"], "split": w["split"], "l2": "flushed (512 MB write) between timed steps",
-               "t_factor_s": round(t_factor, 3), "parallelism": "replicas" if world > 1 else "single GPU",
+               "t_factor_s": round(t_factor, 3), "t_factor_device_s": round(t_factor_dev, 3),
+               "parallelism": "replicas" if world > 1 else "single GPU",
                "hbm_frac_of_measured": hbm_frac, "algorithmic_bytes_per_step": bytes_apply,
                "algorithmic_flops_per_step": (front + back) * w["split"] ** 2}
         if cpu is not None and "rel_err_gpu" in cpu:

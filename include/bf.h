@@ -141,6 +141,17 @@ bf_status bf_factor(bf_plan* plan);
  * Errors: BF_ERR_STATE (not factored), BF_ERR_NOMEM, BF_ERR_CUDA. */
 bf_status bf_upload(bf_plan* plan);
 
+/* Factor and upload in one step, with the O(r N log N) phase tables (Eqs. 1,
+ * 2, 3, bf3 and the switch step of Algorithm 4.1) computed on the device in
+ * FP64 (and their FP32 copies) instead of on the host; the amplitude split
+ * (Algorithm 1) and the real Lagrange matrices are still built on the host.
+ * Only the built-in phase kinds (not BF_PHASE_USER) have a device form.  The
+ * host keeps no phase tables, so bf_plan_save and bf_plan_view of tables
+ * return BF_ERR_STATE.  On an already factored plan this is bf_upload.
+ * Errors: BF_ERR_ARG, BF_ERR_STATE, BF_ERR_UNSUPPORTED (user phase),
+ * BF_ERR_NOMEM, BF_ERR_CUDA. */
+bf_status bf_factor_device(bf_plan* plan);
+
 /* Pre-allocate device workspace for applies of up to m_max right-hand sides at
  * precision prec (so that later bf_apply calls allocate nothing and can be
  * captured in a CUDA graph).  Errors: BF_ERR_NOMEM, BF_ERR_CUDA. */

@@ -154,6 +154,134 @@ bf_status ensure(void** p, size_t* have, size_t need)
 
 }  // namespace
 
+namespace {
+
+// Arena layout without a host image of the phase tables: small parts are kept
+// for copying, tables only get their (aligned) place.
+struct Layout {
+    size_t size = 0;
+    std::vector<std::pair<size_t, std::vector<unsigned char>>> parts;
+    size_t add(const void* src, size_t n)
+    {
+        const size_t off = (size + 255) & ~(size_t)255;
+        size = off + n;
+        if (src && n)
+            parts.emplace_back(off, std::vector<unsigned char>((const unsigned char*)src, (const unsigned char*)src + n));
+        return off;
+    }
+    template <typename V>
+    size_t addv(const V& v)
+    {
+        return add(v.data(), v.size() * sizeof(typename V::value_type));
+    }
+};
+
+template <typename T, typename C>
+Offs layout_block(Layout& lo, const BlockFactors& B, bool transposed)
+{
+    Offs o;
+    const int r = B.r;
+    const int64_t N = B.N, P = B.P(), ntab = (int64_t)1 << B.l1;
+    o.a = lo.addv(cplx_as<C>(B.a));
+    o.b = lo.addv(cplx_as<C>(B.b));
+    o.Mv = lo.addv(real_as<T>(transposed ? transpose(B.Mv, r, B.nv) : B.Mv));
+    o.EV = lo.add(nullptr, (size_t)(ntab * N) * sizeof(C));
+    std::vector<double> mh;
+    for (auto& M : B.MH) {
+        auto t = transposed ? transpose(M, r, 2 * r) : M;
+        mh.insert(mh.end(), t.begin(), t.end());
+    }
+    o.MH = lo.addv(real_as<T>(mh));
+    o.EH = lo.add(nullptr, (size_t)(B.nH() * P * 2 * r) * sizeof(C));
+    o.S = lo.add(nullptr, (size_t)(P * r * r) * sizeof(C));
+    std::vector<double> mg;
+    for (auto& M : B.MG)
+        for (int pos = 0; pos < 2; ++pos) {
+            std::vector<double> blk(M.begin() + (size_t)pos * r * r, M.begin() + (size_t)(pos + 1) * r * r);
+            auto t = transposed ? transpose(blk, r, r) : blk;
+            mg.insert(mg.end(), t.begin(), t.end());
+        }
+    o.MG = lo.addv(real_as<T>(mg));
+    o.FG = lo.add(nullptr, (size_t)(B.nG() * P * 2 * r) * sizeof(C));
+    o.MU = lo.addv(real_as<T>(B.MU));
+    o.EU = lo.add(nullptr, (size_t)(ntab * N) * sizeof(C));
+    return o;
+}
+
+}  // namespace
+
+bf_status device_construct(bf_plan* p)
+{
+    if (p->dev) return BF_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        set_error("bf_factor_device: no CUDA device available");
+        return BF_ERR_CUDA;
+    }
+    if (p->opt.device < 0 || p->opt.device >= ndev) {
+        set_error("bf_factor_device: device %d not present (%d devices)", p->opt.device, ndev);
+        return BF_ERR_ARG;
+    }
+    BF_CUDA(cudaSetDevice(p->opt.device));
+    DeviceState* ds = new (std::nothrow) DeviceState();
+    if (!ds) {
+        set_error("bf_factor_device: out of host memory");
+        return BF_ERR_NOMEM;
+    }
+    ds->device = p->opt.device;
+    Layout l64, l32;
+    std::vector<Offs> o64, o32;
+    for (auto& B : p->blocks) {
+        o64.push_back(layout_block<double, double2>(l64, B, false));
+        o32.push_back(layout_block<float, float2>(l32, B, true));
+    }
+    auto fail = [&](bf_status st) {
+        if (ds->arena64) cudaFree(ds->arena64);
+        if (ds->arena32) cudaFree(ds->arena32);
+        if (ds->err) cudaFree(ds->err);
+        delete ds;
+        return st;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&ds->arena64, l64.size)) != cudaSuccess || (e = cudaMalloc(&ds->arena32, l32.size)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ds->err, sizeof(int))) != cudaSuccess || (e = cudaMemset(ds->err, 0, sizeof(int))) != cudaSuccess) {
+        set_error("bf_factor_device: cudaMalloc: %s", cudaGetErrorString(e));
+        return fail(e == cudaErrorMemoryAllocation ? BF_ERR_NOMEM : BF_ERR_CUDA);
+    }
+    for (auto* lo : {&l64, &l32}) {
+        unsigned char* base = (unsigned char*)(lo == &l64 ? ds->arena64 : ds->arena32);
+        for (auto& pt : lo->parts)
+            if ((e = cudaMemcpy(base + pt.first, pt.second.data(), pt.second.size(), cudaMemcpyHostToDevice)) !=
+                cudaSuccess) {
+                set_error("bf_factor_device: copy: %s", cudaGetErrorString(e));
+                return fail(BF_ERR_CUDA);
+            }
+    }
+    ds->bytes64 = l64.size;
+    ds->bytes32 = l32.size;
+    for (size_t i = 0; i < p->blocks.size(); ++i) {
+        DevBlock db;
+        db.g = geo_of(p->blocks[i]);
+        db.row0 = p->blocks[i].row0;
+        db.col0 = p->blocks[i].col0;
+        bind(db.f64, (unsigned char*)ds->arena64, o64[i]);
+        bind(db.f32, (unsigned char*)ds->arena32, o32[i]);
+        e = construct_tables(p->blocks[i], p->kern.d.phase_kind, p->kern.d.phase_param, p->kern.n_global, db.f64,
+                             db.f32, 0);
+        if (e != cudaSuccess) {
+            set_error("bf_factor_device: table kernels: %s", cudaGetErrorString(e));
+            return fail(BF_ERR_CUDA);
+        }
+        ds->blocks.push_back(db);
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+        set_error("bf_factor_device: %s", cudaGetErrorString(e));
+        return fail(BF_ERR_CUDA);
+    }
+    p->dev = ds;
+    return BF_OK;
+}
+
 bf_status device_upload(bf_plan* p)
 {
     if (p->dev) return BF_OK;

@@ -63,6 +63,11 @@ struct DeviceState {
     int* err = nullptr;     // device error word (0 = ok)
 };
 
+// ---- construction of the phase tables on the device (bf_construct.cu) ----
+cudaError_t construct_tables(const BlockFactors& B, int phase_kind, double phase_param, int64_t n_global,
+                             const DevFactors<double, double2>& f64, const DevFactors<float, float2>& f32,
+                             cudaStream_t st);
+
 // ---- launchers (return cudaGetLastError() of the last launch) ----
 // Plain FP64 form: one kernel per butterfly stage, state through global memory.
 cudaError_t launch_plain_f64(const DevBlock& B, const double2* F, int64_t m, double2* G, int beta,

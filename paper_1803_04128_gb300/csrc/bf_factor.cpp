@@ -249,7 +249,7 @@ bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0
 }
 
 // ---------------------------------------------------------------------------
-bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B)
+bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B, bool tables)
 {
     const int64_t N = B.N;
     const int r = B.r, n0 = B.n0;
@@ -276,9 +276,9 @@ bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B
         std::vector<double> pts((size_t)nv);
         for (int64_t x = 0; x < nv; ++x) pts[(size_t)x] = (double)x;
         B.Mv = lagrange(gB, pts);
-        B.EV.assign((size_t)(nA * N), cd(0));
-#pragma omp parallel for schedule(static)
-        for (int64_t a = 0; a < nA; ++a) {
+        if (tables) B.EV.assign((size_t)(nA * N), cd(0));
+#pragma omp parallel for schedule(static) if (tables)
+        for (int64_t a = 0; a < (tables ? nA : 0); ++a) {
             const int64_t cA = centre(a * na, na);
             for (int64_t j = 0; j < N; ++j) B.EV[(size_t)(a * N + j)] = expi(F(cA, j));
         }
@@ -294,9 +294,9 @@ bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B
         for (int c = 0; c < 2; ++c)
             for (int s = 0; s < r; ++s) pts.push_back((double)(gC[(size_t)s] + c * (nb / 2)));
         B.MH.push_back(lagrange(gB, pts));
-        std::vector<cd> E((size_t)(P * 2 * r));
-#pragma omp parallel for schedule(static)
-        for (int64_t a = 0; a < nA; ++a) {
+        std::vector<cd> E(tables ? (size_t)(P * 2 * r) : 0);
+#pragma omp parallel for schedule(static) if (tables)
+        for (int64_t a = 0; a < (tables ? nA : 0); ++a) {
             const int64_t cA = centre(a * na, na), cP = centre((a >> 1) * 2 * na, 2 * na);
             for (int64_t bb = 0; bb < nBl; ++bb)
                 for (int c = 0; c < 2; ++c)
@@ -312,9 +312,9 @@ bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B
         const int64_t nA = (int64_t)1 << h, na = N >> h;
         const int64_t nBl = (int64_t)1 << (L - h), nb = N >> (L - h);
         auto gA = grid_rel(na, r), gB = grid_rel(nb, r);
-        B.S.assign((size_t)(P * r * r), cd(0));
-#pragma omp parallel for schedule(static)
-        for (int64_t a = 0; a < nA; ++a) {
+        if (tables) B.S.assign((size_t)(P * r * r), cd(0));
+#pragma omp parallel for schedule(static) if (tables)
+        for (int64_t a = 0; a < (tables ? nA : 0); ++a) {
             const int64_t cA = centre(a * na, na);
             for (int64_t bb = 0; bb < nBl; ++bb) {
                 const int64_t cB = centre(bb * nb, nb);
@@ -345,9 +345,9 @@ bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B
                 for (int s = 0; s < r; ++s) MG[(size_t)((pos * r + t) * r + s)] = Lg[(size_t)(s * r + t)];
         }
         B.MG.push_back(std::move(MG));
-        std::vector<cd> E((size_t)(P * 2 * r));
-#pragma omp parallel for schedule(static)
-        for (int64_t a = 0; a < nA; ++a)
+        std::vector<cd> E(tables ? (size_t)(P * 2 * r) : 0);
+#pragma omp parallel for schedule(static) if (tables)
+        for (int64_t a = 0; a < (tables ? nA : 0); ++a)
             for (int64_t bb = 0; bb < nBl; ++bb) {
                 const int64_t cB = centre(bb * nb, nb);
                 for (int c = 0; c < 2; ++c) {
@@ -370,9 +370,9 @@ bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B
         B.MU.assign((size_t)(nu * r), 0.0);
         for (int64_t x = 0; x < nu; ++x)
             for (int s = 0; s < r; ++s) B.MU[(size_t)(x * r + s)] = Lg[(size_t)(s * nu + x)];
-        B.EU.assign((size_t)(nC * N), cd(0));
-#pragma omp parallel for schedule(static)
-        for (int64_t c = 0; c < nC; ++c) {
+        if (tables) B.EU.assign((size_t)(nC * N), cd(0));
+#pragma omp parallel for schedule(static) if (tables)
+        for (int64_t c = 0; c < (tables ? nC : 0); ++c) {
             const int64_t cC = centre(c * nc, nc);
             for (int64_t x = 0; x < N; ++x) B.EU[(size_t)(c * N + x)] = expi(F(x, cC));
         }

@@ -82,7 +82,9 @@ inline int64_t centre(int64_t start, int64_t n) { return start + (n - 1) / 2; }
 int choose_l1(int r, int n0);
 
 // construction
-bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B);
+// tables = false: geometry, amplitude split and the real matrices only (the
+// phase tables are then built on the device, bf_factor_device)
+bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B, bool tables = true);
 bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0, int64_t col0,
                           int64_t N, std::vector<cd>& a, std::vector<cd>& b, int& ra,
                           double& sigma_ratio);
@@ -108,6 +110,9 @@ CMat adjoint(const CMat& A);
 
 // device side (bf_device.cu)
 bf_status device_upload(bf_plan* p);
+// device construction of the phase tables (bf_construct.cu, bf_device.cu)
+bool construct_supported(int phase_kind);
+bf_status device_construct(bf_plan* p);
 bf_status device_reserve(bf_plan* p, bf_precision prec, int64_t m, void* stream);
 bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G,
                        void* stream);

@@ -173,6 +173,53 @@ bf_status bf_factor(bf_plan* p)
     return BF_OK;
 }
 
+bf_status bf_factor_device(bf_plan* p)
+{
+    if (!p) {
+        set_error("bf_factor_device: NULL plan");
+        return BF_ERR_ARG;
+    }
+    if (p->factored) return bf_upload(p);
+    if (p->user_kinds_lost) {
+        set_error("bf_factor_device: plan was loaded without its callbacks");
+        return BF_ERR_STATE;
+    }
+    if (!bfi::construct_supported(p->kern.d.phase_kind)) {
+        set_error("bf_factor_device: phase kind %d has no device form (use bf_factor)", p->kern.d.phase_kind);
+        return BF_ERR_UNSUPPORTED;
+    }
+    const int sp = p->opt.split;
+    const int64_t Nb = p->N / sp;
+    try {
+        p->blocks.assign((size_t)(sp * sp), BlockFactors());
+        for (int rh = 0; rh < sp; ++rh)
+            for (int ch = 0; ch < sp; ++ch) {
+                BlockFactors& B = p->blocks[(size_t)(rh * sp + ch)];
+                B.N = Nb;
+                B.row0 = rh * Nb;
+                B.col0 = ch * Nb;
+                B.r = p->r;
+                B.n0 = p->n0;
+                bf_status st = factor_block(p->kern, p->opt, B, false);
+                if (st != BF_OK) {
+                    p->blocks.clear();
+                    return st;
+                }
+            }
+    } catch (const std::bad_alloc&) {
+        p->blocks.clear();
+        set_error("bf_factor_device: out of host memory");
+        return BF_ERR_NOMEM;
+    }
+    bf_status st = bfi::device_construct(p);
+    if (st != BF_OK) {
+        p->blocks.clear();
+        return st;
+    }
+    p->factored = true;
+    return BF_OK;
+}
+
 bf_status bf_upload(bf_plan* p)
 {
     if (!p) {

@@ -212,3 +212,14 @@ def test_bf16x3_refuses_tiles_that_do_not_fit():
     with pytest.raises(L.BFError) as e:
         plan.apply(F, prec=api.BF16X3)
     assert e.value.status == L.BF_ERR_UNSUPPORTED
+
+
+def test_largest_serving_operator_n_2_20_sampled():
+    # the largest operator of the serving workload (N = 2^20): FP32 and FP64 on 48 sampled rows
+    N, m = 1 << 20, 3
+    plan = api.Plan(N, eps=1e-6, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(N, m, seed=21)
+    rows = inputs.sample_rows(N, 48, seed=22)
+    gd = od.direct(od.FIO, N, F, rows, amp=1)
+    assert relerr(run(plan, F, api.F32)[rows], gd) < 1e-5
+    assert relerr(run(plan, F, api.F64)[rows], gd) < 1e-6
