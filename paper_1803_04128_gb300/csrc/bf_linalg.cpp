@@ -28,12 +28,46 @@ CMat adjoint(const CMat& A)
     return T;
 }
 
+// sum over i in [i0, m) of conj(v[i - i0]) * X(i, j): in fixed chunks of rows whose
+// partial sums are added in chunk order, so the result does not depend on the
+// number of threads; long columns are split over threads
+static cd col_dot(const std::vector<cd>& v, const CMat& X, int64_t j, int64_t i0, int64_t m)
+{
+    constexpr int64_t kChunk = 1 << 15;
+    const int64_t len = m - i0, nch = (len + kChunk - 1) / kChunk;
+    if (nch <= 1) {
+        cd d = 0;
+        for (int64_t i = i0; i < m; ++i) d += std::conj(v[(size_t)(i - i0)]) * X(i, j);
+        return d;
+    }
+    std::vector<cd> part((size_t)nch);
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < nch; ++c) {
+        cd d = 0;
+        const int64_t e = std::min(m, i0 + (c + 1) * kChunk);
+        for (int64_t i = i0 + c * kChunk; i < e; ++i) d += std::conj(v[(size_t)(i - i0)]) * X(i, j);
+        part[(size_t)c] = d;
+    }
+    cd d = 0;
+    for (auto& x : part) d += x;
+    return d;
+}
+
+// X(i, j) -= v[i - i0] * s for i in [i0, m), rows split over threads when long
+static void col_axpy(const std::vector<cd>& v, CMat& X, int64_t j, int64_t i0, int64_t m, cd s)
+{
+#pragma omp parallel for schedule(static) if (m - i0 > (1 << 15))
+    for (int64_t i = i0; i < m; ++i) X(i, j) -= v[(size_t)(i - i0)] * s;
+}
+
 int pivoted_qr(const CMat& A, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv)
 {
     const int64_t m = A.m, n = A.n;
     CMat R = A;
     piv.resize((size_t)n);
     std::vector<double> nrm((size_t)n);
+    const bool wide = n > 4096;  // many columns: split the column loops over threads
+#pragma omp parallel for schedule(static) if (wide)
     for (int64_t j = 0; j < n; ++j) {
         piv[(size_t)j] = j;
         double s = 0;
@@ -73,12 +107,18 @@ int pivoted_qr(const CMat& A, int kmax, double tol, CMat& Q, std::vector<int64_t
         if (vn > 0)
             for (auto& e : v) e /= vn;
         // apply H = I - 2 v v^* to R[k:, k:]
-        for (int64_t j = k; j < n; ++j) {
-            cd dot = 0;
-            for (int64_t i = k; i < m; ++i) dot += std::conj(v[(size_t)(i - k)]) * R(i, j);
-            dot *= 2.0;
-            for (int64_t i = k; i < m; ++i) R(i, j) -= v[(size_t)(i - k)] * dot;
+        if (wide) {
+#pragma omp parallel for schedule(static)
+            for (int64_t j = k; j < n; ++j) {
+                cd dot = 0;
+                for (int64_t i = k; i < m; ++i) dot += std::conj(v[(size_t)(i - k)]) * R(i, j);
+                dot *= 2.0;
+                for (int64_t i = k; i < m; ++i) R(i, j) -= v[(size_t)(i - k)] * dot;
+            }
+        } else {
+            for (int64_t j = k; j < n; ++j) col_axpy(v, R, j, k, m, 2.0 * col_dot(v, R, j, k, m));
         }
+#pragma omp parallel for schedule(static) if (wide)
         for (int64_t j = k + 1; j < n; ++j) {
             nrm[(size_t)j] -= std::norm(R(k, j));
             if (nrm[(size_t)j] < 0) nrm[(size_t)j] = 0;
@@ -90,12 +130,7 @@ int pivoted_qr(const CMat& A, int kmax, double tol, CMat& Q, std::vector<int64_t
     for (int64_t j = 0; j < k; ++j) Q(j, j) = 1;
     for (int64_t s2 = k - 1; s2 >= 0; --s2) {
         const auto& v = vs[(size_t)s2];
-        for (int64_t j = 0; j < k; ++j) {
-            cd dot = 0;
-            for (int64_t i = s2; i < m; ++i) dot += std::conj(v[(size_t)(i - s2)]) * Q(i, j);
-            dot *= 2.0;
-            for (int64_t i = s2; i < m; ++i) Q(i, j) -= v[(size_t)(i - s2)] * dot;
-        }
+        for (int64_t j = 0; j < k; ++j) col_axpy(v, Q, j, s2, m, 2.0 * col_dot(v, Q, j, s2, m));
     }
     return (int)k;
 }
