@@ -279,7 +279,10 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
     __syncthreads();
 
     // ---- V (Eq. 1): item (u, j, c) computes mu[j][.][k*mr + c] of tile u for every k
-    for (int it = tid; it < tpc * T * mr; it += kThreads) {
+    // (with few items, one item per amplitude term k instead)
+    const int nk = (ra > 1 && tpc * T * mr * 2 <= kThreads) ? ra : 1;
+    for (int itk = tid; itk < tpc * T * mr * nk; itk += kThreads) {
+        const int it = itk / nk, kk = itk - it * nk;
         const int c = it & (mr - 1), j = (it >> lmr) & (T - 1), u = it >> (lmr + K);
         const int64_t xi_base = c0_of(u) * T * NV;
         const float2* fs = Fof(u) + (size_t)j * NV * mr + c;
@@ -287,7 +290,7 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
         float2 f[NV];
 #pragma unroll
         for (int x = 0; x < NV; ++x) f[x] = fs[x * mr];
-        for (int k = 0; k < ra; ++k) {
+        for (int k = nk > 1 ? kk : 0; k < (nk > 1 ? kk + 1 : ra); ++k) {
             float2 acc[R];
 #pragma unroll
             for (int t = 0; t < R; ++t) acc[t] = make_float2(0.f, 0.f);
@@ -461,10 +464,14 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
         }
 
         // ---- U (Eq. bf3) contributions of T_Omega nodes c0b .. c0b + tpc - 1, in that order;
-        // each accumulator entry (lp, i, c) belongs to one thread
+        // each accumulator entry (lp, i, c) belongs to one thread.  Item (lp, c, part): part
+        // of nis equal ranges of the NU points i (nis > 1 only when T * mr < kThreads)
         {
-            const int c = tid & (mr - 1);
-            for (int lp = tid >> lmr; lp < T; lp += kThreads >> lmr) {
+            int lnis = 0;
+            while ((1 << lnis) < NU && ((T * mr) << (lnis + 1)) <= kThreads) ++lnis;
+            const int nis = 1 << lnis, ni = NU >> lnis;
+            const int c = tid & (mr - 1), part = (tid >> lmr) & (nis - 1);
+            for (int lp = tid >> (lmr + lnis); lp < T; lp += kThreads >> (lmr + lnis)) {
                 const int slot = (int)brev((unsigned)lp, K);
                 float2* ap = acc + (size_t)lp * NU * mr + c;
                 for (int u = 0; u < tpc; ++u) {
@@ -476,7 +483,7 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
                         for (int s = 0; s < R; ++s) v[s] = xs[s * CTp + k * mr];
                         const float2* ak = A.ak + (size_t)k * N + x0g + lp * NU;
 #pragma unroll 4
-                        for (int i = 0; i < NU; ++i) {
+                        for (int i = part * ni; i < (part + 1) * ni; ++i) {
                             float2 w = make_float2(0.f, 0.f);
                             const float4* mu = reinterpret_cast<const float4*>(MUs + i * R4);
 #pragma unroll
