@@ -331,6 +331,12 @@ def run_serving(args, w, rank, world, local):
     b = results["batched_f32"]
     bl = results["batched_f32_light"]
     p = results["plain_f64_per_request"]
+    units_all = b["units_per_s"]
+    if world > 1:  # each rank serves its own trace on its own GPU: the job's rate is the sum
+        import torch.distributed as dist
+        t = torch.tensor([b["units_per_s"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        units_all = float(t.item())
     if rank == 0:
         cfg = {"workload": w["desc"], "operators_N": Ns, "m_choices": list(mset), "r": plans[0].info()["r"],
                "eps": w["eps"], "t_factor_s": round(t_factor, 2), "warmup_s": warm,
@@ -342,13 +348,13 @@ def run_serving(args, w, rank, world, local):
                        "counted in 'pending' and not in the latency percentiles.  At the offered 2000 req/s the "
                        "work arriving exceeds the GPU's capacity, so its p50/p99 measure queue growth over the "
                        "window; p50_ms/p99_ms of this line are those of the light rate, which the server sustains"}
-        line = {"metric": METRIC, "value": b["units_per_s"] / 1e9, "unit": UNIT, "n_gpus": world,
+        line = {"metric": METRIC, "value": units_all / 1e9, "unit": UNIT, "n_gpus": world,
                 "steps": int(b["completed"]), "warmup": warm, "ms_per_step": b["mean_ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded complex Gaussian F; analytic kernel; Poisson arrivals)", "config": cfg,
                 "p50_ms": bl["p50_ms"], "p99_ms": bl["p99_ms"], "p99_ms_at_offered_rate": b["p99_ms"],
                 "roofline": None, "cpu_baseline": None,
-                "e2e": {"value": b["units_per_s"] / 1e9, "unit": UNIT, "h2d_bytes_per_step": None,
+                "e2e": {"value": units_all / 1e9, "unit": UNIT, "h2d_bytes_per_step": None,
                         "d2h_bytes_per_step": None, "note": "requests are served from host buffers"},
                 "gpu_launches": None, "clocks": b["clocks"]}
         print(json.dumps(line))
@@ -550,6 +556,11 @@ def main():
     torch.cuda.synchronize()
     t_factor_dev = time.perf_counter() - t0
     info = plan.info()
+    mr_tuned = None
+    if prec == api.F32:
+        # column-slice width of the fused FP32 apply chosen by timing (off the timed region)
+        tune_path = os.path.join(tempfile.gettempdir(), "bf_autotune_bench_%d.txt" % os.getpid())
+        mr_tuned = api.autotune(plan, m, tune_path)
     plan.reserve(prec, m)
     Fh = inputs.complex_gaussian(N, m, seed=rank)
     F = torch.from_numpy(Fh).to(cdt).cuda()
@@ -648,6 +659,7 @@ def main():
         cfg = {"workload": w["desc"], "N": N, "m": m, "r": info["r"], "r_alpha": info["r_alpha"],
                "eps": w["eps"], "L": info["L"], "split": w["split"], "l2": "flushed (512 MB write) between timed steps",
                "t_factor_s": round(t_factor, 3), "t_factor_device_s": round(t_factor_dev, 3),
+               "mr_autotuned": mr_tuned,
                "parallelism": "replicas" if world > 1 else "single GPU",
                "hbm_frac_of_measured": hbm_frac, "algorithmic_bytes_per_step": bytes_apply,
                "algorithmic_flops_per_step": (front + back) * w["split"] ** 2}
