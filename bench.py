@@ -103,8 +103,12 @@ def tensor_flops(info, m, N, split):
 
 def algorithmic(info, m, N, split):
     """Algorithmic flops per launch of the front and back kernels and the
-    algorithmic bytes of one apply (c64), from the factored form's stage
-    formulas (stated in DESIGN.md)."""
+    algorithmic bytes of one apply (c64), from the factored form's stages.
+    Per column (1 complex mul = 6 flops, real x complex MAC = 4, complex
+    MAC = 8): front = 6N + 2^l1 N (6 + 4r) + kH P (12r + 8r^2) + 8 P r^2;
+    back = kG P (8r^2 + 16r) + 2^l1 N (4r + 8) + 8N.  Bytes: the phase
+    tables EV, EU (2^l1 N each), EH/FG (2r P per level), S (r^2 P), a and b
+    (r_alpha N each), all c64, plus F and G (N m each)."""
     r, l1, ra = info["r"], info["l1"], info["r_alpha"]
     L, h = info["L"], info["h"]
     Nb = N // split

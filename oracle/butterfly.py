@@ -14,7 +14,7 @@ level L-l of T_Omega; lambda^{AB}_t are the expansion coefficients; xi^B_t and
 x^A_t are the mock-Chebyshev index grids of Eq. (gdB)/(gdA); M^B_t, M^A_t are
 their Lagrange polynomials; c_A, c_B are centre indices (Eq. RAB).
 
-Readings of the paper taken here (each one is listed in the design doc):
+Readings of the paper taken here, where it is silent, garbled or ambiguous:
   * 0-based indices: x_i = i/N, xi_j = j - N/2 (Eq. 1D-xandxi, shifted).
   * Leaves of both trees hold n0 indices (the paper's Fig. "submatrices" uses
     n0 = 1, the default); L = log2(N/n0), h = floor(L/2) when L is odd.
