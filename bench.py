@@ -53,8 +53,8 @@ NUM_SMS = 152
 
 
 def max_over_ranks(x, world, device):
-    """The timing rule across ranks: each rank's value reduced with MAX (NCCL on the
-    GPU machine; gloo on CPU in the tests)."""
+    """The timing rule across ranks: each rank's value reduced with MAX (over the
+    process group of the run: NCCL with GPUs, gloo for CPU ranks)."""
     if world <= 1:
         return float(x)
     import torch
