@@ -21,9 +21,11 @@
  *    2 x double.  Right-hand-side blocks are row-major [N][m] with the m
  *    right-hand sides innermost (PyTorch's layout for a contiguous (N, m)).
  *  - The caller owns F and G; the plan owns its factors and workspace.
- *  - Calls on one plan are not thread-safe, except that bf_apply calls on
- *    distinct streams may overlap once the plan is uploaded and its
- *    workspace is reserved for each stream (bf_reserve).
+ *  - Calls on one plan are not thread-safe.  Applies of one plan share its
+ *    workspace (and its cached FP64 graph), so the caller keeps them from
+ *    overlapping on the GPU (one stream, or ordered streams); concurrent
+ *    applies of one operator go through a bf_server, whose slots each have
+ *    their own workspace.
  *  - No entry point calls exit(), abort() or traps on the device; GPU-side
  *    failures (a bounded wait that ran out) are reported as BF_ERR_TIMEOUT
  *    by bf_sync_status().

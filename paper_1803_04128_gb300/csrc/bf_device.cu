@@ -372,6 +372,80 @@ bf_status device_reserve(bf_plan* p, bf_precision prec, int64_t m, void*)
     return ensure(&ds->ws32, &ds->ws32_bytes, need);
 }
 
+namespace {
+
+// The plain FP64 form launches one kernel per stage; at small N the launches
+// dominate, so the sequence is captured once per (F, G, m, workspace) into a
+// CUDA graph and replayed.  Skipped (direct launches) while the caller's
+// stream is itself being captured.
+bf_status apply_f64(bf_plan* p, const void* F, int64_t m, void* G, cudaStream_t st)
+{
+    DeviceState* ds = p->dev;
+    const int sp = p->opt.split;
+    auto launch_all = [&](cudaStream_t s) {
+        for (size_t i = 0; i < ds->blocks.size(); ++i) {
+            const DevBlock& B = ds->blocks[i];
+            const int beta = (sp == 2 && (i % 2) == 1) ? 1 : 0;  // second column half accumulates
+            const size_t half = ds->ws64_bytes / 2 / sizeof(double2);
+            cudaError_t e = launch_plain_f64(B, (const double2*)F + B.col0 * m, m, (double2*)G + B.row0 * m, beta,
+                                             (double2*)ds->ws64, (double2*)ds->ws64 + half, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        const cudaError_t e = launch_all(st);
+        if (e != cudaSuccess) {
+            set_error("bf_apply: kernel launch failed: %s", cudaGetErrorString(e));
+            return BF_ERR_CUDA;
+        }
+        return BF_OK;
+    }
+    const bool hit = ds->g64 && ds->g64_F == F && ds->g64_G == G && ds->g64_m == m && ds->g64_ws == ds->ws64;
+    if (!hit) {
+        if (ds->g64) {
+            cudaGraphExecDestroy(ds->g64);
+            ds->g64 = nullptr;
+        }
+        if (!ds->cap) BF_CUDA(cudaStreamCreateWithFlags(&ds->cap, cudaStreamNonBlocking));
+        prof_suppress(true);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(ds->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t el = launch_all(ds->cap);
+            e = cudaStreamEndCapture(ds->cap, &g);
+            if (e == cudaSuccess) e = el;
+        }
+        prof_suppress(false);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ds->g64, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ds->g64 = nullptr;
+            cudaGetLastError();
+            const cudaError_t e2 = launch_all(st);  // fall back to direct launches
+            if (e2 != cudaSuccess) {
+                set_error("bf_apply: kernel launch failed: %s", cudaGetErrorString(e2));
+                return BF_ERR_CUDA;
+            }
+            return BF_OK;
+        }
+        ds->g64_F = F;
+        ds->g64_G = G;
+        ds->g64_m = m;
+        ds->g64_ws = ds->ws64;
+    }
+    ProfScope ps("plain_f64_graph", st);
+    const cudaError_t e = cudaGraphLaunch(ds->g64, st);
+    if (e != cudaSuccess) {
+        set_error("bf_apply: graph launch failed: %s", cudaGetErrorString(e));
+        return BF_ERR_CUDA;
+    }
+    return BF_OK;
+}
+
+}  // namespace
+
 bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G, void* stream)
 {
     DeviceState* ds = p->dev;
@@ -394,6 +468,7 @@ bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, 
     }
     bf_status rs = device_reserve(p, prec, m, stream);
     if (rs != BF_OK) return rs;
+    if (prec == BF_PREC_F64) return apply_f64(p, F, m, G, st);
     const int sp = p->opt.split;
     for (size_t i = 0; i < ds->blocks.size(); ++i) {
         const DevBlock& B = ds->blocks[i];
@@ -513,6 +588,8 @@ void device_free(bf_plan* p)
     cudaSetDevice(ds->device);
     cudaFree(ds->arena64);
     cudaFree(ds->arena32);
+    if (ds->g64) cudaGraphExecDestroy(ds->g64);
+    if (ds->cap) cudaStreamDestroy(ds->cap);
     cudaFree(ds->ws64);
     cudaFree(ds->ws32);
     cudaFree(ds->stage);

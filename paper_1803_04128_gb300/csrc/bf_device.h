@@ -61,6 +61,14 @@ struct DeviceState {
     void* stage = nullptr;  // F/G staging for bf_apply_host
     size_t stage_bytes = 0;
     int* err = nullptr;     // device error word (0 = ok)
+    // the plain FP64 apply (one launch per stage) replayed from a CUDA graph
+    // captured for the last (F, G, m, workspace)
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t g64 = nullptr;
+    const void* g64_F = nullptr;
+    void* g64_G = nullptr;
+    int64_t g64_m = 0;
+    void* g64_ws = nullptr;
 };
 
 // ---- construction of the phase tables on the device (bf_construct.cu) ----
@@ -98,6 +106,8 @@ cudaError_t launch_tc(const DevBlock& B, const float2* F, int64_t m, float2* G, 
 void prof_start(const char* name, cudaStream_t st, void** tok);
 void prof_stop(void* tok, cudaStream_t st);
 bool prof_active();
+// no timing records from this thread while on (launches being captured into a graph)
+void prof_suppress(bool on);
 struct ProfScope {
     void* tok;
     cudaStream_t st;
