@@ -223,3 +223,41 @@ def test_largest_serving_operator_n_2_20_sampled():
     gd = od.direct(od.FIO, N, F, rows, amp=1)
     assert relerr(run(plan, F, api.F32)[rows], gd) < 1e-5
     assert relerr(run(plan, F, api.F64)[rows], gd) < 1e-6
+
+
+# ------------------------------------------------------- more edge cases ----
+@pytest.mark.parametrize("n0", [4, 8])
+def test_leaves_of_n0_indices_match_algorithm_4_1(n0):
+    # leaves of n0 > 1 indices (Sec. 4 uses n0 = 1; the levels of <= r indices fold into V and U)
+    N, r, m = 4096, 10, 3
+    plan = api.Plan(N, r=r, n0=n0, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(N, m, seed=n0)
+    ent = lambda I, J: od.amplitude(1, N, np.asarray(I)[:, None], np.asarray(J)[None, :])
+    a, b = olr.amplitude_split(ent, N, N)
+    ref = obf.ibf_apply(L.PHASE_FIO, N, F, r, a, b, n0=n0)
+    assert relerr(run(plan, F, api.F32), ref) < 2e-6
+    assert relerr(run(plan, F, api.F64), ref) < 1e-12
+
+
+def test_many_ragged_columns_sampled():
+    # m = 1000 (62 full slices of 16 and a ragged one of 8), sampled rows vs the direct oracle
+    N, m = 4096, 1000
+    plan = api.Plan(N, eps=1e-6, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(N, m, seed=31)
+    rows = inputs.sample_rows(N, 24, seed=32)
+    gd = od.direct(od.FIO, N, F, rows, amp=1)
+    g = run(plan, F, api.F32)
+    assert relerr(g[rows], gd) < 1e-5
+    # every column equals its own single-column apply (slices never mix columns)
+    for c in (0, 15, 16, 991, 999):
+        assert np.array_equal(run(plan, F[:, c:c + 1], api.F32)[:, 0], g[:, c])
+
+
+def test_zero_amplitude_gives_zero():
+    # alpha = 0 has numerical rank 0: the apply writes G = 0 in every precision
+    N, m = 1024, 4
+    plan = api.Plan(N, r=10, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_USER, alpha=lambda x, xi: 0.0)
+    assert plan.info()["r_alpha"] == 0
+    F = inputs.complex_gaussian(N, m, seed=33)
+    for prec in (api.F32, api.F64):
+        assert np.all(run(plan, F, prec) == 0)
