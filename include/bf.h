@@ -154,6 +154,22 @@ bf_status bf_upload(bf_plan* plan);
  * BF_ERR_NOMEM, BF_ERR_CUDA. */
 bf_status bf_factor_device(bf_plan* plan);
 
+/* Factor for the on-the-fly apply: no phase tables anywhere.  The host builds
+ * the amplitude split (Algorithm 1) and the real Lagrange matrices; the device
+ * keeps those, 16 bytes of phase coefficients per global grid row and the
+ * interpolation grids, i.e. O(r_alpha N) memory instead of the O(r N log N)
+ * tables.  The FP32 apply kernels then evaluate every phase factor they use
+ * (Eqs. 1, 2, 3, bf3 and the switch step of Algorithm 4.1: e^{2 pi i Phi} at
+ * grid points of the two trees) from Phi's closed form, with Phi mod 1 held
+ * as an exact 32-bit fixed-point number of turns.  Only the built-in phase
+ * kinds, N <= 2^30 and BF_PREC_F32 applies (bf_apply, bf_apply_host,
+ * bf_apply_f32_noalloc, the sharded apply); F64 and BF16X3 applies, batches
+ * and servers return BF_ERR_UNSUPPORTED, bf_plan_save and table views
+ * BF_ERR_STATE.  On an already factored plan: BF_ERR_STATE.
+ * Errors: BF_ERR_ARG, BF_ERR_STATE, BF_ERR_UNSUPPORTED, BF_ERR_NOMEM,
+ * BF_ERR_CUDA. */
+bf_status bf_factor_otf(bf_plan* plan);
+
 /* Pre-allocate device workspace for applies of up to m_max right-hand sides at
  * precision prec (so that later bf_apply calls allocate nothing and can be
  * captured in a CUDA graph).  Errors: BF_ERR_NOMEM, BF_ERR_CUDA. */

@@ -73,6 +73,7 @@ _SIGS = {
     "bf_factor": (ctypes.c_int, [_P]),
     "bf_upload": (ctypes.c_int, [_P]),
     "bf_factor_device": (ctypes.c_int, [_P]),
+    "bf_factor_otf": (ctypes.c_int, [_P]),
     "bf_reserve": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     "bf_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, _P, _P]),
     "bf_apply_host": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, _P, _P]),

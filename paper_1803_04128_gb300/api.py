@@ -41,7 +41,7 @@ class Plan:
 
     def __init__(self, N, eps=1e-6, phase_kind=L.PHASE_FIO, phase_param=1.0, amp_kind=L.AMP_ONE,
                  r=0, n0=1, split=1, seed=0, keep_host=True, device=0, factor=True, phi=None, alpha=None,
-                 factor_on_device=False, _handle=None):
+                 factor_on_device=False, on_the_fly=False, _handle=None):
         self._lib = L.lib()
         self._h = ctypes.c_void_p()
         self._keep = []
@@ -68,7 +68,9 @@ class Plan:
             o.r, o.n0, o.split, o.seed, o.keep_host, o.device = r, n0, split, seed, int(keep_host), device
             L.check(self._lib.bf_plan_create(ctypes.byref(d), eps, ctypes.byref(o), ctypes.byref(self._h)),
                     "bf_plan_create")
-            if factor_on_device:
+            if on_the_fly:
+                self.factor_otf()
+            elif factor_on_device:
                 self.factor_device()
             elif factor:
                 self.factor()
@@ -81,6 +83,12 @@ class Plan:
     def factor_device(self):
         """Factor with the phase tables built on the GPU (bf_factor_device)."""
         L.check(self._lib.bf_factor_device(self._h), "bf_factor_device")
+        return self
+
+    def factor_otf(self):
+        """Factor for the on-the-fly FP32 apply (bf_factor_otf): no phase tables,
+        the apply kernels evaluate the phases; O(r_alpha N) device memory."""
+        L.check(self._lib.bf_factor_otf(self._h), "bf_factor_otf")
         return self
 
     def upload(self):

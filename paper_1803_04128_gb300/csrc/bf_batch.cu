@@ -89,6 +89,11 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
             free_batch(b);
             return st;
         }
+        if (it.plan->otf) {
+            free_batch(b);
+            set_error("bf_batch_create: item %d: plans factored by bf_factor_otf are not batched (use bf_apply)", i);
+            return BF_ERR_UNSUPPORTED;
+        }
         if (it.plan->blocks.size() != 1) {
             free_batch(b);
             set_error("bf_batch_create: item %d: split plans are not batched (apply them with bf_apply)", i);

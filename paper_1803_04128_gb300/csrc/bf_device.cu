@@ -1,5 +1,6 @@
 // Device residency of the factors, workspaces and apply dispatch.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -176,12 +177,13 @@ struct Layout {
     }
 };
 
+// tables = false: no place for the phase tables (their offsets are not used)
 template <typename T, typename C>
-Offs layout_block(Layout& lo, const BlockFactors& B, bool transposed)
+Offs layout_block(Layout& lo, const BlockFactors& B, bool transposed, bool tables = true)
 {
     Offs o;
     const int r = B.r;
-    const int64_t N = B.N, P = B.P(), ntab = (int64_t)1 << B.l1;
+    const int64_t N = B.N, P = tables ? B.P() : 0, ntab = tables ? (int64_t)1 << B.l1 : 0;
     o.a = lo.addv(cplx_as<C>(B.a));
     o.b = lo.addv(cplx_as<C>(B.b));
     o.Mv = lo.addv(real_as<T>(transposed ? transpose(B.Mv, r, B.nv) : B.Mv));
@@ -282,6 +284,129 @@ bf_status device_construct(bf_plan* p)
     return BF_OK;
 }
 
+namespace {
+
+// frac(v) 2^64 mod 2^64 (exact while the lowest set bit of v is at least 2^-64)
+uint64_t fixed64(double v)
+{
+    const double f = v - std::trunc(v);  // exact, |f| < 1
+    const uint64_t m = (uint64_t)std::ldexp(std::fabs(f), 64);
+    return f < 0 ? (uint64_t)0 - m : m;
+}
+
+}  // namespace
+
+bf_status device_otf(bf_plan* p)
+{
+    if (p->dev) return BF_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        set_error("bf_factor_otf: no CUDA device available");
+        return BF_ERR_CUDA;
+    }
+    if (p->opt.device < 0 || p->opt.device >= ndev) {
+        set_error("bf_factor_otf: device %d not present (%d devices)", p->opt.device, ndev);
+        return BF_ERR_ARG;
+    }
+    const int64_t Ng = p->kern.n_global;
+    int lNg = 0;
+    while (((int64_t)1 << lNg) < Ng) ++lNg;
+    double kappa, rho;
+    int xxi = 0, sq = 0;
+    if (!p->kern.row_terms(0, &kappa, &rho, &xxi, &sq) || lNg < 1 || lNg > 30) {
+        set_error("bf_factor_otf: phase kind %d / N=%lld has no on-the-fly form", p->kern.d.phase_kind,
+                  (long long)Ng);
+        return BF_ERR_UNSUPPORTED;
+    }
+    BF_CUDA(cudaSetDevice(p->opt.device));
+    // per-row phase coefficients and the interpolation grids of every node size
+    std::vector<uint4> rows;
+    std::vector<int> grids;
+    try {
+        rows.resize((size_t)Ng);
+        int lN = 0;  // log2 of the block size: node sizes 2^0 .. 2^lN
+        while (!p->blocks.empty() && ((int64_t)1 << lN) < p->blocks[0].N) ++lN;
+        grids.assign((size_t)(lN + 1) * 16, 0);
+        for (int e = 0; e <= lN; ++e) {
+            const std::vector<int64_t> gv = grid_rel((int64_t)1 << e, p->r);
+            for (size_t t = 0; t < gv.size() && t < 16; ++t) grids[(size_t)e * 16 + t] = (int)gv[t];
+        }
+    } catch (const std::bad_alloc&) {
+        set_error("bf_factor_otf: out of host memory");
+        return BF_ERR_NOMEM;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < Ng; ++i) {
+        double k, r;
+        int a, b;
+        p->kern.row_terms(i, &k, &r, &a, &b);
+        const uint64_t K = fixed64(k);
+        const uint32_t R = (uint32_t)((fixed64(r) + 0x80000000ull) >> 32);
+        rows[(size_t)i] = make_uint4((unsigned)(K & 0xffffffffu), (unsigned)(K >> 32), R, 0u);
+    }
+    DeviceState* ds = new (std::nothrow) DeviceState();
+    if (!ds) {
+        set_error("bf_factor_otf: out of host memory");
+        return BF_ERR_NOMEM;
+    }
+    ds->device = p->opt.device;
+    ds->otf = true;
+    Layout l32;
+    std::vector<Offs> o32;
+    for (auto& B : p->blocks) o32.push_back(layout_block<float, float2>(l32, B, true, false));
+    const size_t rows_bytes = rows.size() * sizeof(uint4), grid_off = (rows_bytes + 255) & ~(size_t)255;
+    auto fail = [&](bf_status st) {
+        if (ds->arena32) cudaFree(ds->arena32);
+        if (ds->otf_data) cudaFree(ds->otf_data);
+        if (ds->err) cudaFree(ds->err);
+        delete ds;
+        return st;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&ds->arena32, l32.size)) != cudaSuccess ||
+        (e = cudaMalloc(&ds->otf_data, grid_off + grids.size() * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ds->err, sizeof(int))) != cudaSuccess || (e = cudaMemset(ds->err, 0, sizeof(int))) != cudaSuccess) {
+        set_error("bf_factor_otf: cudaMalloc: %s", cudaGetErrorString(e));
+        return fail(e == cudaErrorMemoryAllocation ? BF_ERR_NOMEM : BF_ERR_CUDA);
+    }
+    for (auto& pt : l32.parts)
+        if ((e = cudaMemcpy((unsigned char*)ds->arena32 + pt.first, pt.second.data(), pt.second.size(),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            break;
+    if (e == cudaSuccess) e = cudaMemcpy(ds->otf_data, rows.data(), rows_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy((unsigned char*)ds->otf_data + grid_off, grids.data(), grids.size() * sizeof(int),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        set_error("bf_factor_otf: copy: %s", cudaGetErrorString(e));
+        return fail(BF_ERR_CUDA);
+    }
+    ds->bytes32 = l32.size + grid_off + grids.size() * sizeof(int);
+    for (size_t i = 0; i < p->blocks.size(); ++i) {
+        const BlockFactors& Bf = p->blocks[i];
+        DevBlock db;
+        db.g = geo_of(Bf);
+        db.g.otf = 1;
+        db.row0 = Bf.row0;
+        db.col0 = Bf.col0;
+        bind(db.f32, (unsigned char*)ds->arena32, o32[i]);
+        db.f32.EV = db.f32.EH = db.f32.S = db.f32.FG = db.f32.EU = nullptr;
+        db.ph.rows = (const uint4*)ds->otf_data;
+        db.ph.grids = (const int*)((const unsigned char*)ds->otf_data + grid_off);
+        db.ph.row0 = (int)Bf.row0;
+        db.ph.col0 = (int)Bf.col0;
+        db.ph.half = (int)(Ng / 2);
+        int lN = 0;
+        while (((int64_t)1 << lN) < Bf.N) ++lN;
+        db.ph.lN = lN;
+        db.ph.sh1 = xxi ? 32 - lNg : -1;
+        db.ph.sh2 = sq ? 30 - lNg : -1;
+        ds->blocks.push_back(db);
+    }
+    p->dev = ds;
+    return BF_OK;
+}
+
 bf_status device_upload(bf_plan* p)
 {
     if (p->dev) return BF_OK;
@@ -360,6 +485,10 @@ bf_status device_upload(bf_plan* p)
 bf_status device_reserve(bf_plan* p, bf_precision prec, int64_t m, void*)
 {
     DeviceState* ds = p->dev;
+    if (ds->otf && prec != BF_PREC_F32) {
+        set_error("plan factored by bf_factor_otf: only BF_PREC_F32 applies (no phase tables)");
+        return BF_ERR_UNSUPPORTED;
+    }
     BF_CUDA(cudaSetDevice(ds->device));
     size_t need = 0;
     for (auto& B : ds->blocks) {
@@ -450,6 +579,10 @@ bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, 
 {
     DeviceState* ds = p->dev;
     cudaStream_t st = (cudaStream_t)stream;
+    if (ds->otf && prec != BF_PREC_F32) {
+        set_error("bf_apply: plan factored by bf_factor_otf: only BF_PREC_F32 applies (no phase tables)");
+        return BF_ERR_UNSUPPORTED;
+    }
     if (prec == BF_PREC_BF16X3) {
         for (auto& B : ds->blocks) {
             const char* why = "";
@@ -511,6 +644,10 @@ bf_status device_apply_ws(bf_plan* p, bf_precision prec, const void* F, int64_t 
 {
     DeviceState* ds = p->dev;
     cudaStream_t st = (cudaStream_t)stream;
+    if (ds->otf && prec != BF_PREC_F32) {
+        set_error("plan factored by bf_factor_otf: only BF_PREC_F32 applies (no phase tables)");
+        return BF_ERR_UNSUPPORTED;
+    }
     if (prec == BF_PREC_BF16X3) {
         for (auto& B : ds->blocks) {
             const char* why = "";
@@ -593,6 +730,7 @@ void device_free(bf_plan* p)
     cudaFree(ds->ws64);
     cudaFree(ds->ws32);
     cudaFree(ds->stage);
+    cudaFree(ds->otf_data);
     cudaFree(ds->err);
     delete ds;
     p->dev = nullptr;

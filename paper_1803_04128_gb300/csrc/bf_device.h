@@ -17,6 +17,25 @@ struct Geo {
     int r, n0, L, h, l1, nv;  // nv = n0 * 2^l1 (V and U leaf size)
     int kH, kG;               // number of H and G levels
     int ra;                   // amplitude rank
+    int otf = 0;              // 1: no phase tables, the kernels evaluate the phases (OtfPhase)
+};
+
+// Phases evaluated inside the apply kernels (bf_factor_otf).  Every entry of
+// the phase tables is e^{2 pi i (sum of +-Phi at grid points)} (Sec. 4, Eqs. 1,
+// 2, 3, bf3 and the switch step of Algorithm 4.1), and for the built-in kinds
+// Phi(x_i, xi_j) mod 1 at global grid indices (i, j), xi = j - Ng/2, is
+//   xxi * (i xi mod Ng) / Ng + kappa_i |xi| + rho_i + sq * (xi^2 mod 4 Ng) / (4 Ng).
+// The kernels hold it as an unsigned 32-bit count of 2^-32 turns, so sums and
+// differences of phases wrap mod 1 exactly: the integer residues are exact,
+// kappa_i |xi| is a 64-bit fixed-point product (K_i = frac(kappa_i) 2^64).
+struct OtfPhase {
+    const uint4* rows = nullptr;  // [Ng] per global row i: (K_i low word, K_i high word, round(frac(rho_i) 2^32), 0)
+    const int* grids = nullptr;   // [lN + 1][16]: interpolation indices of a node of 2^e points (grid_rel)
+    int row0 = 0, col0 = 0;       // block origin in global indices (Ng <= 2^30)
+    int half = 0;                 // Ng / 2
+    int lN = 0;                   // log2 of the block size
+    int sh1 = -1;                 // 32 - log2 Ng if the x xi term is present, else -1
+    int sh2 = -1;                 // 30 - log2 Ng if the xi^2 term is present, else -1
 };
 
 // Factor arrays of one sub-BF in one precision; T = float or double, C = float2/double2.
@@ -43,6 +62,7 @@ struct DevFactors {
 struct DevBlock {
     Geo g{};
     int64_t row0 = 0, col0 = 0;
+    OtfPhase ph;  // g.otf = 1 only
     DevFactors<double, double2> f64;
     DevFactors<float, float2> f32;
 };
@@ -61,6 +81,8 @@ struct DeviceState {
     void* stage = nullptr;  // F/G staging for bf_apply_host
     size_t stage_bytes = 0;
     int* err = nullptr;     // device error word (0 = ok)
+    bool otf = false;       // factored by bf_factor_otf: no phase tables, FP32 apply only
+    void* otf_data = nullptr;  // OtfPhase rows and grids
     // the plain FP64 apply (one launch per stage) replayed from a CUDA graph
     // captured for the last (F, G, m, workspace)
     cudaStream_t cap = nullptr;

@@ -77,6 +77,37 @@ double KernelFn::phase_frac(int64_t i, int64_t j) const
     return t1 + t2;
 }
 
+bool KernelFn::row_terms(int64_t i, double* kappa, double* rho, int* xxi, int* sq) const
+{
+    const double x = (double)i / (double)n_global;
+    const double s = d.phase_param;
+    *kappa = *rho = 0.0;
+    *xxi = *sq = 0;
+    switch (d.phase_kind) {
+    case BF_PHASE_DFT:
+        *xxi = 1;
+        return true;
+    case BF_PHASE_FIO:
+        *xxi = 1;
+        *kappa = (2.0 + s * std::sin(kTwoPi * x)) / 16.0;
+        return true;
+    case BF_PHASE_FIO_PW: {
+        *xxi = 1;
+        const double c = (2.0 + s * std::sin(kTwoPi * x)) / 16.0;
+        *kappa = (2 * i < n_global) ? c : -0.5 * c;
+        return true;
+    }
+    case BF_PHASE_ONES:
+        return true;
+    case BF_PHASE_SEP:
+        *sq = 1;
+        *rho = 0.3 * std::sin(kTwoPi * x);
+        return true;
+    default:
+        return false;
+    }
+}
+
 cd KernelFn::amplitude(int64_t i, int64_t j) const
 {
     const int64_t Ng = n_global;

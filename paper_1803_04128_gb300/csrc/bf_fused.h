@@ -34,6 +34,7 @@ struct FrontArgs {
     WLayout wl;
     int64_t c0_lo;     // first T_Omega node (level L-h) of this shard's tiles
     int64_t xi_lo;     // F holds rows xi_lo ..: row xi at F + (xi - xi_lo) * m
+    OtfPhase ph;       // g.otf = 1: phases evaluated in the kernel (EV, EH, S unused)
 };
 
 struct BackArgs {
@@ -52,6 +53,7 @@ struct BackArgs {
     const float2* ak;  // [ra][N]
     float2* G;         // [N][m]
     int beta;
+    OtfPhase ph;       // g.otf = 1: phases evaluated in the kernel (FG, EU unused)
 };
 
 // One operator of a batched launch: its front and back argument blocks and work counts.
@@ -82,6 +84,9 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
 // one of the two fused FP32 kernels with prepared arguments (nblocks CTAs)
 cudaError_t launch_f32_front(int r, const FrontArgs& fa, size_t smem, int64_t nblocks, cudaStream_t st);
 cudaError_t launch_f32_back(int r, const BackArgs& ba, size_t smem, int64_t nblocks, cudaStream_t st);
+// the same with the phases evaluated in the kernel (bf_kernels_otf.cu; args with g.otf = 1)
+cudaError_t launch_part_otf(int r, const FrontArgs* fa, const BackArgs* ba, size_t smem, int64_t nblocks,
+                            cudaStream_t st);
 // set_attr: only set the kernel's shared-memory limit to bl.smem (no launch);
 // grid_out != NULL: only compute the persistent grid (occupancy x SMs) for bl.smem;
 // otherwise launch (bl.grid CTAs).

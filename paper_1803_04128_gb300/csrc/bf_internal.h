@@ -22,6 +22,9 @@ struct KernelFn {
     int64_t n_global = 0;  // grid size of x_i = i/n_global, xi_j = j - n_global/2
     // Phi(x_i, xi_j) reduced mod 1 (exactly for the built-in kinds).
     double phase_frac(int64_t i, int64_t j) const;
+    // For the built-in kinds, phase_frac(i, j) = xxi (i xi mod Ng) / Ng + kappa_i |xi| + rho_i
+    // + sq (xi^2 mod 4 Ng) / (4 Ng) mod 1 (xi = j - Ng/2); false for user phases.
+    bool row_terms(int64_t i, double* kappa, double* rho, int* xxi, int* sq) const;
     cd amplitude(int64_t i, int64_t j) const;
 };
 
@@ -63,6 +66,7 @@ struct bf_plan {
     int r = 0, n0 = 1, L = 0, h = 0, l1 = 0;
     bool factored = false;
     bool user_kinds_lost = false;  // loaded from file with user callbacks
+    bool otf = false;              // factored by bf_factor_otf (no phase tables; FP32 applies only)
     std::vector<bfi::BlockFactors> blocks;  // 1 or 4
     bfi::DeviceState* dev = nullptr;
     std::map<int64_t, int> tuned_mr;  // autotuned column-slice width per m (FP32 fused apply)
@@ -113,6 +117,8 @@ bf_status device_upload(bf_plan* p);
 // device construction of the phase tables (bf_construct.cu, bf_device.cu)
 bool construct_supported(int phase_kind);
 bf_status device_construct(bf_plan* p);
+// device residency without phase tables (bf_factor_otf): the FP32 kernels evaluate the phases
+bf_status device_otf(bf_plan* p);
 bf_status device_reserve(bf_plan* p, bf_precision prec, int64_t m, void* stream);
 bf_status device_apply(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G,
                        void* stream);

@@ -63,7 +63,7 @@ bf_status bf_plan_save(const bf_plan* p, const char* path)
     }
     for (auto& B : p->blocks)
         if (B.S.empty()) {
-            set_error("bf_plan_save: host factors were released (keep_host = 0)");
+            set_error("bf_plan_save: the host holds no phase tables (keep_host = 0, bf_factor_device or bf_factor_otf)");
             return BF_ERR_STATE;
         }
     FILE* f = fopen(path, "wb");

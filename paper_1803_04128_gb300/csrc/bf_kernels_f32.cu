@@ -1,532 +1,13 @@
-// Fused FP32 apply of one sub-BF in two launches.
-//
-// Front pass (one CTA per tile x column slice): reads 2^kH consecutive
-// xi-leaves of F, applies V (Eq. 1), all kH H levels (Eq. 2) and the switch
-// (step 4 of Algorithm 4.1) with the coefficients held in shared memory, and
-// writes the switch-level coefficients.  A front tile is fixed by an x-node p
-// at level l1 and a chunk c0 of T_Omega nodes: its 2^kH pairs stay closed
-// under the kH H levels because the pair (A, B) at level l only depends on
-// (parent(A), children(B)) at level l-1 (Sec. 4).
-//
-// Back pass (one CTA per x-node p' at level h x column slice): loops over the
-// 2^l1 chunks c0' of T_Omega nodes; for each, loads 2^kG switch-level pairs,
-// applies the kG G levels (Eq. 3), and accumulates the U stage (Eq. bf3) of
-// its 2^kG x-leaves in shared memory; finally multiplies by a_k and sums the
-// amplitude terms (Eq. tg) into G.
-//
-// Inside a tile the levels run in place: after level j the coefficients of
-// the logical pair [a: j bits][b: K-j bits] live in slot b * 2^j + rev_j(a),
-// so every group of two pairs reads and writes the same two slots.
-//
-// Columns: a tile carries CT = r_alpha * mr live columns, col = k * mr + c
-// (amplitude term k, right-hand side slice * mr + c), padded to CTp, a power
-// of two, so that a thread's column is tid & (CTp - 1).  Global state between
-// the passes: W[slice][q][t][CTp] (q = switch-level pair index).
-//
-// Every tile input (factor phases, Lagrange matrices, the F rows, b_k) is
-// staged into shared memory with cp.async in one commit group before use.
+// Fused FP32 apply of one sub-BF in two launches (front: V, H levels, switch;
+// back: G levels, U), phases read from the tables; the batched persistent
+// kernel; configuration and launchers.  The tile bodies are in bf_f32_tile.h.
 #include <algorithm>
 #include <cstdio>
 
-#include "bf_device.h"
-#include "bf_fused.h"
+#include "bf_f32_tile.h"
 
 namespace bfi {
 namespace {
-
-constexpr int kThreads = 256;
-
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b)
-{
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ void cfmaf(float2& acc, float2 a, float2 b)
-{
-    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
-    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
-}
-__device__ __forceinline__ unsigned brev(unsigned v, int bits)
-{
-    return bits == 0 ? 0u : (__brev(v) >> (32 - bits));
-}
-
-// ---- cp.async (16- and 8-byte, the latter with zero fill) ----
-__device__ __forceinline__ void cp16(void* dst, const void* src)
-{
-    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp8(void* dst, const void* src, bool valid)
-{
-    unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    int n = valid ? 8 : 0;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// wait until at most 0 / 1 of this thread's committed groups are still pending
-__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// real rows x cols matrix (row-major, global) -> shared rows padded to c4 floats, 8-byte copies
-__device__ __forceinline__ void stage_matrix(float* dst, const float* src, int rows, int cols, int c4, int tid)
-{
-    const int half = cols / 2;
-    for (int e = tid; e < rows * half; e += kThreads) {
-        const int rr = e / half, cc = e - rr * half;
-        cp8(dst + rr * c4 + 2 * cc, src + rr * cols + 2 * cc, true);
-    }
-}
-
-// pair index of (a, b) of column slice sl in the workspace layout w
-__device__ __forceinline__ int64_t w_pair(const WLayout& w, int64_t a, int64_t b, int sl)
-{
-    const int64_t d = a >> w.la, s = b >> w.lb;
-    return d * w.sD + s * w.sS + sl * w.slice + ((a - (d << w.la)) << w.lb) + (b - (s << w.lb));
-}
-
-template <int R>
-struct Pad4 {
-    static constexpr int v = (R + 3) & ~3;
-};
-
-// H level (Eq. 2) on one (group, column): two inputs -> two outputs in place.
-template <int R>
-__device__ __forceinline__ void h_item(float2* x0, float2* x1, int CTp, const float2* E0, const float2* E1,
-                                       const float* Mh)
-{
-    constexpr int R4 = Pad4<R>::v;
-    float2 lam[2 * R];
-#pragma unroll
-    for (int s = 0; s < R; ++s) {
-        lam[s] = x0[s * CTp];
-        lam[R + s] = x1[s * CTp];
-    }
-    float2 o0[R], o1[R];
-#pragma unroll
-    for (int t = 0; t < R; ++t) o0[t] = o1[t] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int cs2 = 0; cs2 < R; ++cs2) {
-        const float4 e0 = reinterpret_cast<const float4*>(E0)[cs2];
-        const float4 e1 = reinterpret_cast<const float4*>(E1)[cs2];
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-            const int cs = 2 * cs2 + h2;
-            const float2 u0 = cmulf(h2 ? make_float2(e0.z, e0.w) : make_float2(e0.x, e0.y), lam[cs]);
-            const float2 u1 = cmulf(h2 ? make_float2(e1.z, e1.w) : make_float2(e1.x, e1.y), lam[cs]);
-            const float4* mh = reinterpret_cast<const float4*>(Mh + cs * R4);
-#pragma unroll
-            for (int t4 = 0; t4 < R4 / 4; ++t4) {
-                const float4 w = mh[t4];
-                const float ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int t = 4 * t4 + q;
-                    if (t < R) {
-                        o0[t].x = fmaf(ww[q], u0.x, o0[t].x);
-                        o0[t].y = fmaf(ww[q], u0.y, o0[t].y);
-                        o1[t].x = fmaf(ww[q], u1.x, o1[t].x);
-                        o1[t].y = fmaf(ww[q], u1.y, o1[t].y);
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-        x0[t * CTp] = o0[t];
-        x1[t * CTp] = o1[t];
-    }
-}
-
-// G level (Eq. 3) on one (group, column): nu_pos = sum_c FG[pos][c] (MG[pos] nu_c).
-template <int R>
-__device__ __forceinline__ void g_item(float2* x0, float2* x1, int CTp, const float2* F0, const float2* F1,
-                                       const float* Mg)
-{
-    constexpr int R4 = Pad4<R>::v;
-    float2 nu0[R], nu1[R];
-#pragma unroll
-    for (int s = 0; s < R; ++s) {
-        nu0[s] = x0[s * CTp];
-        nu1[s] = x1[s * CTp];
-    }
-#pragma unroll
-    for (int pos = 0; pos < 2; ++pos) {
-        float2 w0[R], w1[R];
-#pragma unroll
-        for (int t = 0; t < R; ++t) w0[t] = w1[t] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int s = 0; s < R; ++s) {
-            const float4* mg = reinterpret_cast<const float4*>(Mg + (pos * R + s) * R4);
-#pragma unroll
-            for (int t4 = 0; t4 < R4 / 4; ++t4) {
-                const float4 w = mg[t4];
-                const float ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int t = 4 * t4 + q;
-                    if (t < R) {
-                        w0[t].x = fmaf(ww[q], nu0[s].x, w0[t].x);
-                        w0[t].y = fmaf(ww[q], nu0[s].y, w0[t].y);
-                        w1[t].x = fmaf(ww[q], nu1[s].x, w1[t].x);
-                        w1[t].y = fmaf(ww[q], nu1[s].y, w1[t].y);
-                    }
-                }
-            }
-        }
-        const float2* Fp = pos ? F1 : F0;  // [c][t]
-        float2* xo = pos ? x1 : x0;
-#pragma unroll
-        for (int t2 = 0; t2 < R / 2; ++t2) {
-            const float4 fa = reinterpret_cast<const float4*>(Fp)[t2];
-            const float4 fb = reinterpret_cast<const float4*>(Fp + R)[t2];
-            float2 o = cmulf(make_float2(fa.x, fa.y), w0[2 * t2]);
-            cfmaf(o, make_float2(fb.x, fb.y), w1[2 * t2]);
-            xo[(2 * t2) * CTp] = o;
-            float2 o2 = cmulf(make_float2(fa.z, fa.w), w0[2 * t2 + 1]);
-            cfmaf(o2, make_float2(fb.z, fb.w), w1[2 * t2 + 1]);
-            xo[(2 * t2 + 1) * CTp] = o2;
-        }
-    }
-}
-
-// ------------------------------------------------------------------ front --
-// Shared memory: Mv^T [NV][R4] | MH^T [kH][2R][R4] | per tile u < tpc:
-// X [T][R][CTp] | EH double buffer [2][T][2][R] | EV [T*NV] | F rows [T*NV][mr].
-// A CTA applies tpc consecutive tiles (work indices work * tpc + u): with few
-// columns per tile, several tiles share the CTA's threads and their loads are
-// in flight together; each tile's arithmetic is the same for any tpc.  The
-// phases of level j are staged (cp.async) while level j-1 is computed; b_k and
-// the switch matrices are read through the read-only cache.
-template <int R, int NV>
-__device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, unsigned char* smem_raw)
-{
-    constexpr int R4 = Pad4<R>::v;
-    const Geo& g = A.g;
-    const int K = g.kH, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra, tpc = A.tpc;
-    const int nP = 1 << g.l1;                        // x-nodes at level l1
-    const int64_t nBh = (int64_t)1 << (g.L - g.h);   // T_Omega nodes at level L-h
-    const int64_t N = g.N, P = g.P, m = A.m;
-    const int L = g.L, l1 = g.l1;
-    const size_t tile_f2 = (size_t)T * R * CTp + (size_t)2 * T * 2 * R + (size_t)T * NV + (size_t)T * NV * mr;
-
-    float* MvTs = reinterpret_cast<float*>(smem_raw);                      // [NV][R4]
-    float* MHTs = MvTs + NV * R4;                                          // [K][2R][R4]
-    float2* tiles = reinterpret_cast<float2*>(MHTs + (size_t)K * 2 * R * R4);
-    auto Xof = [&](int u) { return tiles + (size_t)u * tile_f2; };                         // [T][R][CTp]
-    auto EHof = [&](int u) { return Xof(u) + (size_t)T * R * CTp; };                       // [2][T][2][R]
-    auto EVof = [&](int u) { return EHof(u) + (size_t)2 * T * 2 * R; };                    // [T*NV]
-    auto Fof = [&](int u) { return EVof(u) + (size_t)T * NV; };                            // [T*NV][mr]
-    // tile u: work index work * tpc + u -> (column slice, x-node p, T_Omega chunk c0)
-    __shared__ int64_t s_p[16], s_c0[16];
-    __shared__ int s_slice[16];
-    const int tid = threadIdx.x;
-    if (tid < tpc) {
-        const int64_t idx = work * tpc + tid, tile = idx / A.nslice;
-        s_slice[tid] = (int)(idx - tile * A.nslice);
-        s_p[tid] = tile & (nP - 1);
-        s_c0[tid] = A.c0_lo + (tile >> l1);
-    }
-    __syncthreads();
-    auto slice_of = [&](int u) { return s_slice[u]; };
-    auto p_of = [&](int u) { return s_p[u]; };
-    auto c0_of = [&](int u) { return s_c0[u]; };
-
-    const float2* EHg = A.EH;
-    auto stage_eh = [&](int j) {  // phases of level l1 + j into buffer (j - 1) & 1 of every tile
-        const int64_t nBl = (int64_t)1 << (L - l1 - j);
-        const float2* eh = EHg + (size_t)(j - 1) * P * 2 * R;
-        for (int u = 0; u < tpc; ++u) {
-            const int64_t p = p_of(u), c0 = c0_of(u);
-            float2* dst = EHof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
-            for (int e = tid; e < T * R; e += kThreads) {  // R 16-byte chunks per pair
-                const int lp = e / R, w = e - lp * R;
-                const int64_t ap = (p << j) + (lp >> (K - j));
-                const int64_t bp = (c0 << (K - j)) + (lp & ((1 << (K - j)) - 1));
-                cp16(dst + (size_t)lp * 2 * R + 2 * w, eh + (ap * nBl + bp) * 2 * R + 2 * w);
-            }
-        }
-    };
-    // group 0: matrices, EV, F rows, level-1 phases; group 1: level-2 phases
-    stage_matrix(MvTs, A.MvT, NV, R, R4, tid);
-    stage_matrix(MHTs, A.MHT, K * 2 * R, R, R4, tid);
-    for (int u = 0; u < tpc; ++u) {
-        const int64_t xi_base = c0_of(u) * T * NV;
-        const float2* ev = A.EV + p_of(u) * N + xi_base;
-        float2* EVs = EVof(u);
-        for (int e = tid; e < T * NV / 2; e += kThreads) cp16(EVs + 2 * e, ev + 2 * e);
-        const int64_t cbase = (int64_t)slice_of(u) * mr;
-        float2* Fs = Fof(u);
-        for (int e = tid; e < T * NV * mr; e += kThreads) {
-            const int row = e >> lmr, c = e & (mr - 1);
-            const bool valid = cbase + c < m;
-            cp8(Fs + e, A.F + (xi_base - A.xi_lo + row) * m + (valid ? cbase + c : 0), valid);
-        }
-    }
-    if (K >= 1) stage_eh(1);
-    cp_commit();
-    if (K >= 2) {
-        stage_eh(2);
-        cp_commit();
-    }
-    // padding columns of the tiles start (and stay) at zero
-    for (int u = 0; u < tpc; ++u) {
-        float2* X = Xof(u);
-        for (int e = tid; e < T * R * CTp; e += kThreads)
-            if ((e & (CTp - 1)) >= ra * mr) X[e] = make_float2(0.f, 0.f);
-    }
-    if (K >= 2) cp_wait1(); else cp_wait0();
-    __syncthreads();
-
-    // ---- V (Eq. 1): item (u, j, c) computes mu[j][.][k*mr + c] of tile u for every k
-    // (with few items, one item per amplitude term k instead)
-    const int nk = (ra > 1 && tpc * T * mr * 2 <= kThreads) ? ra : 1;
-    for (int itk = tid; itk < tpc * T * mr * nk; itk += kThreads) {
-        const int it = itk / nk, kk = itk - it * nk;
-        const int c = it & (mr - 1), j = (it >> lmr) & (T - 1), u = it >> (lmr + K);
-        const int64_t xi_base = c0_of(u) * T * NV;
-        const float2* fs = Fof(u) + (size_t)j * NV * mr + c;
-        const float2* EVs = EVof(u);
-        float2 f[NV];
-#pragma unroll
-        for (int x = 0; x < NV; ++x) f[x] = fs[x * mr];
-        for (int k = nk > 1 ? kk : 0; k < (nk > 1 ? kk + 1 : ra); ++k) {
-            float2 acc[R];
-#pragma unroll
-            for (int t = 0; t < R; ++t) acc[t] = make_float2(0.f, 0.f);
-            const float2* bk = A.bk + (size_t)k * N + xi_base + j * NV;
-#pragma unroll
-            for (int x = 0; x < NV; ++x) {
-                const float2 z = cmulf(EVs[j * NV + x], cmulf(__ldg(bk + x), f[x]));
-                const float4* mv = reinterpret_cast<const float4*>(MvTs + x * R4);
-#pragma unroll
-                for (int t4 = 0; t4 < R4 / 4; ++t4) {
-                    const float4 w = mv[t4];
-                    const float ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int t = 4 * t4 + q;
-                        if (t < R) {
-                            acc[t].x = fmaf(ww[q], z.x, acc[t].x);
-                            acc[t].y = fmaf(ww[q], z.y, acc[t].y);
-                        }
-                    }
-                }
-            }
-            float2* xo = Xof(u) + (size_t)j * R * CTp + k * mr + c;
-#pragma unroll
-            for (int t = 0; t < R; ++t) xo[t * CTp] = acc[t];
-        }
-    }
-    __syncthreads();
-
-    // ---- H levels (Eq. 2), in place; item (u, grp, col)
-    for (int j = 1; j <= K; ++j) {
-        if (j > 1) {
-            if (j < K) cp_wait1(); else cp_wait0();
-            __syncthreads();
-        }
-        const int kj = K - j, half = 1 << kj;
-        const float* Mh = MHTs + (size_t)(j - 1) * 2 * R * R4;
-        for (int it = tid; it < tpc * (T / 2) * CTp; it += kThreads) {
-            const int col = it & (CTp - 1), grp = (it >> lct) & (T / 2 - 1), u = it >> (lct + K - 1);
-            const int a = grp >> kj, bp = grp & (half - 1);
-            const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
-            float2* x0 = Xof(u) + (size_t)base * R * CTp + col;
-            float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
-            const float2* Eh = EHof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
-            h_item<R>(x0, x1, CTp, Eh + (size_t)((2 * a) * half + bp) * 2 * R,
-                      Eh + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mh);
-        }
-        __syncthreads();
-        if (j + 2 <= K) {
-            stage_eh(j + 2);
-            cp_commit();
-        }
-    }
-
-    // ---- switch (step 4) and write-out of the switch-level coefficients; item (u, lp, col)
-    for (int it = tid; it < tpc * T * CTp; it += kThreads) {
-        const int col = it & (CTp - 1), lp = (it >> lct) & (T - 1), u = it >> (lct + K);
-        const int slot = (int)brev((unsigned)lp, K);
-        const float2* xs = Xof(u) + (size_t)slot * R * CTp + col;
-        float2 mu[R];
-#pragma unroll
-        for (int s = 0; s < R; ++s) mu[s] = xs[s * CTp];
-        const int64_t q = ((p_of(u) << K) + lp) * nBh + c0_of(u);
-        const float4* Sp = reinterpret_cast<const float4*>(A.S + q * R * R);
-        float2* wo = A.W + (size_t)w_pair(A.wl, (p_of(u) << K) + lp, c0_of(u), slice_of(u)) * R * CTp + col;
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int s2 = 0; s2 < R / 2; ++s2) {
-                const float4 sv = __ldg(Sp + t * (R / 2) + s2);
-                cfmaf(acc, make_float2(sv.x, sv.y), mu[2 * s2]);
-                cfmaf(acc, make_float2(sv.z, sv.w), mu[2 * s2 + 1]);
-            }
-            wo[t * CTp] = acc;
-        }
-    }
-}
-
-// ------------------------------------------------------------------- back --
-// Shared memory: MG^T [kG][2][R][R4] | MU [NU][R4] | U accumulator [XN][mr] |
-// per chunk u < tpc: X [T][R][CTp] | FG double buffer [2][T][2][R] | EU [XN].
-// The 2^l1 chunks c0' of T_Omega nodes are taken tpc at a time: their loads and
-// G levels run together, their U contributions are accumulated one chunk after
-// the other in increasing c0' (the same order for any tpc).
-template <int R, int NU>
-__device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsigned char* smem_raw)
-{
-    constexpr int R4 = Pad4<R>::v;
-    const Geo& g = A.g;
-    const int K = g.kG, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra, tpc = A.tpc;
-    const int slice = (int)(work % A.nslice);
-    const int64_t pp = A.pp_lo + work / A.nslice;  // x-node at level h
-    const int nC = 1 << g.l1;                      // chunks c0' (= T_Omega nodes at level l1)
-    const int XN = T * NU;                         // output points of this CTA
-    const int64_t N = g.N, P = g.P;
-    const int L = g.L, h = g.h;
-    const size_t chunk_f2 = (size_t)T * R * CTp + (size_t)2 * T * 2 * R + XN;
-
-    float* MGTs = reinterpret_cast<float*>(smem_raw);                 // [K][2][R][R4]
-    float* MUs = MGTs + (size_t)K * 2 * R * R4;                       // [NU][R4]
-    float2* acc = reinterpret_cast<float2*>(MUs + (size_t)NU * R4);   // [XN][mr]
-    float2* chunks = acc + (size_t)XN * mr;
-    auto Xof = [&](int u) { return chunks + (size_t)u * chunk_f2; };             // [T][R][CTp]
-    auto FGof = [&](int u) { return Xof(u) + (size_t)T * R * CTp; };             // [2][T][2][R]
-    auto EUof = [&](int u) { return FGof(u) + (size_t)2 * T * 2 * R; };          // [XN]
-
-    const int tid = threadIdx.x;
-    const int64_t x0g = pp * XN;
-    const float2* FGg = A.FG;
-    int c0b = 0;
-    auto stage_fg = [&](int j) {  // phases of level h + j into buffer (j - 1) & 1 of every chunk
-        const int64_t nBl = (int64_t)1 << (L - h - j);
-        const float2* fg = FGg + (size_t)(j - 1) * P * 2 * R;
-        for (int u = 0; u < tpc; ++u) {
-            float2* dst = FGof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
-            for (int e = tid; e < T * R; e += kThreads) {
-                const int lp = e / R, w = e - lp * R;
-                const int64_t ap = (pp << j) + (lp >> (K - j));
-                const int64_t bp = ((int64_t)(c0b + u) << (K - j)) + (lp & ((1 << (K - j)) - 1));
-                cp16(dst + (size_t)lp * 2 * R + 2 * w, fg + (ap * nBl + bp) * 2 * R + 2 * w);
-            }
-        }
-    };
-    stage_matrix(MGTs, A.MGT, K * 2 * R, R, R4, tid);
-    stage_matrix(MUs, A.MU, NU, R, R4, tid);
-    for (int e = tid; e < XN * mr; e += kThreads) acc[e] = make_float2(0.f, 0.f);
-
-    for (c0b = 0; c0b < nC; c0b += tpc) {
-        __syncthreads();  // the previous chunks' U stage is done with X and EU
-        for (int u = 0; u < tpc; ++u) {  // pairs (pp, c0 * T + j), j < T: one contiguous block of T*R*CTp
-            const int c0 = c0b + u;
-            const float2* src = A.W + (size_t)w_pair(A.wl, pp, (int64_t)c0 * T, slice) * R * CTp;
-            float2* X = Xof(u);
-            for (int e = tid; e < T * R * CTp / 2; e += kThreads) cp16(X + 2 * e, src + 2 * e);
-            float2* EUs = EUof(u);
-            for (int e = tid; e < XN / 2; e += kThreads) cp16(EUs + 2 * e, A.EU + (size_t)c0 * N + x0g + 2 * e);
-        }
-        if (K >= 1) stage_fg(1);
-        cp_commit();
-        if (K >= 2) {
-            stage_fg(2);
-            cp_commit();
-        }
-        if (K >= 2) cp_wait1(); else cp_wait0();
-        __syncthreads();
-
-        // ---- G levels (Eq. 3), in place; item (u, grp, col)
-        for (int j = 1; j <= K; ++j) {
-            if (j > 1) {
-                if (j < K) cp_wait1(); else cp_wait0();
-                __syncthreads();
-            }
-            const int kj = K - j, half = 1 << kj;
-            const float* Mg = MGTs + (size_t)(j - 1) * 2 * R * R4;
-            for (int it = tid; it < tpc * (T / 2) * CTp; it += kThreads) {
-                const int col = it & (CTp - 1), grp = (it >> lct) & (T / 2 - 1), u = it >> (lct + K - 1);
-                const int a = grp >> kj, bp = grp & (half - 1);
-                const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
-                float2* x0 = Xof(u) + (size_t)base * R * CTp + col;
-                float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
-                const float2* Fg = FGof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
-                g_item<R>(x0, x1, CTp, Fg + (size_t)((2 * a) * half + bp) * 2 * R,
-                          Fg + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mg);
-            }
-            __syncthreads();
-            if (j + 2 <= K) {
-                stage_fg(j + 2);
-                cp_commit();
-            }
-        }
-
-        // ---- U (Eq. bf3) contributions of T_Omega nodes c0b .. c0b + tpc - 1, in that order;
-        // each accumulator entry (lp, i, c) belongs to one thread.  Item (lp, c, part): part
-        // of nis equal ranges of the NU points i (nis > 1 only when T * mr < kThreads)
-        {
-            int lnis = 0;
-            while ((1 << lnis) < NU && ((T * mr) << (lnis + 1)) <= kThreads) ++lnis;
-            const int nis = 1 << lnis, ni = NU >> lnis;
-            const int c = tid & (mr - 1), part = (tid >> lmr) & (nis - 1);
-            for (int lp = tid >> (lmr + lnis); lp < T; lp += kThreads >> (lmr + lnis)) {
-                const int slot = (int)brev((unsigned)lp, K);
-                float2* ap = acc + (size_t)lp * NU * mr + c;
-                for (int u = 0; u < tpc; ++u) {
-                    const float2* xs = Xof(u) + (size_t)slot * R * CTp + c;
-                    const float2* EUs = EUof(u);
-                    for (int k = 0; k < ra; ++k) {
-                        float2 v[R];
-#pragma unroll
-                        for (int s = 0; s < R; ++s) v[s] = xs[s * CTp + k * mr];
-                        const float2* ak = A.ak + (size_t)k * N + x0g + lp * NU;
-#pragma unroll 4
-                        for (int i = part * ni; i < (part + 1) * ni; ++i) {
-                            float2 w = make_float2(0.f, 0.f);
-                            const float4* mu = reinterpret_cast<const float4*>(MUs + i * R4);
-#pragma unroll
-                            for (int s4 = 0; s4 < R4 / 4; ++s4) {
-                                const float4 m4 = mu[s4];
-                                const float mm[4] = {m4.x, m4.y, m4.z, m4.w};
-#pragma unroll
-                                for (int q = 0; q < 4; ++q) {
-                                    const int s = 4 * s4 + q;
-                                    if (s < R) {
-                                        w.x = fmaf(mm[q], v[s].x, w.x);
-                                        w.y = fmaf(mm[q], v[s].y, w.y);
-                                    }
-                                }
-                            }
-                            float2 o = ap[i * mr];
-                            cfmaf(o, cmulf(__ldg(ak + i), EUs[lp * NU + i]), w);
-                            ap[i * mr] = o;
-                        }
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();
-    // ---- write G
-    {
-        const int c = tid & (mr - 1);
-        const int64_t cg = (int64_t)slice * mr + c;
-        if (cg < A.m) {
-            for (int x = tid >> lmr; x < XN; x += kThreads >> lmr) {
-                float2* gp = A.G + (x0g - A.x_lo + x) * A.m + cg;
-                float2 v = acc[x * mr + c];
-                if (A.beta) {
-                    const float2 o = *gp;
-                    v.x += o.x;
-                    v.y += o.y;
-                }
-                *gp = v;
-            }
-        }
-    }
-}
 
 template <int R, int NV>
 __global__ void __launch_bounds__(kThreads, 2) front_f32(FrontArgs A)
@@ -541,31 +22,6 @@ __global__ void __launch_bounds__(kThreads, 2) back_f32(BackArgs A)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     back_tile<R, NU>(A, blockIdx.x, smem_raw);
 }
-
-int ilog2(int v)
-{
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return l;
-}
-
-size_t front_smem(const Geo& g, int R, int NV, int CTp, int mr, int tpc)
-{
-    const size_t T = (size_t)1 << g.kH, R4 = (R + 3) & ~3;
-    return sizeof(float2) * (size_t)tpc * (T * R * CTp + 2 * T * 2 * R + T * NV + T * NV * mr) +
-           sizeof(float) * ((size_t)NV * R4 + (size_t)g.kH * 2 * R * R4);
-}
-
-size_t back_smem(const Geo& g, int R, int NU, int CTp, int mr, int tpc)
-{
-    const size_t T = (size_t)1 << g.kG, R4 = (R + 3) & ~3;
-    const size_t XN = T * NU;
-    return sizeof(float2) * (XN * mr + (size_t)tpc * (T * R * CTp + 2 * T * 2 * R + XN)) +
-           sizeof(float) * ((size_t)g.kG * 2 * R * R4 + (size_t)NU * R4);
-}
-
-template <int R>
-constexpr int nv_of() { return (R < 8) ? 8 : (R < 16 ? 16 : 32); }
 
 template <int R>
 cudaError_t launch_r(const FrontArgs& fa, const BackArgs& ba, size_t sf, size_t sb, int64_t nfront, int64_t nback,
@@ -760,6 +216,7 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     fa->wl = WLayout{g.h, g.L - g.h, 0, 0, g.P};
     fa->c0_lo = 0;
     fa->xi_lo = 0;
+    fa->ph = B.ph;
     ba->g = g;
     ba->m = m;
     ba->mr = cfg.mr;
@@ -779,6 +236,7 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     ba->ak = B.f32.a;
     ba->G = G;
     ba->beta = beta;
+    ba->ph = B.ph;
     *sf = front_smem(g, g.r, NV, CTp, cfg.mr, cfg.tpc_f);
     *sb = back_smem(g, g.r, NV, CTp, cfg.mr, cfg.tpc_b);
     *nfront = ((int64_t)1 << g.l1) * ((int64_t)1 << (g.L - g.h)) * cfg.nslice / cfg.tpc_f;
@@ -810,6 +268,7 @@ cudaError_t launch_part_r(const FrontArgs* fa, const BackArgs* ba, size_t smem, 
 cudaError_t launch_part(int r, const FrontArgs* fa, const BackArgs* ba, size_t smem, int64_t nblocks, cudaStream_t st)
 {
     if (nblocks < 1) return cudaSuccess;
+    if (fa ? fa->g.otf : ba->g.otf) return launch_part_otf(r, fa, ba, smem, nblocks, st);
     switch (r) {
     case 6: return launch_part_r<6>(fa, ba, smem, nblocks, st);
     case 8: return launch_part_r<8>(fa, ba, smem, nblocks, st);
@@ -842,6 +301,10 @@ cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, floa
     size_t sf, sb;
     int64_t nf, nb;
     if (!fused_make_args(B, F, m, G, beta, ws, mr_hint, &fa, &ba, &sf, &sb, &nf, &nb)) return cudaErrorNotSupported;
+    if (B.g.otf) {
+        const cudaError_t e = launch_part(B.g.r, &fa, nullptr, sf, nf, st);
+        return e != cudaSuccess ? e : launch_part(B.g.r, nullptr, &ba, sb, nb, st);
+    }
     switch (B.g.r) {
     case 6: return launch_r<6>(fa, ba, sf, sb, nf, nb, st);
     case 8: return launch_r<8>(fa, ba, sf, sb, nf, nb, st);

@@ -173,21 +173,12 @@ bf_status bf_factor(bf_plan* p)
     return BF_OK;
 }
 
-bf_status bf_factor_device(bf_plan* p)
+namespace {
+
+// Geometry, amplitude split and the real Lagrange matrices of every sub-BF,
+// without the phase tables (the device builds or evaluates those).
+bf_status factor_host_parts(bf_plan* p, const char* who)
 {
-    if (!p) {
-        set_error("bf_factor_device: NULL plan");
-        return BF_ERR_ARG;
-    }
-    if (p->factored) return bf_upload(p);
-    if (p->user_kinds_lost) {
-        set_error("bf_factor_device: plan was loaded without its callbacks");
-        return BF_ERR_STATE;
-    }
-    if (!bfi::construct_supported(p->kern.d.phase_kind)) {
-        set_error("bf_factor_device: phase kind %d has no device form (use bf_factor)", p->kern.d.phase_kind);
-        return BF_ERR_UNSUPPORTED;
-    }
     const int sp = p->opt.split;
     const int64_t Nb = p->N / sp;
     try {
@@ -208,15 +199,67 @@ bf_status bf_factor_device(bf_plan* p)
             }
     } catch (const std::bad_alloc&) {
         p->blocks.clear();
-        set_error("bf_factor_device: out of host memory");
+        set_error("%s: out of host memory", who);
         return BF_ERR_NOMEM;
     }
+    return BF_OK;
+}
+
+}  // namespace
+
+bf_status bf_factor_device(bf_plan* p)
+{
+    if (!p) {
+        set_error("bf_factor_device: NULL plan");
+        return BF_ERR_ARG;
+    }
+    if (p->factored) return bf_upload(p);
+    if (p->user_kinds_lost) {
+        set_error("bf_factor_device: plan was loaded without its callbacks");
+        return BF_ERR_STATE;
+    }
+    if (!bfi::construct_supported(p->kern.d.phase_kind)) {
+        set_error("bf_factor_device: phase kind %d has no device form (use bf_factor)", p->kern.d.phase_kind);
+        return BF_ERR_UNSUPPORTED;
+    }
+    const bf_status hs = factor_host_parts(p, "bf_factor_device");
+    if (hs != BF_OK) return hs;
     bf_status st = bfi::device_construct(p);
     if (st != BF_OK) {
         p->blocks.clear();
         return st;
     }
     p->factored = true;
+    return BF_OK;
+}
+
+bf_status bf_factor_otf(bf_plan* p)
+{
+    if (!p) {
+        set_error("bf_factor_otf: NULL plan");
+        return BF_ERR_ARG;
+    }
+    if (p->factored) {
+        set_error("bf_factor_otf: plan already factored");
+        return BF_ERR_STATE;
+    }
+    if (p->user_kinds_lost) {
+        set_error("bf_factor_otf: plan was loaded without its callbacks");
+        return BF_ERR_STATE;
+    }
+    if (!bfi::construct_supported(p->kern.d.phase_kind)) {
+        set_error("bf_factor_otf: phase kind %d has no closed form on the device", p->kern.d.phase_kind);
+        return BF_ERR_UNSUPPORTED;
+    }
+    const bf_status hs = factor_host_parts(p, "bf_factor_otf");
+    if (hs != BF_OK) return hs;
+    bf_status st = bfi::device_otf(p);
+    if (st != BF_OK) {
+        p->blocks.clear();
+        return st;
+    }
+    p->factored = true;
+    p->otf = true;
     return BF_OK;
 }
 

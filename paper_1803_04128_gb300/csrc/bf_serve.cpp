@@ -285,6 +285,10 @@ bf_status bf_server_add_operator(bf_server* s, bf_plan* plan, int* op_id)
         set_error("bf_server_add_operator: plan not factored");
         return BF_ERR_STATE;
     }
+    if (plan->otf) {
+        set_error("bf_server_add_operator: plans factored by bf_factor_otf are not served");
+        return BF_ERR_UNSUPPORTED;
+    }
     if (plan->opt.device != s->opt.device) {
         set_error("bf_server_add_operator: plan is on device %d, server on %d", plan->opt.device, s->opt.device);
         return BF_ERR_ARG;

@@ -101,6 +101,17 @@ def test_bad_arguments_raise():
         api.Plan(1024, r=20)                 # r outside the built kernels
 
 
+def test_factor_otf_refusals_before_any_device_work():
+    # a user phase has no closed form for the kernels; a factored plan is not re-factored
+    with pytest.raises(L.BFError) as e:
+        api.Plan(1024, r=10, phase_kind=L.PHASE_USER, phi=lambda x, xi: x * xi, on_the_fly=True)
+    assert e.value.status == L.BF_ERR_UNSUPPORTED
+    p = api.Plan(1024, r=10)
+    with pytest.raises(L.BFError) as e:
+        p.factor_otf()
+    assert e.value.status == L.BF_ERR_STATE
+
+
 def test_save_load_roundtrip():
     p = api.Plan(1024, r=10, amp_kind=L.AMP_SMOOTH)
     F = inputs.complex_gaussian(1024, 2, seed=4)
