@@ -497,6 +497,52 @@ def run_batched(args, w, rank, world, local):
     return 0
 
 
+def otf_side(args, w, plan, F, G, flush, stream, world, local, alu_peak, front, back):
+    """Time the on-the-fly plan of the same operator (bf_factor_otf) with the main
+    line's protocol; its result is compared with the table apply's G."""
+    import torch
+    from paper_1803_04128_gb300 import api
+    N, m = w["N"], w["m"]
+    t0 = time.perf_counter()
+    po = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
+                  on_the_fly=True)
+    t_factor = time.perf_counter() - t0
+    tune_path = os.path.join(tempfile.gettempdir(), "bf_autotune_bench_otf_%d.txt" % os.getpid())
+    mr = api.autotune(po, m, tune_path)
+    po.reserve(api.F32, m)
+    Go = torch.empty_like(F)
+    for _ in range(args.warmup):
+        flush.zero_()
+        po.apply(F, Go, api.F32)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with api.KernelTimer() as kt:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            po.apply(F, Go, api.F32)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    assert po.sync_status() == 0
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, "cuda")
+    rel = float((Go - G).norm() / G.norm())
+    io, it = po.info(), plan.info()
+    km = {k: v[1] / v[0] for k, v in kt.result.items()}
+    out = {"value": job_rate(world, N * m, args.steps, ms), "unit": UNIT, "ms_per_step": ms / args.steps,
+           "dev_bytes_f32": io["dev_bytes_f32"], "dev_bytes_f32_with_tables": it["dev_bytes_f32"],
+           "dev_bytes_f64_with_tables": it["dev_bytes_f64"], "t_factor_s": round(t_factor, 3),
+           "mr_autotuned": mr, "rel_diff_vs_table_apply": rel, "kernel_ms": km,
+           "traffic": {k: ncu_traffic(k, args.workload, m) for k in ("front_f32_otf", "back_f32_otf")}}
+    if "front_f32_otf" in km:
+        out["alu_frac_algorithmic"] = {
+            "front_f32_otf": front / (km["front_f32_otf"] * 1e-3) / 1e12 / alu_peak,
+            "back_f32_otf": back / (km["back_f32_otf"] * 1e-3) / 1e12 / alu_peak}
+        out["note"] = ("algorithmic flops of the apply (the phase evaluation is extra work) over each kernel's "
+                       "CUDA-event time, against the FP32 FMA peak")
+    po.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -510,6 +556,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--otf", action="store_true",
+                    help="time the on-the-fly plan (bf_factor_otf, FP32 only) as the main line")
+    ap.add_argument("--no-otf-side", action="store_true",
+                    help="skip the on-the-fly side measurement of FP32 workloads")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.prec and args.prec != w["prec"]:
@@ -521,6 +571,9 @@ def main():
     if args.m:
         w["m"] = args.m
         w["desc"] += " [m overridden to %d]" % args.m
+    if args.otf:
+        w["prec"] = "f32"
+        w["desc"] += " [on-the-fly plan: phases evaluated in the kernels]"
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -552,7 +605,8 @@ def main():
     prec = {"f64": api.F64, "f32": api.F32, "bf16x3": api.BF16X3}[w["prec"]]
     cdt = torch.complex128 if prec == api.F64 else torch.complex64
     t0 = time.perf_counter()
-    plan = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local)
+    plan = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
+                    on_the_fly=args.otf)
     t_factor = time.perf_counter() - t0
     # the same operator with its phase tables built on the GPU (bf_factor_device), for the record
     torch.cuda.synchronize()
@@ -581,6 +635,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
 
+    fk, bk = ("front_f32_otf", "back_f32_otf") if args.otf else ("front_f32", "back_f32")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         with api.KernelTimer() as kt:
@@ -603,11 +658,11 @@ def main():
     alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12   # TFLOP/s FP32 FMA
     roof = None
     launches = sum(n for n, _ in kt.result.values())
-    if prec == api.F32 and "front_f32" in kt.result:
-        nf, tf = kt.result["front_f32"]
-        nb, tb = kt.result["back_f32"]
+    if prec == api.F32 and fk in kt.result:
+        nf, tf = kt.result[fk]
+        nb, tb = kt.result[bk]
         nblk = w["split"] ** 2
-        dom, n_l, t_l, flops = ("front_f32", nf, tf, front) if tf >= tb else ("back_f32", nb, tb, back)
+        dom, n_l, t_l, flops = (fk, nf, tf, front) if tf >= tb else (bk, nb, tb, back)
         avg_ms = t_l / n_l
         achieved = flops / (avg_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
@@ -663,6 +718,11 @@ def main():
         e2e = {"value": job_rate(world, N * m, args.steps, 1e3 * t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
+    # the same operator factored for the on-the-fly apply (no phase tables), timed alike
+    otf = None
+    if prec == api.F32 and not args.otf and not args.no_otf_side:
+        otf = otf_side(args, w, plan, F, G, flush, stream, world, local, alu_peak, front, back)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         Gh = G.cpu().numpy()
@@ -685,6 +745,8 @@ def main():
                 "data": "synthetic (seeded complex Gaussian F; analytic kernel)", "config": cfg,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary()}
+        if otf is not None:
+            line["on_the_fly"] = otf
         print(json.dumps(line))
     plan.close()
     if world > 1:
