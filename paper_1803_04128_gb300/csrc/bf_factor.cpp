@@ -225,6 +225,15 @@ bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0
                 M((int64_t)ii, jj) = k.amplitude(row0 + I[ii], col0 + J[(size_t)jj]);
         return M;
     };
+    // adjoint(entries(I, J)) built directly, in parallel over the rows I
+    auto entries_adj = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J) {
+        CMat M((int64_t)J.size(), (int64_t)I.size());
+#pragma omp parallel for schedule(static)
+        for (int64_t ii = 0; ii < (int64_t)I.size(); ++ii)
+            for (size_t jj = 0; jj < J.size(); ++jj)
+                M((int64_t)jj, ii) = std::conj(k.amplitude(row0 + I[(size_t)ii], col0 + J[jj]));
+        return M;
+    };
     std::vector<int64_t> all((size_t)N);
     for (int64_t i = 0; i < N; ++i) all[(size_t)i] = i;
     std::vector<int64_t> pi_col, pi_row, piv;
@@ -238,13 +247,13 @@ bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0
         std::sort(pi_col.begin(), pi_col.end());
         // rq random columns + important columns; pivoted LQ of K(:, J) picks rows
         auto J = sample_union(rng, N, rq, pi_col);
-        kr = pivoted_qr(adjoint(entries(all, J)), r, qr_tol, Q, piv);
+        kr = pivoted_qr(entries_adj(all, J), r, qr_tol, Q, piv);
         pi_row.assign(piv.begin(), piv.begin() + std::max(kr, 1));
         std::sort(pi_row.begin(), pi_row.end());
     }
     CMat Qc, Qr;
     int kc = pivoted_qr(entries(all, pi_col), r, qr_tol, Qc, piv);
-    int kr = pivoted_qr(adjoint(entries(pi_row, all)), r, qr_tol, Qr, piv);
+    int kr = pivoted_qr(entries_adj(pi_row, all), r, qr_tol, Qr, piv);
     if (kc == 0 || kr == 0) {  // zero amplitude
         ra = 0;
         a.clear();

@@ -105,7 +105,7 @@ struct CMat {
 // Householder QR with column pivoting, stopped after kmax steps or when the
 // largest remaining column norm falls below tol * (first pivot norm).
 // Returns the rank k; Q is m x k (orthonormal columns), piv the full pivot order.
-int pivoted_qr(const CMat& A, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv);
+int pivoted_qr(CMat A, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv);
 // One-sided Jacobi SVD of a small matrix: A = U diag(S) V^*.
 void jacobi_svd(const CMat& A, CMat& U, std::vector<double>& S, CMat& V);
 CMat pinv(const CMat& A, double rcond);

@@ -23,8 +23,13 @@ CMat matmul(const CMat& A, const CMat& B)
 CMat adjoint(const CMat& A)
 {
     CMat T(A.n, A.m);
-    for (int64_t j = 0; j < A.n; ++j)
-        for (int64_t i = 0; i < A.m; ++i) T(j, i) = std::conj(A(i, j));
+    // blocks of 256 rows of A (columns of T) in parallel, so both sides stay in cache
+#pragma omp parallel for schedule(static) if (A.m * A.n > (1 << 20))
+    for (int64_t i0 = 0; i0 < A.m; i0 += 256) {
+        const int64_t i1 = std::min(A.m, i0 + 256);
+        for (int64_t j = 0; j < A.n; ++j)
+            for (int64_t i = i0; i < i1; ++i) T(j, i) = std::conj(A(i, j));
+    }
     return T;
 }
 
@@ -60,10 +65,9 @@ static void col_axpy(const std::vector<cd>& v, CMat& X, int64_t j, int64_t i0, i
     for (int64_t i = i0; i < m; ++i) X(i, j) -= v[(size_t)(i - i0)] * s;
 }
 
-int pivoted_qr(const CMat& A, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv)
+int pivoted_qr(CMat R, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv)
 {
-    const int64_t m = A.m, n = A.n;
-    CMat R = A;
+    const int64_t m = R.m, n = R.n;  // R starts as the input matrix (moved in by callers with temporaries)
     piv.resize((size_t)n);
     std::vector<double> nrm((size_t)n);
     const bool wide = n > 4096;  // many columns: split the column loops over threads
