@@ -43,6 +43,9 @@ WORKLOADS = {
                    desc="serving: Poisson arrivals (mean 2000 req/s) against 4 resident operators N=2^14,2^16,2^18,2^20 "
                         "of the fio2 kernel, m uniform in {1,4,16,64}, host buffers, continuous batching on 4 slots, "
                         "complex FP32; compared with the plain per-request FP64 form; latency also at 100 req/s"),
+    "fio_big": dict(N=1 << 22, m=16, phase=1, amp=1, eps=1e-6, prec="f32", split=1, otf=True,
+                    desc="1D FIO as fio2 at N=2^22, m=16, on-the-fly plan (no phase tables; FP32+FP64 tables "
+                         "would take ~42 GB), complex FP32 apply, eps=1e-6"),
     "fio3": dict(N=262144, m=256, phase=2, amp=1, eps=1e-4, prec="bf16x3", split=2,
                  desc="piecewise FIO (jump at x=1/2), N=262144 as four N/2 sub-BFs, m=256, alpha as fio2, "
                       "split-BF16 tensor-core apply (hi/lo operands, FP32 accumulation), BF eps=1e-4 (r=8)"),
@@ -214,7 +217,8 @@ def cpu_oracle_rate(w, F, G_gpu, budget_s, max_rows=None):
     from paper_1803_04128_gb300 import inputs
     N, m = w["N"], w["m"]
     kind = w["phase"]
-    probe = inputs.sample_rows(N, min(N, 64), seed=11)   # enough rows to keep every host thread busy
+    # enough rows to keep every host thread busy, fewer for very long rows
+    probe = inputs.sample_rows(N, int(min(N, 64, max(8, (1 << 28) // (N * m)))), seed=11)
     t0 = time.perf_counter()
     od.direct(kind, N, F, probe, amp=w["amp"])
     per_row = (time.perf_counter() - t0) / probe.size
@@ -573,9 +577,10 @@ def main():
     if args.m:
         w["m"] = args.m
         w["desc"] += " [m overridden to %d]" % args.m
-    if args.otf:
+    if args.otf and not w.get("otf"):
         w["prec"] = "f32"
         w["desc"] += " [on-the-fly plan: phases evaluated in the kernels]"
+    args.otf = args.otf or bool(w.get("otf"))
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -611,12 +616,14 @@ def main():
                     on_the_fly=args.otf)
     t_factor = time.perf_counter() - t0
     # the same operator with its phase tables built on the GPU (bf_factor_device), for the record
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
-             factor_on_device=True).close()
-    torch.cuda.synchronize()
-    t_factor_dev = time.perf_counter() - t0
+    t_factor_dev = None
+    if not w.get("otf"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
+                 factor_on_device=True).close()
+        torch.cuda.synchronize()
+        t_factor_dev = time.perf_counter() - t0
     info = plan.info()
     mr_tuned = None
     if prec == api.F32:
@@ -735,7 +742,10 @@ def main():
     if rank == 0:
         cfg = {"workload": w["desc"], "N": N, "m": m, "r": info["r"], "r_alpha": info["r_alpha"],
                "eps": w["eps"], "L": info["L"], "split": w["split"], "l2": "flushed (512 MB write) between timed steps",
-               "t_factor_s": round(t_factor, 3), "t_factor_device_s": round(t_factor_dev, 3),
+               "t_factor_s": round(t_factor, 3),
+               "t_factor_device_s": None if t_factor_dev is None else round(t_factor_dev, 3),
+               "plan": "on-the-fly (bf_factor_otf)" if args.otf else "phase tables",
+               "dev_bytes_f32": plan.info()["dev_bytes_f32"], "dev_bytes_f64": plan.info()["dev_bytes_f64"],
                "mr_autotuned": mr_tuned,
                "parallelism": "replicas" if world > 1 else "single GPU",
                "hbm_frac_of_measured": hbm_frac, "algorithmic_bytes_per_step": bytes_apply,

@@ -125,8 +125,8 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
     for (int i = 0; i < n; ++i) {
         const DevBlock& B = in[i].plan->dev->blocks[0];
         ws_off[(size_t)i] = ws_total;
-        ws_total += (std::max(fused_f32_ws_bytes(B.g, in[i].m, in[i].plan->mr_hint(in[i].m)),
-                              fused_f32_ws_bytes(B.g, in[i].m, 0)) + 255) & ~(size_t)255;
+        ws_total += (std::max(fused_f32_ws_bytes(B.g, in[i].m, in[i].plan->mr_hint(in[i].m), false),
+                              fused_f32_ws_bytes(B.g, in[i].m, 0, false)) + 255) & ~(size_t)255;
     }
     if ((e = cudaMalloc(&b->ws, std::max<size_t>(ws_total, 256))) != cudaSuccess) {
         free_batch(b);

@@ -112,8 +112,10 @@ struct FusedCfg {
     int tpc_b;    // T_Omega chunks a back CTA processes together
 };
 // mr_hint: column-slice width chosen by the autotuner (0 = built-in rule)
-FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint = 0);
-size_t fused_f32_ws_bytes(const Geo& g, int64_t m, int mr_hint = 0);
+// split: the plain apply's level passes (long H or G ranges in several passes); false: one pass per
+// side, as the batched and sharded applies run them
+FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint = 0, bool split = true);
+size_t fused_f32_ws_bytes(const Geo& g, int64_t m, int mr_hint = 0, bool split = true);
 cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta,
                              float2* ws, cudaStream_t st, int mr_hint = 0);
 bool fused_f32_supported(int r);

@@ -284,6 +284,53 @@ __device__ __forceinline__ void g_item(float2* x0, float2* x1, int CTp, const fl
     }
 }
 
+// Switch blocks (step 4 of Algorithm 4.1) of the T = 2^K pairs (x-node (p << K) + lp at
+// level h, T_Omega node c0 at level L-h), lp < T, evaluated into Ss [T][R][R]:
+// entry (lp, t, s) = e(Phi(x_t, xi_s) - Phi(c_A, xi_s) - Phi(x_t, c_B)); one (lp, t) row per
+// item, so the rows x_t and c_A are read once.
+template <int R>
+__device__ __forceinline__ void otf_switch_fill(const OtfPhase& ph, const Geo& g, int p, int K, int c0, float2* Ss,
+                                                int tid)
+{
+    const int T = 1 << K, nah = (int)(g.N >> g.h), nbh = (int)(g.N >> (g.L - g.h));
+    const int cB = centre_of(c0 * nbh, nbh);
+    const int* gA = otf_grid(ph, nah);
+    const int* gB = otf_grid(ph, nbh);
+    for (int e = tid; e < T * R; e += kThreads) {
+        const int lp = e / R, t = e - lp * R;
+        const int a = (p << K) + lp, x = a * nah + __ldg(gA + t), ca = centre_of(a * nah, nah);
+        const OtfRow wx = otf_row(ph, x), wa = otf_row(ph, ca);
+        const unsigned base = (wx.R - wa.R) - otf_turns(ph, x, cB);
+        const unsigned long long dK = wx.K - wa.K;
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            const int xi = otf_xi(ph, c0 * nbh + __ldg(gB + s));
+            Ss[e * R + s] = otf_exp(base + otf_ixi(ph, x - ca, xi) + otf_kmul(dK, abs(xi)));
+        }
+    }
+}
+
+// Switch on one (pair, column): wo[t] = sum_s S[t][s] xs[s] (strides CTp); S row-major
+// [R][R] in shared memory (FROM_SMEM) or global memory.
+template <int R, bool FROM_SMEM>
+__device__ __forceinline__ void switch_item(const float2* xs, int CTp, const float4* Sp, float2* wo)
+{
+    float2 mu[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) mu[s] = xs[s * CTp];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int s2 = 0; s2 < R / 2; ++s2) {
+            const float4 sv = FROM_SMEM ? Sp[t * (R / 2) + s2] : __ldg(Sp + t * (R / 2) + s2);
+            cfmaf(acc, make_float2(sv.x, sv.y), mu[2 * s2]);
+            cfmaf(acc, make_float2(sv.z, sv.w), mu[2 * s2 + 1]);
+        }
+        wo[t * CTp] = acc;
+    }
+}
+
 // ------------------------------------------------------------------ front --
 // Shared memory: Mv^T [NV][R4] | MH^T [kH][2R][R4] | per tile u < tpc:
 // X [T][R][CTp] | EH double buffer [2][T][2][R] | EV [T*NV] | F rows [T*NV][mr]
@@ -300,13 +347,13 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
 {
     constexpr int R4 = Pad4<R>::v;
     const Geo& g = A.g;
-    const int K = g.kH, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra, tpc = A.tpc;
+    const int K = A.K, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra, tpc = A.tpc;
     const int nP = 1 << g.l1;                        // x-nodes at level l1
     const int64_t nBh = (int64_t)1 << (g.L - g.h);   // T_Omega nodes at level L-h
     const int64_t N = g.N, P = g.P, m = A.m;
     const int L = g.L, l1 = g.l1;
     const size_t tile_f2 = (size_t)T * R * CTp + (size_t)2 * T * 2 * R + (size_t)T * NV + (size_t)T * NV * mr +
-                           (OTF ? (size_t)T * R * R : 0);
+                           (OTF && A.last ? (size_t)T * R * R : 0);
 
     float* MvTs = reinterpret_cast<float*>(smem_raw);                      // [NV][R4]
     float* MHTs = MvTs + NV * R4;                                          // [K][2R][R4]
@@ -373,25 +420,7 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
             // EV entry xi = e(Phi(c_A, xi)), A = x-node p at level l1 (Eq. 1)
             const int na = (int)(N >> l1), cA = centre_of((int)p_of(u) * na, na), xb = (int)xi_base;
             for (int e = tid; e < T * NV; e += kThreads) EVs[e] = otf_exp(otf_turns(A.ph, cA, xb + e));
-            // switch entry (lp, t, s) = e(Phi(x_t, xi_s) - Phi(c_A, xi_s) - Phi(x_t, c_B)), pair (A, B)
-            // at level h; one (lp, t) row per item, so the rows x_t and c_A are read once
-            const int nah = (int)(N >> g.h), nbh = (int)(N >> (L - g.h)), c0 = (int)c0_of(u);
-            const int cB = centre_of(c0 * nbh, nbh);
-            const int* gA = otf_grid(A.ph, nah);
-            const int* gB = otf_grid(A.ph, nbh);
-            float2* Ss = Sof(u);
-            for (int e = tid; e < T * R; e += kThreads) {
-                const int lp = e / R, t = e - lp * R;
-                const int a = ((int)p_of(u) << K) + lp, x = a * nah + __ldg(gA + t), ca = centre_of(a * nah, nah);
-                const OtfRow wx = otf_row(A.ph, x), wa = otf_row(A.ph, ca);
-                const unsigned base = (wx.R - wa.R) - otf_turns(A.ph, x, cB);
-                const unsigned long long dK = wx.K - wa.K;
-#pragma unroll
-                for (int s = 0; s < R; ++s) {
-                    const int xi = otf_xi(A.ph, c0 * nbh + __ldg(gB + s));
-                    Ss[e * R + s] = otf_exp(base + otf_ixi(A.ph, x - ca, xi) + otf_kmul(dK, abs(xi)));
-                }
-            }
+            if (A.last) otf_switch_fill<R>(A.ph, g, (int)p_of(u), K, (int)c0_of(u), Sof(u), tid);
         } else {
             const float2* ev = A.EV + p_of(u) * N + xi_base;
             for (int e = tid; e < T * NV / 2; e += kThreads) cp16(EVs + 2 * e, ev + 2 * e);
@@ -486,28 +515,24 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
         }
     }
 
-    // ---- switch (step 4) and write-out of the switch-level coefficients; item (u, lp, col)
+    // ---- switch (step 4) and write-out of the switch-level coefficients; item (u, lp, col).
+    // Without the switch (the H levels continue in a middle pass) the level-(l1 + K)
+    // coefficients are written as they are.
     for (int it = tid; it < tpc * T * CTp; it += kThreads) {
         const int col = it & (CTp - 1), lp = (it >> lct) & (T - 1), u = it >> (lct + K);
         const int slot = (int)brev((unsigned)lp, K);
         const float2* xs = Xof(u) + (size_t)slot * R * CTp + col;
-        float2 mu[R];
+        if (A.last) {
+            const int64_t q = ((p_of(u) << K) + lp) * nBh + c0_of(u);
+            float2* wo = A.W + (size_t)w_pair(A.wl, (p_of(u) << K) + lp, c0_of(u), slice_of(u)) * R * CTp + col;
+            if constexpr (OTF)
+                switch_item<R, true>(xs, CTp, reinterpret_cast<const float4*>(Sof(u) + (size_t)lp * R * R), wo);
+            else
+                switch_item<R, false>(xs, CTp, reinterpret_cast<const float4*>(A.S + q * R * R), wo);
+        } else {
+            float2* wo = A.Wo + (size_t)w_pair(A.wlo, (p_of(u) << K) + lp, c0_of(u), slice_of(u)) * R * CTp + col;
 #pragma unroll
-        for (int s = 0; s < R; ++s) mu[s] = xs[s * CTp];
-        const int64_t q = ((p_of(u) << K) + lp) * nBh + c0_of(u);
-        const float4* Sp = OTF ? reinterpret_cast<const float4*>(Sof(u) + (size_t)lp * R * R)
-                               : reinterpret_cast<const float4*>(A.S + q * R * R);
-        float2* wo = A.W + (size_t)w_pair(A.wl, (p_of(u) << K) + lp, c0_of(u), slice_of(u)) * R * CTp + col;
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int s2 = 0; s2 < R / 2; ++s2) {
-                const float4 sv = OTF ? Sp[t * (R / 2) + s2] : __ldg(Sp + t * (R / 2) + s2);
-                cfmaf(acc, make_float2(sv.x, sv.y), mu[2 * s2]);
-                cfmaf(acc, make_float2(sv.z, sv.w), mu[2 * s2 + 1]);
-            }
-            wo[t * CTp] = acc;
+            for (int s = 0; s < R; ++s) wo[s * CTp] = xs[s * CTp];
         }
     }
 }
@@ -524,13 +549,14 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
 {
     constexpr int R4 = Pad4<R>::v;
     const Geo& g = A.g;
-    const int K = g.kG, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra, tpc = A.tpc;
+    const int K = A.K, T = 1 << K, CTp = A.CTp, lct = A.lct, mr = A.mr, lmr = A.lmr, ra = g.ra, tpc = A.tpc;
     const int slice = (int)(work % A.nslice);
-    const int64_t pp = A.pp_lo + work / A.nslice;  // x-node at level h
+    const int64_t pp = A.pp_lo + work / A.nslice;  // x-node at level lb
     const int nC = 1 << g.l1;                      // chunks c0' (= T_Omega nodes at level l1)
     const int XN = T * NU;                         // output points of this CTA
     const int64_t N = g.N, P = g.P;
-    const int L = g.L, h = g.h;
+    const int L = g.L, h = A.lb;  // the pass starts at level lb (h unless the G levels are split)
+    const int e0 = A.lb - g.h;    // index of level lb + 1 in the G matrix and phase stacks
     const size_t chunk_f2 = (size_t)T * R * CTp + (size_t)2 * T * 2 * R + XN;
 
     float* MGTs = reinterpret_cast<float*>(smem_raw);                 // [K][2][R][R4]
@@ -563,7 +589,7 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
             return;
         }
         const int64_t nBl = (int64_t)1 << (L - h - j);
-        const float2* fg = FGg + (size_t)(j - 1) * P * 2 * R;
+        const float2* fg = FGg + (size_t)(e0 + j - 1) * P * 2 * R;
         for (int u = 0; u < tpc; ++u) {
             float2* dst = FGof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
             for (int e = tid; e < T * R; e += kThreads) {
@@ -574,7 +600,7 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
             }
         }
     };
-    stage_matrix(MGTs, A.MGT, K * 2 * R, R, R4, tid);
+    stage_matrix(MGTs, A.MGT + (size_t)e0 * 2 * R * R, K * 2 * R, R, R4, tid);
     stage_matrix(MUs, A.MU, NU, R, R4, tid);
     for (int e = tid; e < XN * mr; e += kThreads) acc[e] = make_float2(0.f, 0.f);
 
@@ -692,6 +718,139 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
     }
 }
 
+// -------------------------------------------------------------------- mid --
+// A middle pass of a split level range (MidArgs): K levels of H (GK = 0, Eq. 2) or
+// G (GK = 1, Eq. 3) over tiles of T = 2^K pairs read from and written to HBM.
+// Shared memory: M^T [K][2R][R4] | per tile u < tpc: X [T][R][CTp] | phase double
+// buffer [2][T][2][R] | (OTF, last H pass) switch blocks [T][R][R].  The in-place slot
+// order, the staging one level ahead and the level items are those of the front and
+// back tiles, so each tile's arithmetic is the same as there.
+template <int R, int GK, bool OTF = false>
+__device__ __forceinline__ void mid_tile(const MidArgs& A, int64_t work, unsigned char* smem_raw)
+{
+    constexpr int R4 = Pad4<R>::v;
+    const Geo& g = A.g;
+    const int K = A.K, T = 1 << K, CTp = A.CTp, lct = A.lct, tpc = A.tpc, la = A.la, L = g.L;
+    const int64_t N = g.N, P = g.P;
+    const bool last = !GK && A.last;
+    const size_t tile_f2 = (size_t)T * R * CTp + (size_t)2 * T * 2 * R + (OTF && last ? (size_t)T * R * R : 0);
+
+    float* MTs = reinterpret_cast<float*>(smem_raw);                      // [K][2R][R4]
+    float2* tiles = reinterpret_cast<float2*>(MTs + (size_t)K * 2 * R * R4);
+    auto Xof = [&](int u) { return tiles + (size_t)u * tile_f2; };        // [T][R][CTp]
+    auto Eof = [&](int u) { return Xof(u) + (size_t)T * R * CTp; };       // [2][T][2][R]
+    auto Sof = [&](int u) { return Eof(u) + (size_t)2 * T * 2 * R; };     // [T][R][R]
+    // tile u: work index work * tpc + u -> (column slice, x-node p at level la, chunk c)
+    __shared__ int s_p[16], s_c[16], s_slice[16];
+    const int tid = threadIdx.x;
+    if (tid < tpc) {
+        const int64_t idx = work * tpc + tid, tile = idx / A.nslice;
+        s_slice[tid] = (int)(idx - tile * A.nslice);
+        s_p[tid] = (int)(tile & ((1ll << la) - 1));
+        s_c[tid] = (int)(tile >> la);
+    }
+    __syncthreads();
+
+    auto stage = [&](int j) {  // phases of level la + j into buffer (j - 1) & 1 of every tile
+        const int l = la + j;
+        for (int u = 0; u < tpc; ++u) {
+            const int p = s_p[u], c = s_c[u];
+            float2* dst = Eof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
+            if constexpr (OTF) {
+                const int na = (int)(N >> l), nb = (int)(N >> (L - l));
+                const int* gr = otf_grid(A.ph, GK ? na : nb / 2);
+                for (int e = tid; e < T * 2 * R; e += kThreads) {
+                    const int lp = e / (2 * R), cs = e - lp * 2 * R, ch = cs >= R, s = cs - ch * R;
+                    const int ap = (p << j) + (lp >> (K - j));
+                    const int bp = (c << (K - j)) + (lp & ((1 << (K - j)) - 1));
+                    if constexpr (GK) {  // FG entry (lp, ch, t) = e(Phi(x_t, c_C) - Phi(x_t, c_B))
+                        const int x = ap * na + __ldg(gr + s);
+                        const int cB = centre_of(bp * nb, nb), cC = centre_of(bp * nb + ch * (nb / 2), nb / 2);
+                        dst[e] = otf_exp(otf_coldiff(A.ph, x, cC, cB));
+                    } else {             // EH entry (lp, ch, s) = e(Phi(c_A, xi_s) - Phi(c_P, xi_s))
+                        const int xi = bp * nb + ch * (nb / 2) + __ldg(gr + s);
+                        const int cA = centre_of(ap * na, na), cP = centre_of((ap >> 1) * 2 * na, 2 * na);
+                        dst[e] = otf_exp(otf_rowdiff(A.ph, cA, cP, xi));
+                    }
+                }
+            } else {
+                const int64_t nBl = (int64_t)1 << (L - l);
+                const float2* tab = A.E + (size_t)(A.e0 + j - 1) * P * 2 * R;
+                for (int e = tid; e < T * R; e += kThreads) {  // R 16-byte chunks per pair
+                    const int lp = e / R, w = e - lp * R;
+                    const int64_t ap = ((int64_t)p << j) + (lp >> (K - j));
+                    const int64_t bp = ((int64_t)c << (K - j)) + (lp & ((1 << (K - j)) - 1));
+                    cp16(dst + (size_t)lp * 2 * R + 2 * w, tab + (ap * nBl + bp) * 2 * R + 2 * w);
+                }
+            }
+        }
+    };
+    // group 0: matrices, the tiles' pairs, level-1 phases; group 1: level-2 phases
+    stage_matrix(MTs, A.MT + (size_t)A.e0 * 2 * R * R, K * 2 * R, R, R4, tid);
+    for (int u = 0; u < tpc; ++u) {  // pairs (p, c T + i), i < T: one contiguous block of T*R*CTp
+        const float2* src = A.Wi + (size_t)w_pair(A.wli, s_p[u], (int64_t)s_c[u] * T, s_slice[u]) * R * CTp;
+        float2* X = Xof(u);
+        for (int e = tid; e < T * R * CTp / 2; e += kThreads) cp16(X + 2 * e, src + 2 * e);
+        if constexpr (OTF) {
+            if (last) otf_switch_fill<R>(A.ph, g, s_p[u], K, s_c[u], Sof(u), tid);
+        }
+    }
+    stage(1);
+    cp_commit();
+    if (K >= 2) {
+        stage(2);
+        cp_commit();
+    }
+    if (K >= 2) cp_wait1(); else cp_wait0();
+    __syncthreads();
+
+    for (int j = 1; j <= K; ++j) {
+        if (j > 1) {
+            if (j < K) cp_wait1(); else cp_wait0();
+            __syncthreads();
+        }
+        const int kj = K - j, half = 1 << kj;
+        const float* Mj = MTs + (size_t)(j - 1) * 2 * R * R4;
+        for (int it = tid; it < tpc * (T / 2) * CTp; it += kThreads) {
+            const int col = it & (CTp - 1), grp = (it >> lct) & (T / 2 - 1), u = it >> (lct + K - 1);
+            const int a = grp >> kj, bp = grp & (half - 1);
+            const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
+            float2* x0 = Xof(u) + (size_t)base * R * CTp + col;
+            float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
+            const float2* Eb = Eof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
+            const float2* E0 = Eb + (size_t)((2 * a) * half + bp) * 2 * R;
+            const float2* E1 = Eb + (size_t)((2 * a + 1) * half + bp) * 2 * R;
+            if constexpr (GK) g_item<R>(x0, x1, CTp, E0, E1, Mj);
+            else h_item<R>(x0, x1, CTp, E0, E1, Mj);
+        }
+        __syncthreads();
+        if (j + 2 <= K) {
+            stage(j + 2);
+            cp_commit();
+        }
+    }
+
+    // ---- write-out at level la + K (after the switch if the pass reaches h); item (u, lp, col)
+    for (int it = tid; it < tpc * T * CTp; it += kThreads) {
+        const int col = it & (CTp - 1), lp = (it >> lct) & (T - 1), u = it >> (lct + K);
+        const int slot = (int)brev((unsigned)lp, K);
+        const float2* xs = Xof(u) + (size_t)slot * R * CTp + col;
+        const int64_t a = ((int64_t)s_p[u] << K) + lp;
+        float2* wo = A.Wo + (size_t)w_pair(A.wlo, a, s_c[u], s_slice[u]) * R * CTp + col;
+        if (last) {
+            if constexpr (OTF) {
+                switch_item<R, true>(xs, CTp, reinterpret_cast<const float4*>(Sof(u) + (size_t)lp * R * R), wo);
+            } else {
+                const int64_t q = a * ((int64_t)1 << (L - g.h)) + s_c[u];
+                switch_item<R, false>(xs, CTp, reinterpret_cast<const float4*>(A.S + q * R * R), wo);
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < R; ++s) wo[s * CTp] = xs[s * CTp];
+        }
+    }
+}
+
 inline int ilog2(int v)
 {
     int l = 0;
@@ -699,19 +858,30 @@ inline int ilog2(int v)
     return l;
 }
 
-inline size_t front_smem(const Geo& g, int R, int NV, int CTp, int mr, int tpc)
+// shared memory of a front pass of K H levels (last: it reaches h and applies the switch)
+inline size_t front_smem(const Geo& g, int K, bool last, int R, int NV, int CTp, int mr, int tpc)
 {
-    const size_t T = (size_t)1 << g.kH, R4 = (R + 3) & ~3;
-    return sizeof(float2) * (size_t)tpc * (T * R * CTp + 2 * T * 2 * R + T * NV + T * NV * mr + (g.otf ? T * R * R : 0)) +
-           sizeof(float) * ((size_t)NV * R4 + (size_t)g.kH * 2 * R * R4);
+    const size_t T = (size_t)1 << K, R4 = (R + 3) & ~3;
+    return sizeof(float2) * (size_t)tpc *
+               (T * R * CTp + 2 * T * 2 * R + T * NV + T * NV * mr + (g.otf && last ? T * R * R : 0)) +
+           sizeof(float) * ((size_t)NV * R4 + (size_t)K * 2 * R * R4);
 }
 
-inline size_t back_smem(const Geo& g, int R, int NU, int CTp, int mr, int tpc)
+// shared memory of a back pass of K G levels
+inline size_t back_smem(const Geo& g, int K, int R, int NU, int CTp, int mr, int tpc)
 {
-    const size_t T = (size_t)1 << g.kG, R4 = (R + 3) & ~3;
+    const size_t T = (size_t)1 << K, R4 = (R + 3) & ~3;
     const size_t XN = T * NU;
     return sizeof(float2) * (XN * mr + (size_t)tpc * (T * R * CTp + 2 * T * 2 * R + XN)) +
-           sizeof(float) * ((size_t)g.kG * 2 * R * R4 + (size_t)NU * R4);
+           sizeof(float) * ((size_t)K * 2 * R * R4 + (size_t)NU * R4);
+}
+
+// shared memory of a middle pass of K levels (last: an H pass that reaches h)
+inline size_t mid_smem(const Geo& g, int K, bool last, int R, int CTp, int tpc)
+{
+    const size_t T = (size_t)1 << K, R4 = (R + 3) & ~3;
+    return sizeof(float2) * (size_t)tpc * (T * R * CTp + 2 * T * 2 * R + (g.otf && last ? T * R * R : 0)) +
+           sizeof(float) * ((size_t)K * 2 * R * R4);
 }
 
 template <int R>

@@ -35,6 +35,10 @@ struct FrontArgs {
     int64_t c0_lo;     // first T_Omega node (level L-h) of this shard's tiles
     int64_t xi_lo;     // F holds rows xi_lo ..: row xi at F + (xi - xi_lo) * m
     OtfPhase ph;       // g.otf = 1: phases evaluated in the kernel (EV, EH, S unused)
+    int K;             // H levels of this pass, l1+1 .. l1+K (tiles of 2^K pairs): kH unless split
+    int last;          // 1: the pass reaches level h: apply the switch and write W (layout wl)
+    float2* Wo;        // last = 0: the coefficients at level l1 + K, layout wlo
+    WLayout wlo;
 };
 
 struct BackArgs {
@@ -54,6 +58,31 @@ struct BackArgs {
     float2* G;         // [N][m]
     int beta;
     OtfPhase ph;       // g.otf = 1: phases evaluated in the kernel (FG, EU unused)
+    int K;             // G levels of this pass, lb+1 .. lb+K = L-l1: kG unless split
+    int lb;            // level of the input pairs in W (layout wl): h unless split
+};
+
+// A middle pass of a split level range: tiles of 2^K pairs read at level la
+// (layout wli), K levels of H (Eq. 2) or G (Eq. 3) applied in shared memory,
+// written at level la + K (layout wlo); an H pass that reaches level h applies
+// the switch first.  A tile is (p: x-node at level la, c: chunk of 2^K
+// consecutive T_Omega nodes at level L-la, column slice), as in the front.
+struct MidArgs {
+    Geo g;
+    int mr, lmr, CTp, lct, nslice;
+    int tpc;           // tiles per CTA
+    int gkind;         // 0: H levels, 1: G levels
+    int la, K;
+    int last;          // H only: la + K = h
+    const float2* Wi;  // input pairs, layout wli
+    WLayout wli;
+    float2* Wo;        // output pairs, layout wlo
+    WLayout wlo;
+    const float* MT;   // MH^T [kH][2R][R] or MG^T [kG][2][R][R] (all levels of that kind)
+    const float2* E;   // EH or FG [k][P][2][R] (null with g.otf)
+    int e0;            // index of level la + 1 in MT and E
+    const float2* S;   // switch blocks [P][R][R] (last; null with g.otf)
+    OtfPhase ph;
 };
 
 // One operator of a batched launch: its front and back argument blocks and work counts.
@@ -79,6 +108,7 @@ struct BatchLaunch {
     int grid = 0;
 };
 
+// one front and one back pass over all kH and kG levels (the batched and sharded applies)
 bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int mr_hint,
                      FrontArgs* fa, BackArgs* ba, size_t* sf, size_t* sb, int64_t* nfront, int64_t* nback);
 // one of the two fused FP32 kernels with prepared arguments (nblocks CTAs)
@@ -87,6 +117,9 @@ cudaError_t launch_f32_back(int r, const BackArgs& ba, size_t smem, int64_t nblo
 // the same with the phases evaluated in the kernel (bf_kernels_otf.cu; args with g.otf = 1)
 cudaError_t launch_part_otf(int r, const FrontArgs* fa, const BackArgs* ba, size_t smem, int64_t nblocks,
                             cudaStream_t st);
+// one middle pass (table phases or, with g.otf, evaluated ones)
+cudaError_t launch_mid(int r, const MidArgs& ma, size_t smem, int64_t nblocks, cudaStream_t st);
+cudaError_t launch_mid_otf(int r, const MidArgs& ma, size_t smem, int64_t nblocks, cudaStream_t st);
 // set_attr: only set the kernel's shared-memory limit to bl.smem (no launch);
 // grid_out != NULL: only compute the persistent grid (occupancy x SMs) for bl.smem;
 // otherwise launch (bl.grid CTAs).

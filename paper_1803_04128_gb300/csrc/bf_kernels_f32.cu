@@ -3,6 +3,7 @@
 // kernel; configuration and launchers.  The tile bodies are in bf_f32_tile.h.
 #include <algorithm>
 #include <cstdio>
+#include <vector>
 
 #include "bf_f32_tile.h"
 
@@ -138,15 +139,67 @@ cudaError_t batch_launch_r(const BatchLaunch& bl, cudaStream_t st, bool set_attr
 
 bool fused_f32_supported(int r) { return r == 6 || r == 8 || r == 10 || r == 12 || r == 14 || r == 16; }
 
-FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint)
+namespace {
+
+// Level passes of the plain apply.  A tile of 2^k pairs closes k levels; beyond
+// kSplitAbove levels the shared memory of one tile leaves too few columns per tile,
+// so the plain apply splits the kH H levels and the kG G levels into passes of at
+// most kPassMax levels (as even as possible), linked through HBM workspaces.  The
+// batched and sharded applies keep one pass per side.
+constexpr int kSplitAbove = 5, kPassMax = 4;
+
+std::vector<int> split_levels(int k, bool split)
 {
-    const int Tmax = 1 << (g.kG > g.kH ? g.kG : g.kH);
+    if (!split || k <= kSplitAbove) return {k};
+    const int n = (k + kPassMax - 1) / kPassMax, base = k / n, extra = k % n;
+    std::vector<int> v;
+    for (int i = 0; i < n; ++i) v.push_back(base + (i < extra ? 1 : 0));
+    return v;
+}
+
+struct Passes {
+    std::vector<int> hs;  // H pass sizes in level order; hs[0] includes V, the last one the switch
+    std::vector<int> gs;  // G pass sizes in level order; the last one includes U
+    bool split() const { return hs.size() > 1 || gs.size() > 1; }
+    int kmax() const
+    {
+        int k = 0;
+        for (int v : hs) k = std::max(k, v);
+        for (int v : gs) k = std::max(k, v);
+        return k;
+    }
+};
+
+Passes passes_of(const Geo& g, bool split) { return Passes{split_levels(g.kH, split), split_levels(g.kG, split)}; }
+
+// largest shared memory of any pass for (mr, CTp) with one tile per CTA
+size_t passes_smem(const Geo& g, const Passes& ps, int NV, int CTp, int mr)
+{
+    const int R = g.r;
+    size_t s = std::max(front_smem(g, ps.hs[0], ps.hs.size() == 1, R, NV, CTp, mr, 1),
+                        back_smem(g, ps.gs.back(), R, NV, CTp, mr, 1));
+    for (size_t i = 1; i < ps.hs.size(); ++i) s = std::max(s, mid_smem(g, ps.hs[i], i + 1 == ps.hs.size(), R, CTp, 1));
+    for (size_t i = 0; i + 1 < ps.gs.size(); ++i) s = std::max(s, mid_smem(g, ps.gs[i], false, R, CTp, 1));
+    return s;
+}
+
+// tiles per CTA of a pass of k levels with `tiles` tiles per column slice: up to one
+// (tile, group, column) item per thread and level, two CTAs per SM
+template <typename SmemFn>
+int tiles_per_cta(int k, int CTp, int64_t tiles, SmemFn smem)
+{
+    const int items = std::max(1, (1 << k) / 2) * CTp;
+    int tpc = 1;
+    while (tpc < 16 && 2 * tpc <= tiles && 2 * tpc * items <= kThreads && smem(2 * tpc) <= 113 * 1024) tpc *= 2;
+    return tpc;
+}
+
+FusedCfg config_of(const Geo& g, int64_t m, int mr_hint, const Passes& ps)
+{
+    const int Tmax = 1 << ps.kmax();
     const int ra = g.ra > 0 ? g.ra : 1;
     const int NV = g.nv;
-    auto smem = [&](int mr) {
-        const int CTp = 1 << ilog2(ra * mr);
-        return std::max(front_smem(g, g.r, NV, CTp, mr, 1), back_smem(g, g.r, NV, CTp, mr, 1));
-    };
+    auto smem = [&](int mr) { return passes_smem(g, ps, NV, 1 << ilog2(ra * mr), mr); };
     int mr;
     if (mr_hint > 0 && (mr_hint & (mr_hint - 1)) == 0 && (1 << ilog2(ra * mr_hint)) <= 256 &&
         smem(mr_hint) <= 200 * 1024) {
@@ -165,38 +218,30 @@ FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint)
     FusedCfg c;
     c.mr = mr;
     c.nslice = (int)((m + mr - 1) / mr);
-    // with few columns per tile, several front tiles (back chunks) per CTA: up to one
-    // (tile, group, column) item per thread and level, two CTAs per SM
+    // with few columns per tile, several front tiles (back chunks) per CTA
     const int CTp = 1 << ilog2(ra * mr);
-    const int itemsH = std::max(1, (1 << g.kH) / 2) * CTp, itemsG = std::max(1, (1 << g.kG) / 2) * CTp;
-    const int64_t maxf = (int64_t)1 << (g.l1 + g.L - g.h), maxb = (int64_t)1 << g.l1;
-    c.tpc_f = 1;
-    while (c.tpc_f < 16 && 2 * c.tpc_f <= maxf && 2 * c.tpc_f * itemsH <= kThreads &&
-           front_smem(g, g.r, NV, CTp, mr, 2 * c.tpc_f) <= 113 * 1024)
-        c.tpc_f *= 2;
-    c.tpc_b = 1;
-    while (c.tpc_b < 16 && 2 * c.tpc_b <= maxb && 2 * c.tpc_b * itemsG <= kThreads &&
-           back_smem(g, g.r, NV, CTp, mr, 2 * c.tpc_b) <= 113 * 1024)
-        c.tpc_b *= 2;
+    const int kf = ps.hs[0], kb = ps.gs.back();
+    const bool lastf = ps.hs.size() == 1;
+    c.tpc_f = tiles_per_cta(kf, CTp, (int64_t)1 << (g.L - kf),
+                            [&](int t) { return front_smem(g, kf, lastf, g.r, NV, CTp, mr, t); });
+    c.tpc_b = tiles_per_cta(kb, CTp, (int64_t)1 << g.l1, [&](int t) { return back_smem(g, kb, g.r, NV, CTp, mr, t); });
     return c;
 }
 
-size_t fused_f32_ws_bytes(const Geo& g, int64_t m, int mr_hint)
-{
-    const FusedCfg c = fused_f32_config(g, m, mr_hint);
-    const int CTp = 1 << ilog2((g.ra > 0 ? g.ra : 1) * c.mr);
-    return (size_t)c.nslice * g.P * g.r * CTp * sizeof(float2);
-}
-
-bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int mr_hint,
-                     FrontArgs* fa, BackArgs* ba, size_t* sf, size_t* sb, int64_t* nfront, int64_t* nback)
+// Front and back argument blocks of the first H pass and the last G pass.  ws holds
+// W (the switch-level coefficients) and, for a split plan, two more buffers of the
+// same size for the coefficients between passes.
+bool make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int mr_hint,
+               const Passes& ps, FrontArgs* fa, BackArgs* ba, size_t* sf, size_t* sb, int64_t* nfront,
+               int64_t* nback)
 {
     const Geo& g = B.g;
     if (!fused_f32_supported(g.r)) return false;
     const int NV = (g.r < 8) ? 8 : (g.r < 16 ? 16 : 32);
     if (g.nv != NV || g.ra < 1) return false;
-    const FusedCfg cfg = fused_f32_config(g, m, mr_hint);
+    const FusedCfg cfg = config_of(g, m, mr_hint, ps);
     const int CTp = 1 << ilog2(g.ra * cfg.mr);
+    const int kf = ps.hs[0], kb = ps.gs.back();
     fa->g = g;
     fa->F = F;
     fa->m = m;
@@ -217,6 +262,10 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     fa->c0_lo = 0;
     fa->xi_lo = 0;
     fa->ph = B.ph;
+    fa->K = kf;
+    fa->last = ps.hs.size() == 1;
+    fa->Wo = nullptr;
+    fa->wlo = WLayout{g.l1 + kf, g.L - g.l1 - kf, 0, 0, g.P};
     ba->g = g;
     ba->m = m;
     ba->mr = cfg.mr;
@@ -237,11 +286,36 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
     ba->G = G;
     ba->beta = beta;
     ba->ph = B.ph;
-    *sf = front_smem(g, g.r, NV, CTp, cfg.mr, cfg.tpc_f);
-    *sb = back_smem(g, g.r, NV, CTp, cfg.mr, cfg.tpc_b);
-    *nfront = ((int64_t)1 << g.l1) * ((int64_t)1 << (g.L - g.h)) * cfg.nslice / cfg.tpc_f;
-    *nback = ((int64_t)1 << g.h) * cfg.nslice;
+    ba->K = kb;
+    ba->lb = g.L - g.l1 - kb;
+    if (ba->lb != g.h) ba->wl = WLayout{ba->lb, g.L - ba->lb, 0, 0, g.P};
+    *sf = front_smem(g, kf, fa->last, g.r, NV, CTp, cfg.mr, cfg.tpc_f);
+    *sb = back_smem(g, kb, g.r, NV, CTp, cfg.mr, cfg.tpc_b);
+    *nfront = ((int64_t)1 << (g.L - kf)) * cfg.nslice / cfg.tpc_f;
+    *nback = ((int64_t)1 << ba->lb) * cfg.nslice;
     return true;
+}
+
+}  // namespace
+
+FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint, bool split)
+{
+    return config_of(g, m, mr_hint, passes_of(g, split));
+}
+
+size_t fused_f32_ws_bytes(const Geo& g, int64_t m, int mr_hint, bool split)
+{
+    const Passes ps = passes_of(g, split);
+    const FusedCfg c = config_of(g, m, mr_hint, ps);
+    const int CTp = 1 << ilog2((g.ra > 0 ? g.ra : 1) * c.mr);
+    const size_t w = (size_t)c.nslice * g.P * g.r * CTp * sizeof(float2);
+    return ps.split() ? 3 * w : w;
+}
+
+bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int mr_hint,
+                     FrontArgs* fa, BackArgs* ba, size_t* sf, size_t* sb, int64_t* nfront, int64_t* nback)
+{
+    return make_args(B, F, m, G, beta, ws, mr_hint, passes_of(B.g, false), fa, ba, sf, sb, nfront, nback);
 }
 
 template <int R>
@@ -296,24 +370,96 @@ cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, floa
         if (!beta) return cudaMemsetAsync(G, 0, (size_t)B.g.N * m * sizeof(float2), st);
         return cudaSuccess;
     }
+    const Geo& g = B.g;
+    const Passes ps = passes_of(g, true);
     FrontArgs fa;
     BackArgs ba;
     size_t sf, sb;
     int64_t nf, nb;
-    if (!fused_make_args(B, F, m, G, beta, ws, mr_hint, &fa, &ba, &sf, &sb, &nf, &nb)) return cudaErrorNotSupported;
-    if (B.g.otf) {
-        const cudaError_t e = launch_part(B.g.r, &fa, nullptr, sf, nf, st);
-        return e != cudaSuccess ? e : launch_part(B.g.r, nullptr, &ba, sb, nb, st);
+    if (!make_args(B, F, m, G, beta, ws, mr_hint, ps, &fa, &ba, &sf, &sb, &nf, &nb)) return cudaErrorNotSupported;
+    if (!ps.split()) {
+        if (g.otf) {
+            const cudaError_t e = launch_part(g.r, &fa, nullptr, sf, nf, st);
+            return e != cudaSuccess ? e : launch_part(g.r, nullptr, &ba, sb, nb, st);
+        }
+        switch (g.r) {
+        case 6: return launch_r<6>(fa, ba, sf, sb, nf, nb, st);
+        case 8: return launch_r<8>(fa, ba, sf, sb, nf, nb, st);
+        case 10: return launch_r<10>(fa, ba, sf, sb, nf, nb, st);
+        case 12: return launch_r<12>(fa, ba, sf, sb, nf, nb, st);
+        case 14: return launch_r<14>(fa, ba, sf, sb, nf, nb, st);
+        case 16: return launch_r<16>(fa, ba, sf, sb, nf, nb, st);
+        default: return cudaErrorNotSupported;
+        }
     }
-    switch (B.g.r) {
-    case 6: return launch_r<6>(fa, ba, sf, sb, nf, nb, st);
-    case 8: return launch_r<8>(fa, ba, sf, sb, nf, nb, st);
-    case 10: return launch_r<10>(fa, ba, sf, sb, nf, nb, st);
-    case 12: return launch_r<12>(fa, ba, sf, sb, nf, nb, st);
-    case 14: return launch_r<14>(fa, ba, sf, sb, nf, nb, st);
-    case 16: return launch_r<16>(fa, ba, sf, sb, nf, nb, st);
-    default: return cudaErrorNotSupported;
+    // Split level ranges: ws = W | two buffers for the coefficients between passes.
+    // Order: front (V + first H pass) -> middle H passes (the last one applies the
+    // switch into W) -> middle G passes -> back (last G pass + U).
+    const size_t w = (size_t)fa.nslice * g.P * g.r * fa.CTp;
+    float2* buf[2] = {ws + w, ws + 2 * w};
+    auto plain = [&](int l) { return WLayout{l, g.L - l, 0, 0, g.P}; };
+    MidArgs ma{};
+    ma.g = g;
+    ma.mr = fa.mr;
+    ma.lmr = fa.lmr;
+    ma.CTp = fa.CTp;
+    ma.lct = fa.lct;
+    ma.nslice = fa.nslice;
+    ma.ph = B.ph;
+    auto run_mid = [&]() {
+        const bool last = ma.gkind == 0 && ma.last;
+        ma.tpc = tiles_per_cta(ma.K, ma.CTp, (int64_t)1 << (g.L - ma.K),
+                               [&](int t) { return mid_smem(g, ma.K, last, g.r, ma.CTp, t); });
+        const size_t smem = mid_smem(g, ma.K, last, g.r, ma.CTp, ma.tpc);
+        const int64_t nblocks = ((int64_t)1 << (g.L - ma.K)) * ma.nslice / ma.tpc;
+        return g.otf ? launch_mid_otf(g.r, ma, smem, nblocks, st) : launch_mid(g.r, ma, smem, nblocks, st);
+    };
+    int cur = 0, lvl = g.l1 + ps.hs[0];
+    if (!fa.last) fa.Wo = buf[cur];
+    cudaError_t e = launch_part(g.r, &fa, nullptr, sf, nf, st);
+    for (size_t i = 1; i < ps.hs.size() && e == cudaSuccess; ++i) {
+        const bool last = i + 1 == ps.hs.size();
+        ma.gkind = 0;
+        ma.la = lvl;
+        ma.K = ps.hs[i];
+        ma.last = last;
+        ma.Wi = buf[cur];
+        ma.wli = plain(lvl);
+        ma.Wo = last ? ws : buf[cur ^ 1];
+        ma.wlo = last ? fa.wl : plain(lvl + ma.K);
+        ma.MT = B.f32.MH;
+        ma.E = B.f32.EH;
+        ma.e0 = lvl - g.l1;
+        ma.S = B.f32.S;
+        e = run_mid();
+        cur ^= 1;
+        lvl += ma.K;
     }
+    const float2* src = ws;  // G side: from W at level h
+    WLayout wsrc = fa.wl;
+    lvl = g.h;
+    for (size_t i = 0; i + 1 < ps.gs.size() && e == cudaSuccess; ++i) {
+        ma.gkind = 1;
+        ma.la = lvl;
+        ma.K = ps.gs[i];
+        ma.last = 0;
+        ma.Wi = src;
+        ma.wli = wsrc;
+        ma.Wo = buf[i & 1];
+        ma.wlo = plain(lvl + ma.K);
+        ma.MT = B.f32.MG;
+        ma.E = B.f32.FG;
+        ma.e0 = lvl - g.h;
+        ma.S = nullptr;
+        e = run_mid();
+        src = ma.Wo;
+        wsrc = ma.wlo;
+        lvl += ma.K;
+    }
+    if (e != cudaSuccess) return e;
+    ba.W = src;
+    ba.wl = wsrc;
+    return launch_part(g.r, nullptr, &ba, sb, nb, st);
 }
 
 cudaError_t batch_launch_f32(int r, const BatchLaunch& bl, cudaStream_t st, bool set_attr, int* grid_out)
