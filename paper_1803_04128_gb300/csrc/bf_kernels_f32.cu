@@ -142,15 +142,16 @@ bool fused_f32_supported(int r) { return r == 6 || r == 8 || r == 10 || r == 12 
 namespace {
 
 // Level passes of the plain apply.  A tile of 2^k pairs closes k levels; beyond
-// kSplitAbove levels the shared memory of one tile leaves too few columns per tile,
-// so the plain apply splits the kH H levels and the kG G levels into passes of at
-// most kPassMax levels (as even as possible), linked through HBM workspaces.  The
-// batched and sharded applies keep one pass per side.
-constexpr int kSplitAbove = 5, kPassMax = 4;
+// kSplitAbove levels (kSplitAboveOtf with evaluated phases, whose last H pass also
+// keeps [2^k][r][r] switch blocks) the shared memory of one tile leaves too few
+// columns per tile, so the plain apply splits the kH H levels and the kG G levels
+// into passes of at most kPassMax levels (as even as possible), linked through HBM
+// workspaces.  The batched and sharded applies keep one pass per side.
+constexpr int kSplitAbove = 5, kSplitAboveOtf = 4, kPassMax = 4;
 
-std::vector<int> split_levels(int k, bool split)
+std::vector<int> split_levels(int k, bool split, bool otf)
 {
-    if (!split || k <= kSplitAbove) return {k};
+    if (!split || k <= (otf ? kSplitAboveOtf : kSplitAbove)) return {k};
     const int n = (k + kPassMax - 1) / kPassMax, base = k / n, extra = k % n;
     std::vector<int> v;
     for (int i = 0; i < n; ++i) v.push_back(base + (i < extra ? 1 : 0));
@@ -170,7 +171,10 @@ struct Passes {
     }
 };
 
-Passes passes_of(const Geo& g, bool split) { return Passes{split_levels(g.kH, split), split_levels(g.kG, split)}; }
+Passes passes_of(const Geo& g, bool split)
+{
+    return Passes{split_levels(g.kH, split, g.otf), split_levels(g.kG, split, g.otf)};
+}
 
 // largest shared memory of any pass for (mr, CTp) with one tile per CTA
 size_t passes_smem(const Geo& g, const Passes& ps, int NV, int CTp, int mr)

@@ -1,7 +1,8 @@
 """GPU tests of the level passes of the plain FP32 apply.
 
-When kH or kG exceeds 5 levels (N >= 2^20 at r = 10), bf_apply runs the H and G
-levels in several passes of at most 4 levels each.  The passes share an HBM
+When kH or kG exceeds 5 levels (N >= 2^20 at r = 10; with on-the-fly phases from
+5 levels, N >= 2^17), bf_apply runs the H and G levels in several passes of at most
+4 levels each.  The passes share an HBM
 workspace.  Every (group, column) item performs the same operations in the same
 order in either form, and values round-trip through HBM exactly.  So the split
 apply must equal, bit for bit, the single-pass kernels that the batched apply
@@ -49,9 +50,10 @@ def test_split_apply_equals_single_pass_batch(r, m):
     assert relerr(G1.cpu().numpy().astype(np.complex128), g64.cpu().numpy()) < 2e-6
 
 
-@pytest.mark.parametrize("m", [2, 40])
-def test_split_otf_apply_equals_single_pass_shard(m):
-    N = 1 << 20
+@pytest.mark.parametrize("lg,m", [(20, 2), (20, 40), (18, 16), (17, 3)])
+def test_split_otf_apply_equals_single_pass_shard(lg, m):
+    # on-the-fly plans split from 5 levels up: 2^18 -> 3 + 2 on each side, 2^17 -> G only
+    N = 1 << lg
     po = api.Plan(N, r=10, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH, on_the_fly=True)
     F = gauss(N, m, 60 + m)
     G1 = po.apply(F, prec=api.F32)
