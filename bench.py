@@ -669,7 +669,19 @@ def main():
     alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12   # TFLOP/s FP32 FMA
     roof = None
     launches = sum(n for n, _ in kt.result.values())
-    if prec == api.F32 and fk in kt.result:
+    if prec == api.F32 and any(k.startswith("mid_") for k in kt.result):
+        # level ranges split into passes (front, middle H and G passes, back): the
+        # apply's algorithmic flops over the summed time of all its passes
+        tot = sum(v[1] for v in kt.result.values())
+        per_apply_ms = tot / args.steps
+        achieved = (front + back) * w["split"] ** 2 / (per_apply_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "all passes of one apply (front, mid_h, mid_g, back)",
+                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)" % (sm_mhz_max, peak_src),
+                "kernel_ms": {k: v[1] / v[0] for k, v in kt.result.items()},
+                "share": {k: v[1] / tot for k, v in kt.result.items()}}
+    elif prec == api.F32 and fk in kt.result:
         nf, tf = kt.result[fk]
         nb, tb = kt.result[bk]
         nblk = w["split"] ** 2
