@@ -233,7 +233,7 @@ FusedCfg config_of(const Geo& g, int64_t m, int mr_hint, const Passes& ps)
 }
 
 // Front and back argument blocks of the first H pass and the last G pass.  ws holds
-// W (the switch-level coefficients) and, for a split plan, two more buffers of the
+// W (the switch-level coefficients) and, for a split plan, one more buffer of the
 // same size for the coefficients between passes.
 bool make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int mr_hint,
                const Passes& ps, FrontArgs* fa, BackArgs* ba, size_t* sf, size_t* sb, int64_t* nfront,
@@ -313,7 +313,7 @@ size_t fused_f32_ws_bytes(const Geo& g, int64_t m, int mr_hint, bool split)
     const FusedCfg c = config_of(g, m, mr_hint, ps);
     const int CTp = 1 << ilog2((g.ra > 0 ? g.ra : 1) * c.mr);
     const size_t w = (size_t)c.nslice * g.P * g.r * CTp * sizeof(float2);
-    return ps.split() ? 3 * w : w;
+    return ps.split() ? 2 * w : w;
 }
 
 bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int mr_hint,
@@ -396,11 +396,13 @@ cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, floa
         default: return cudaErrorNotSupported;
         }
     }
-    // Split level ranges: ws = W | two buffers for the coefficients between passes.
-    // Order: front (V + first H pass) -> middle H passes (the last one applies the
-    // switch into W) -> middle G passes -> back (last G pass + U).
+    // Split level ranges: ws = W | X, one more buffer of W's size.  A pass reads the
+    // buffer the previous one wrote and writes the other: the last H pass writes W
+    // (after the switch), so H pass i of nh writes X if nh - 2 - i is even, else W;
+    // G pass j (of the middle ones) reads W or X and writes X if j is even, else W.
+    // Order: front (V + first H pass) -> middle H passes -> middle G passes -> back.
     const size_t w = (size_t)fa.nslice * g.P * g.r * fa.CTp;
-    float2* buf[2] = {ws + w, ws + 2 * w};
+    float2* X = ws + w;
     auto plain = [&](int l) { return WLayout{l, g.L - l, 0, 0, g.P}; };
     MidArgs ma{};
     ma.g = g;
@@ -418,38 +420,39 @@ cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, floa
         const int64_t nblocks = ((int64_t)1 << (g.L - ma.K)) * ma.nslice / ma.tpc;
         return g.otf ? launch_mid_otf(g.r, ma, smem, nblocks, st) : launch_mid(g.r, ma, smem, nblocks, st);
     };
-    int cur = 0, lvl = g.l1 + ps.hs[0];
-    if (!fa.last) fa.Wo = buf[cur];
+    const int nh = (int)ps.hs.size();
+    auto h_out = [&](int i) { return i == nh - 1 ? ws : (((nh - 2 - i) & 1) == 0 ? X : ws); };
+    int lvl = g.l1 + ps.hs[0];
+    if (!fa.last) fa.Wo = h_out(0);
     cudaError_t e = launch_part(g.r, &fa, nullptr, sf, nf, st);
-    for (size_t i = 1; i < ps.hs.size() && e == cudaSuccess; ++i) {
-        const bool last = i + 1 == ps.hs.size();
+    for (int i = 1; i < nh && e == cudaSuccess; ++i) {
+        const bool last = i == nh - 1;
         ma.gkind = 0;
         ma.la = lvl;
-        ma.K = ps.hs[i];
+        ma.K = ps.hs[(size_t)i];
         ma.last = last;
-        ma.Wi = buf[cur];
+        ma.Wi = h_out(i - 1);
         ma.wli = plain(lvl);
-        ma.Wo = last ? ws : buf[cur ^ 1];
+        ma.Wo = h_out(i);
         ma.wlo = last ? fa.wl : plain(lvl + ma.K);
         ma.MT = B.f32.MH;
         ma.E = B.f32.EH;
         ma.e0 = lvl - g.l1;
         ma.S = B.f32.S;
         e = run_mid();
-        cur ^= 1;
         lvl += ma.K;
     }
     const float2* src = ws;  // G side: from W at level h
     WLayout wsrc = fa.wl;
     lvl = g.h;
-    for (size_t i = 0; i + 1 < ps.gs.size() && e == cudaSuccess; ++i) {
+    for (size_t j = 0; j + 1 < ps.gs.size() && e == cudaSuccess; ++j) {
         ma.gkind = 1;
         ma.la = lvl;
-        ma.K = ps.gs[i];
+        ma.K = ps.gs[j];
         ma.last = 0;
         ma.Wi = src;
         ma.wli = wsrc;
-        ma.Wo = buf[i & 1];
+        ma.Wo = (j & 1) == 0 ? X : ws;
         ma.wlo = plain(lvl + ma.K);
         ma.MT = B.f32.MG;
         ma.E = B.f32.FG;
