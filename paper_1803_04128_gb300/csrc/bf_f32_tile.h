@@ -334,12 +334,16 @@ __device__ __forceinline__ void switch_item(const float2* xs, int CTp, const flo
 // ------------------------------------------------------------------ front --
 // Shared memory: Mv^T [NV][R4] | MH^T [kH][2R][R4] | per tile u < tpc:
 // X [T][R][CTp] | EH double buffer [2][T][2][R] | EV [T*NV] | F rows [T*NV][mr]
-// | (OTF only) switch blocks [T][R][R].
+// | (OTF or s_smem, last pass only) switch blocks [T][R][R] | (bk_smem) b_k [ra][T*NV].
+// The table switch blocks are copied with the last level's phases, so they arrive during
+// the H levels; b_k comes with the F rows.
 // A CTA applies tpc consecutive tiles (work indices work * tpc + u): with few
 // columns per tile, several tiles share the CTA's threads and their loads are
 // in flight together; each tile's arithmetic is the same for any tpc.  The
 // phases of level j are staged (cp.async) while level j-1 is computed; b_k and
-// the switch matrices are read through the read-only cache.  With OTF the
+// the switch matrices are read through the read-only cache unless bk_smem /
+// s_smem put them in shared memory (the single-operator apply, when they fit
+// beside the tiles; the batched kernel keeps its slices wider).  With OTF the
 // phase tables are not read: EV, each level's EH and the switch blocks are
 // evaluated (otf_turns, otf_exp) into the same shared buffers.
 template <int R, int NV, bool OTF = false>
@@ -352,8 +356,9 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
     const int64_t nBh = (int64_t)1 << (g.L - g.h);   // T_Omega nodes at level L-h
     const int64_t N = g.N, P = g.P, m = A.m;
     const int L = g.L, l1 = g.l1;
+    const bool sblk = A.last && (OTF || A.s_smem);  // switch blocks in shared memory
     const size_t tile_f2 = (size_t)T * R * CTp + (size_t)2 * T * 2 * R + (size_t)T * NV + (size_t)T * NV * mr +
-                           (OTF && A.last ? (size_t)T * R * R : 0);
+                           (sblk ? (size_t)T * R * R : 0) + (A.bk_smem ? (size_t)ra * T * NV : 0);
 
     float* MvTs = reinterpret_cast<float*>(smem_raw);                      // [NV][R4]
     float* MHTs = MvTs + NV * R4;                                          // [K][2R][R4]
@@ -362,7 +367,8 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
     auto EHof = [&](int u) { return Xof(u) + (size_t)T * R * CTp; };                       // [2][T][2][R]
     auto EVof = [&](int u) { return EHof(u) + (size_t)2 * T * 2 * R; };                    // [T*NV]
     auto Fof = [&](int u) { return EVof(u) + (size_t)T * NV; };                            // [T*NV][mr]
-    auto Sof = [&](int u) { return Fof(u) + (size_t)T * NV * mr; };                        // [T][R][R] (OTF)
+    auto Sof = [&](int u) { return Fof(u) + (size_t)T * NV * mr; };                        // [T][R][R] (sblk)
+    auto BKof = [&](int u) { return Sof(u) + (sblk ? (size_t)T * R * R : 0); };           // [ra][T*NV] (bk_smem)
     // tile u: work index work * tpc + u -> (column slice, x-node p, T_Omega chunk c0)
     __shared__ int64_t s_p[16], s_c0[16];
     __shared__ int s_slice[16];
@@ -379,6 +385,17 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
     auto c0_of = [&](int u) { return s_c0[u]; };
 
     const float2* EHg = A.EH;
+    // switch blocks of the tiles (tables): pair (x-node (p << K) + lp, T_Omega node c0) at
+    // q = ((p << K) + lp) * nBh + c0 of S [P][R][R], R*R/2 16-byte copies each
+    auto stage_s = [&]() {
+        for (int u = 0; u < tpc; ++u) {
+            const int64_t p = p_of(u), c0 = c0_of(u);
+            for (int e = tid; e < T * R * R / 2; e += kThreads) {
+                const int lp = e / (R * R / 2), w = e - lp * (R * R / 2);
+                cp16(Sof(u) + (size_t)lp * R * R + 2 * w, A.S + (((p << K) + lp) * nBh + c0) * R * R + 2 * w);
+            }
+        }
+    };
     auto stage_eh = [&](int j) {  // phases of level l1 + j into buffer (j - 1) & 1 of every tile
         if constexpr (OTF) {  // EH entry (lp, c, s) = e(Phi(c_A, xi) - Phi(c_P, xi)), Eq. 2
             const int l = l1 + j, na = (int)(N >> l), nb = (int)(N >> (L - l));
@@ -409,6 +426,7 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
                 cp16(dst + (size_t)lp * 2 * R + 2 * w, eh + (ap * nBl + bp) * 2 * R + 2 * w);
             }
         }
+        if (sblk && j == K) stage_s();
     };
     // group 0: matrices, EV, F rows, level-1 phases; group 1: level-2 phases
     stage_matrix(MvTs, A.MvT, NV, R, R4, tid);
@@ -425,6 +443,11 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
             const float2* ev = A.EV + p_of(u) * N + xi_base;
             for (int e = tid; e < T * NV / 2; e += kThreads) cp16(EVs + 2 * e, ev + 2 * e);
         }
+        if (A.bk_smem)
+            for (int e = tid; e < ra * T * NV / 2; e += kThreads) {
+                const int k = e / (T * NV / 2), w = e - k * (T * NV / 2);
+                cp16(BKof(u) + (size_t)k * T * NV + 2 * w, A.bk + (size_t)k * N + xi_base + 2 * w);
+            }
         const int64_t cbase = (int64_t)slice_of(u) * mr;
         float2* Fs = Fof(u);
         for (int e = tid; e < T * NV * mr; e += kThreads) {
@@ -434,6 +457,7 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
         }
     }
     if (K >= 1) stage_eh(1);
+    if (!OTF && sblk && K == 0) stage_s();
     cp_commit();
     if (K >= 2) {
         stage_eh(2);
@@ -464,10 +488,10 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
             float2 acc[R];
 #pragma unroll
             for (int t = 0; t < R; ++t) acc[t] = make_float2(0.f, 0.f);
-            const float2* bk = A.bk + (size_t)k * N + xi_base + j * NV;
+            const float2* bk = A.bk_smem ? BKof(u) + (size_t)k * T * NV + j * NV : A.bk + (size_t)k * N + xi_base + j * NV;
 #pragma unroll
             for (int x = 0; x < NV; ++x) {
-                const float2 z = cmulf(EVs[j * NV + x], cmulf(__ldg(bk + x), f[x]));
+                const float2 z = cmulf(EVs[j * NV + x], cmulf(A.bk_smem ? bk[x] : __ldg(bk + x), f[x]));
                 const float4* mv = reinterpret_cast<const float4*>(MvTs + x * R4);
 #pragma unroll
                 for (int t4 = 0; t4 < R4 / 4; ++t4) {
@@ -525,7 +549,7 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
         if (A.last) {
             const int64_t q = ((p_of(u) << K) + lp) * nBh + c0_of(u);
             float2* wo = A.W + (size_t)w_pair(A.wl, (p_of(u) << K) + lp, c0_of(u), slice_of(u)) * R * CTp + col;
-            if constexpr (OTF)
+            if (sblk)
                 switch_item<R, true>(xs, CTp, reinterpret_cast<const float4*>(Sof(u) + (size_t)lp * R * R), wo);
             else
                 switch_item<R, false>(xs, CTp, reinterpret_cast<const float4*>(A.S + q * R * R), wo);
@@ -858,12 +882,15 @@ inline int ilog2(int v)
     return l;
 }
 
-// shared memory of a front pass of K H levels (last: it reaches h and applies the switch)
-inline size_t front_smem(const Geo& g, int K, bool last, int R, int NV, int CTp, int mr, int tpc)
+// shared memory of a front pass of K H levels (last: it reaches h and applies the switch;
+// s_smem: with the table switch blocks in shared memory; bk_smem: with b_k)
+inline size_t front_smem(const Geo& g, int K, bool last, int R, int NV, int CTp, int mr, int tpc,
+                         bool s_smem = false, bool bk_smem = false)
 {
     const size_t T = (size_t)1 << K, R4 = (R + 3) & ~3;
     return sizeof(float2) * (size_t)tpc *
-               (T * R * CTp + 2 * T * 2 * R + T * NV + T * NV * mr + (g.otf && last ? T * R * R : 0)) +
+               (T * R * CTp + 2 * T * 2 * R + T * NV + T * NV * mr + ((g.otf || s_smem) && last ? T * R * R : 0) +
+                (bk_smem ? (size_t)(g.ra > 0 ? g.ra : 1) * T * NV : 0)) +
            sizeof(float) * ((size_t)NV * R4 + (size_t)K * 2 * R * R4);
 }
 

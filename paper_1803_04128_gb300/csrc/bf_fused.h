@@ -39,6 +39,8 @@ struct FrontArgs {
     int last;          // 1: the pass reaches level h: apply the switch and write W (layout wl)
     float2* Wo;        // last = 0: the coefficients at level l1 + K, layout wlo
     WLayout wlo;
+    int s_smem = 0;    // last = 1, tables: copy each tile's switch blocks into shared memory
+    int bk_smem = 0;   // copy each tile's b_k values into shared memory
 };
 
 struct BackArgs {

@@ -234,10 +234,12 @@ FusedCfg config_of(const Geo& g, int64_t m, int mr_hint, const Passes& ps)
 
 // Front and back argument blocks of the first H pass and the last G pass.  ws holds
 // W (the switch-level coefficients) and, for a split plan, one more buffer of the
-// same size for the coefficients between passes.
+// same size for the coefficients between passes.  s_stage: a front pass that applies the
+// switch copies its tiles' switch blocks, and then b_k, into shared memory when they fit
+// beside the chosen tiles (two CTAs per SM); the arithmetic is the same either way.
 bool make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int mr_hint,
                const Passes& ps, FrontArgs* fa, BackArgs* ba, size_t* sf, size_t* sb, int64_t* nfront,
-               int64_t* nback)
+               int64_t* nback, bool s_stage = false)
 {
     const Geo& g = B.g;
     if (!fused_f32_supported(g.r)) return false;
@@ -294,6 +296,12 @@ bool make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int bet
     ba->lb = g.L - g.l1 - kb;
     if (ba->lb != g.h) ba->wl = WLayout{ba->lb, g.L - ba->lb, 0, 0, g.P};
     *sf = front_smem(g, kf, fa->last, g.r, NV, CTp, cfg.mr, cfg.tpc_f);
+    if (s_stage) {
+        auto fs = [&](bool s, bool b) { return front_smem(g, kf, fa->last, g.r, NV, CTp, cfg.mr, cfg.tpc_f, s, b); };
+        if (fa->last && !g.otf && fs(true, false) <= 113 * 1024) fa->s_smem = 1;
+        if (fs(fa->s_smem, true) <= 113 * 1024) fa->bk_smem = 1;
+        *sf = fs(fa->s_smem, fa->bk_smem);
+    }
     *sb = back_smem(g, kb, g.r, NV, CTp, cfg.mr, cfg.tpc_b);
     *nfront = ((int64_t)1 << (g.L - kf)) * cfg.nslice / cfg.tpc_f;
     *nback = ((int64_t)1 << ba->lb) * cfg.nslice;
@@ -380,7 +388,8 @@ cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, floa
     BackArgs ba;
     size_t sf, sb;
     int64_t nf, nb;
-    if (!make_args(B, F, m, G, beta, ws, mr_hint, ps, &fa, &ba, &sf, &sb, &nf, &nb)) return cudaErrorNotSupported;
+    if (!make_args(B, F, m, G, beta, ws, mr_hint, ps, &fa, &ba, &sf, &sb, &nf, &nb, true))
+        return cudaErrorNotSupported;
     if (!ps.split()) {
         if (g.otf) {
             const cudaError_t e = launch_part(g.r, &fa, nullptr, sf, nf, st);
