@@ -200,8 +200,15 @@ bf_status bf_apply(bf_plan* plan, bf_precision prec, const void* F, int64_t m, v
  * F, G, m, stream as for bf_apply (c64).  Allocates nothing. */
 bf_status bf_apply_f32_noalloc(bf_plan* plan, const void* F, int64_t m, void* G, void* stream);
 
-/* Same as bf_apply but F and G are HOST buffers: copies F to the device,
- * applies, copies G back, and synchronises `stream` before returning. */
+/* Same as bf_apply but F and G are HOST buffers (pinned memory lets the copies
+ * run asynchronously): copies F to the device, applies, copies G back, and
+ * synchronises `stream` before returning.  The result is bitwise that of
+ * bf_apply.  An FP32 apply of a one-sub-BF plan (one front and one back pass)
+ * copies in four row ranges on the plan's own copy stream, overlapped with the
+ * kernels of the other ranges.  Those kernels alternate between `stream` and a
+ * second stream of the plan that first waits for `stream`'s earlier work.  Other
+ * applies copy F, apply on `stream`, then copy G.  The staging buffers belong
+ * to the plan, so host applies of one plan must not overlap. */
 bf_status bf_apply_host(bf_plan* plan, bf_precision prec, const void* F_host, int64_t m,
                         void* G_host, void* stream);
 

@@ -684,6 +684,52 @@ bf_status device_apply_ws(bf_plan* p, bf_precision prec, const void* F, int64_t 
     return BF_OK;
 }
 
+// FP32 apply of a one-sub-BF plan from host buffers in kHostChunks row ranges: the F rows of
+// range k are copied on ds->copy while the front runs on the ranges before it; the G rows of
+// range k are copied back while the back runs on the ranges after it.  Consecutive ranges
+// alternate between st and ds->comp2.  The kernels and their arithmetic are those of bf_apply.
+static bf_status apply_host_pipelined(bf_plan* p, const void* F, int64_t m, void* G, cudaStream_t st,
+                                      unsigned char* dF, unsigned char* dG)
+{
+    DeviceState* ds = p->dev;
+    constexpr int nch = DeviceState::kHostChunks;
+    if (!ds->copy) BF_CUDA(cudaStreamCreateWithFlags(&ds->copy, cudaStreamNonBlocking));
+    if (!ds->comp2) BF_CUDA(cudaStreamCreateWithFlags(&ds->comp2, cudaStreamNonBlocking));
+    for (auto& ev : ds->hev)
+        if (!ev) BF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaEvent_t* fready = ds->hev;
+    cudaEvent_t* gdone = ds->hev + nch;
+    cudaEvent_t ev_in = ds->hev[2 * nch], ev_out = ds->hev[2 * nch + 1];
+    const cudaEvent_t* join = ds->hev + 2 * nch + 2;
+    const size_t rows = (size_t)p->N / nch, bytes = rows * (size_t)m * sizeof(float2);
+    // the copies start after the caller's earlier work on st (it may still use the staging buffers)
+    BF_CUDA(cudaEventRecord(ev_in, st));
+    BF_CUDA(cudaStreamWaitEvent(ds->copy, ev_in, 0));
+    for (int k = 0; k < nch; ++k) {
+        BF_CUDA(cudaMemcpyAsync(dF + k * bytes, (const unsigned char*)F + k * bytes, bytes, cudaMemcpyHostToDevice,
+                                ds->copy));
+        BF_CUDA(cudaEventRecord(fready[k], ds->copy));
+    }
+    bf_status rs = device_reserve(p, BF_PREC_F32, m, st);
+    if (rs != BF_OK) return rs;
+    const cudaError_t e = launch_fused_f32_chunked(ds->blocks[0], (const float2*)dF, m, (float2*)dG,
+                                                   (float2*)ds->ws32, st, ds->comp2, p->mr_hint(m), nch, fready,
+                                                   gdone, join);
+    if (e != cudaSuccess) {
+        set_error("bf_apply_host: kernel launch failed: %s", cudaGetErrorString(e));
+        return BF_ERR_CUDA;
+    }
+    for (int k = 0; k < nch; ++k) {
+        BF_CUDA(cudaStreamWaitEvent(ds->copy, gdone[k], 0));
+        BF_CUDA(cudaMemcpyAsync((unsigned char*)G + k * bytes, dG + k * bytes, bytes, cudaMemcpyDeviceToHost,
+                                ds->copy));
+    }
+    BF_CUDA(cudaEventRecord(ev_out, ds->copy));
+    BF_CUDA(cudaStreamWaitEvent(st, ev_out, 0));
+    BF_CUDA(cudaStreamSynchronize(st));
+    return BF_OK;
+}
+
 bf_status device_apply_host(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G, void* stream)
 {
     DeviceState* ds = p->dev;
@@ -695,6 +741,10 @@ bf_status device_apply_host(bf_plan* p, bf_precision prec, const void* F, int64_
     if (s != BF_OK) return s;
     unsigned char* dF = (unsigned char*)ds->stage;
     unsigned char* dG = dF + nb;
+    if (prec == BF_PREC_F32 && ds->blocks.size() == 1 && fused_f32_supported(ds->blocks[0].g.r) &&
+        ds->blocks[0].g.nv <= 2 * ds->blocks[0].g.r &&
+        fused_f32_chunkable(ds->blocks[0], m, p->mr_hint(m), DeviceState::kHostChunks))
+        return apply_host_pipelined(p, F, m, G, st, dF, dG);
     BF_CUDA(cudaMemcpyAsync(dF, F, nb, cudaMemcpyHostToDevice, st));
     s = device_apply(p, prec, dF, m, dG, stream);
     if (s != BF_OK) return s;
@@ -730,6 +780,10 @@ void device_free(bf_plan* p)
     cudaFree(ds->ws64);
     cudaFree(ds->ws32);
     cudaFree(ds->stage);
+    if (ds->copy) cudaStreamDestroy(ds->copy);
+    if (ds->comp2) cudaStreamDestroy(ds->comp2);
+    for (auto& ev : ds->hev)
+        if (ev) cudaEventDestroy(ev);
     cudaFree(ds->otf_data);
     cudaFree(ds->err);
     delete ds;

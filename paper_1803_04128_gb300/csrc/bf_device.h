@@ -80,6 +80,11 @@ struct DeviceState {
     size_t ws32_bytes = 0;
     void* stage = nullptr;  // F/G staging for bf_apply_host
     size_t stage_bytes = 0;
+    // bf_apply_host's copy stream, second compute stream and events (row ranges copied
+    // while others compute)
+    cudaStream_t copy = nullptr, comp2 = nullptr;
+    static constexpr int kHostChunks = 4;
+    cudaEvent_t hev[2 * kHostChunks + 6] = {};
     int* err = nullptr;     // device error word (0 = ok)
     bool otf = false;       // factored by bf_factor_otf: no phase tables, FP32 apply only
     void* otf_data = nullptr;  // OtfPhase rows and grids
@@ -116,6 +121,16 @@ struct FusedCfg {
 // side, as the batched and sharded applies run them
 FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint = 0, bool split = true);
 size_t fused_f32_ws_bytes(const Geo& g, int64_t m, int mr_hint = 0, bool split = true);
+// The same apply in nch row ranges (a power of two), for copies that overlap the kernels:
+// front launch k waits for fready[k] (F rows [k N/nch, (k+1) N/nch) on the device); gdone[k]
+// is recorded after back launch k (G rows [k N/nch, (k+1) N/nch) final).  Range k runs on
+// st (k even) or st2 (k odd); join[0..3] order st2 after st's earlier work, the backs
+// after all fronts, and st after everything.  Only plans that run one front and one back
+// pass and split evenly (fused_f32_chunkable).
+bool fused_f32_chunkable(const DevBlock& B, int64_t m, int mr_hint, int nch);
+cudaError_t launch_fused_f32_chunked(const DevBlock& B, const float2* F, int64_t m, float2* G, float2* ws,
+                                     cudaStream_t st, cudaStream_t st2, int mr_hint, int nch, const cudaEvent_t* fready,
+                                     const cudaEvent_t* gdone, const cudaEvent_t* join);
 cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta,
                              float2* ws, cudaStream_t st, int mr_hint = 0);
 bool fused_f32_supported(int r);

@@ -478,6 +478,72 @@ cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, floa
     return launch_part(g.r, nullptr, &ba, sb, nb, st);
 }
 
+// Row ranges of a single-pass apply (one front and one back pass): nch front launches over
+// consecutive ranges of T_Omega chunks and nch back launches over consecutive ranges of
+// x-nodes.  Front launch k reads F rows [k N/nch, (k+1) N/nch) only; back launch k writes
+// G rows [k N/nch, (k+1) N/nch) only.  Same tiles, same arithmetic as launch_fused_f32.
+static bool chunk_args(const DevBlock& B, const float2* F, int64_t m, float2* G, float2* ws, int mr_hint, int nch,
+                       FrontArgs* fa, BackArgs* ba, size_t* sf, size_t* sb, int64_t* nf, int64_t* nb)
+{
+    const Geo& g = B.g;
+    if (g.ra == 0 || nch < 1 || (nch & (nch - 1))) return false;
+    const Passes ps = passes_of(g, true);
+    if (ps.split()) return false;
+    if (!make_args(B, F, m, G, 0, ws, mr_hint, ps, fa, ba, sf, sb, nf, nb, true)) return false;
+    const int64_t nc0 = (g.N / g.n0) >> (fa->K + g.l1);  // T_Omega chunks c0 (tiles per x-node)
+    const int64_t npp = (int64_t)1 << ba->lb;             // back x-nodes
+    if (nc0 % nch || npp % nch) return false;
+    if (((nc0 / nch) << g.l1) * fa->nslice % fa->tpc) return false;
+    *nf /= nch;
+    *nb /= nch;
+    return true;
+}
+
+bool fused_f32_chunkable(const DevBlock& B, int64_t m, int mr_hint, int nch)
+{
+    FrontArgs fa;
+    BackArgs ba;
+    size_t sf, sb;
+    int64_t nf, nb;
+    return chunk_args(B, nullptr, m, nullptr, nullptr, mr_hint, nch, &fa, &ba, &sf, &sb, &nf, &nb);
+}
+
+cudaError_t launch_fused_f32_chunked(const DevBlock& B, const float2* F, int64_t m, float2* G, float2* ws,
+                                     cudaStream_t st, cudaStream_t st2, int mr_hint, int nch, const cudaEvent_t* fready,
+                                     const cudaEvent_t* gdone, const cudaEvent_t* join)
+{
+    FrontArgs fa;
+    BackArgs ba;
+    size_t sf, sb;
+    int64_t nf, nb;
+    if (!chunk_args(B, F, m, G, ws, mr_hint, nch, &fa, &ba, &sf, &sb, &nf, &nb)) return cudaErrorNotSupported;
+    const int64_t nc0 = (B.g.N / B.g.n0) >> (fa.K + B.g.l1), npp = (int64_t)1 << ba.lb;
+    // range k runs on stream k mod 2, so that a range's CTAs start while the previous
+    // range's last wave drains; st2 starts after the caller's earlier work on st
+    cudaStream_t S[2] = {st, st2};
+    cudaError_t e = cudaEventRecord(join[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st2, join[0], 0);
+    for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+        if ((e = cudaStreamWaitEvent(S[k & 1], fready[k], 0)) != cudaSuccess) break;
+        fa.c0_lo = k * (nc0 / nch);
+        e = launch_part(B.g.r, &fa, nullptr, sf, nf, S[k & 1]);
+    }
+    // every back range reads the switch-level pairs of all front ranges: join both streams
+    if (e == cudaSuccess) e = cudaEventRecord(join[1], st2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join[1], 0);
+    if (e == cudaSuccess) e = cudaEventRecord(join[2], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st2, join[2], 0);
+    for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+        ba.pp_lo = k * (npp / nch);
+        if ((e = launch_part(B.g.r, nullptr, &ba, sb, nb, S[k & 1])) != cudaSuccess) break;
+        e = cudaEventRecord(gdone[k], S[k & 1]);
+    }
+    // st ends after all back ranges
+    if (e == cudaSuccess) e = cudaEventRecord(join[3], st2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join[3], 0);
+    return e;
+}
+
 cudaError_t batch_launch_f32(int r, const BatchLaunch& bl, cudaStream_t st, bool set_attr, int* grid_out)
 {
     switch (r) {

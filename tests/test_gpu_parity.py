@@ -156,6 +156,34 @@ def test_apply_host_matches_device_apply():
     assert np.array_equal(Gh.astype(np.complex128), Gd)
 
 
+@pytest.mark.parametrize("otf", [False, True])
+def test_apply_host_row_ranges_bitwise(otf):
+    """The host apply copies F and G in row ranges that overlap the front and back
+    launches of the other ranges (one sub-BF, one pass per side): the same tiles as
+    bf_apply, so bitwise the same result, at the benchmark's shape (N = 65536, m = 64)
+    and on a ragged column count; two calls in a row reuse the copy stream and events."""
+    N = 65536
+    plan = api.Plan(N, eps=1e-6, amp_kind=L.AMP_SMOOTH, on_the_fly=otf)
+    for m, seed in ((64, 21), (7, 22)):
+        F = inputs.complex_gaussian(N, m, seed=seed).astype(np.complex64)
+        Gd = run(plan, F, api.F32)
+        for _ in range(2):
+            Gh = plan.apply_host(F)
+            assert np.array_equal(Gh.astype(np.complex128), Gd)
+
+
+def test_apply_host_whole_buffer_paths():
+    """Host applies that copy F and G in one piece (FP64; a plan of four sub-BFs) are
+    bitwise the device applies."""
+    N, m = 4096, 3
+    plan = api.Plan(N, r=10, amp_kind=L.AMP_SMOOTH)
+    F = inputs.complex_gaussian(N, m, seed=23)
+    assert np.array_equal(plan.apply_host(np.ascontiguousarray(F), prec=api.F64), run(plan, F, api.F64))
+    pw = api.Plan(N, r=10, phase_kind=L.PHASE_FIO_PW, amp_kind=L.AMP_SMOOTH, split=2)
+    F32 = F.astype(np.complex64)
+    assert np.array_equal(pw.apply_host(F32).astype(np.complex128), run(pw, F32, api.F32))
+
+
 def test_bad_calls_return_errors():
     plan = api.Plan(1024, r=10)
     F = torch.zeros((1024, 2), dtype=torch.complex64, device="cuda")
