@@ -43,7 +43,9 @@ def rsvd_sampled(entry, m, n, r, q=5, sweeps=2, seed=0):
     J = np.union1d(pi_col, rng.choice(n, min(n, r * q), replace=False))
     I = np.union1d(pi_row, rng.choice(m, min(m, r * q), replace=False))
     M = np.linalg.pinv(Qc[I, :]) @ entry(I, J) @ np.linalg.pinv(Qr.conj().T[:, J])
-    UM, SM, VMh = np.linalg.svd(M)
+    # thin SVD: the column and row bases may have different numerical ranks, and
+    # U0 = Qc U_M, S0, V0 = Qr V_M then all have min of the two columns
+    UM, SM, VMh = np.linalg.svd(M, full_matrices=False)
     return Qc @ UM, SM, (VMh @ Qr.conj().T).conj().T
 
 
