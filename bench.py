@@ -9,6 +9,10 @@ levels, switch, all G levels, U, amplitude split-out).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload fio2|fio1|fio3|fio4|serve5] [--prec f32|f64|bf16x3]
 
+The fio2 line also carries two side measurements of the same operator: the
+plan without phase tables ("on_the_fly") and the plan factored from kernel
+entries alone ("indirect").
+
 Under torchrun each rank applies its own operator replica to its own m
 right-hand sides (weak scaling, no data-path collective).
 """
@@ -549,6 +553,32 @@ def otf_side(args, w, plan, F, G, flush, stream, world, local, alu_peak, front, 
     return out
 
 
+def indirect_side(w, F, G, local):
+    """The same operator factored from its entries alone (indirect access, Scenario 1
+    of Sec. 2.2): amplitude by Algorithm 1 on |K|, phase by Algorithms 3-5, on the
+    host.  One FP32 apply of it is compared with the table apply's G."""
+    import torch
+    from paper_1803_04128_gb300 import api
+    N = w["N"]
+    t0 = time.perf_counter()
+    pi = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
+                  indirect=True)
+    t_factor = time.perf_counter() - t0
+    Gi = torch.empty_like(F)
+    pi.apply(F, Gi, api.F32)
+    torch.cuda.synchronize()
+    assert pi.sync_status() == 0
+    info = pi.info()
+    pi.close()
+    return {"t_recover_s": round(info["t_recover_s"], 3), "t_factor_s": round(t_factor, 3),
+            "phase_rank": info["phase_rank"], "recover_err_k": info["recover_err_k"],
+            "recover_err_amp": info["recover_err_amp"],
+            "rel_diff_vs_table_apply": float((Gi - G).norm() / G.norm()),
+            "note": "t_recover_s: host recovery of amplitude and phase from kernel entries (part of t_factor_s, "
+                    "which adds the butterfly construction); recover_err_k/amp: eps^K, eps^amp of Sec. 5 on "
+                    "256 x 256 sampled entries"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -562,6 +592,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-indirect-side", action="store_true",
+                    help="skip the plan factored from kernel entries alone (indirect access)")
     ap.add_argument("--otf", action="store_true",
                     help="time the on-the-fly plan (bf_factor_otf, FP32 only) as the main line")
     ap.add_argument("--no-otf-side", action="store_true",
@@ -745,6 +777,9 @@ def main():
     otf = None
     if prec == api.F32 and not args.otf and not args.no_otf_side:
         otf = otf_side(args, w, plan, F, G, flush, stream, world, local, alu_peak, front, back)
+    ind = None
+    if prec == api.F32 and not args.otf and not args.no_indirect_side and w["N"] > 0:
+        ind = indirect_side(w, F, G, local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -773,6 +808,8 @@ def main():
                 "clocks": clk.summary()}
         if otf is not None:
             line["on_the_fly"] = otf
+        if ind is not None:
+            line["indirect"] = ind
         print(json.dumps(line))
     plan.close()
     if world > 1:

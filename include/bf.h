@@ -68,7 +68,9 @@ typedef enum {
     BF_PHASE_FIO_PW = 2,  /* x xi + c|xi| for x < 1/2; x xi - c|xi|/2 for x >= 1/2      */
     BF_PHASE_ONES = 3,    /* 0                                                            */
     BF_PHASE_SEP = 4,     /* 0.3 sin(2 pi x) + xi^2/(4N)  (R(A,B) of Eq. RAB vanishes)    */
-    BF_PHASE_USER = 100   /* Phi given by the phi callback                               */
+    BF_PHASE_USER = 100,  /* Phi given by the phi callback                               */
+    BF_PHASE_ENTRIES = 101 /* K known only through its entries (the entry callback): the    *
+                            * amplitude and the phase are recovered (bf_options.indirect)  */
 } bf_phase_kind;
 
 /* Built-in amplitudes alpha(x, xi). */
@@ -92,6 +94,9 @@ typedef struct {
     bf_phase_fn phi;      /* used when phase_kind == BF_PHASE_USER              */
     bf_amp_fn alpha;      /* used when amp_kind == BF_AMP_USER                  */
     void* user;           /* passed to the callbacks                            */
+    bf_amp_fn entry;      /* used when phase_kind == BF_PHASE_ENTRIES: writes    *
+                           * K(x, xi) = alpha e^{2 pi i Phi}, alpha > 0 assumed; *
+                           * amp_kind is then ignored                            */
 } bf_kernel_desc;
 
 typedef struct {
@@ -105,6 +110,18 @@ typedef struct {
     uint64_t seed;        /* sampling seed of Algorithm 1 (default 0)                      */
     int keep_host;        /* keep the FP64 host factors after upload (default 1)           */
     int device;           /* CUDA device of the plan (default 0)                           */
+    /* Indirect access (Scenario 1 of Table sc, Sec. 2.2).  With indirect = 1 (implied by
+     * BF_PHASE_ENTRIES) bf_factor sees K only through its entries: built-in kinds are
+     * evaluated as a black box.  It recovers the amplitude by Algorithm 1 on |K| and a
+     * low-rank phase Psi, e^{2 pi i Psi} = K/|K|, by Algorithms 3-5.  It then builds
+     * the butterfly of Sec. 4 from those factors.  Such plans are factored on the host
+     * only (bf_factor). */
+    int indirect;         /* 0 (default) or 1                                                 */
+    int phase_rank;       /* rank parameter of the phase's Algorithm 1 step (default 20)      */
+    int phase_oversample; /* its oversampling q (default 5)                                   */
+    double phase_tol;     /* relative singular-value cut of the recovered phase (default 1e-13) */
+    double tau;           /* discontinuity threshold of Algorithm 3 on second differences of  *
+                           * Phi in turns (default 0.25: pi/2 of the phase 2 pi Phi)           */
 } bf_options;
 
 typedef struct {
@@ -118,10 +135,28 @@ typedef struct {
     int64_t dev_bytes_bf16;/* device hi/lo BF16 copies of the level matrices                */
     int uploaded;
     double amp_sigma_ratio;/* sigma_{r_alpha+1}/sigma_1 of the amplitude (0 if exact)        */
+    /* indirect plans (0 otherwise), each the maximum over the sub-BFs: */
+    int phase_rank;        /* rank of the recovered phase Psi                                */
+    double t_recover_s;    /* host seconds recovering amplitude and phase (Algorithms 1, 3-5) */
+    double recover_err_k;  /* eps^K of Sec. 5: 2-norm error of the kernel rebuilt from the    *
+                            * recovered factors against K on 256 x 256 sampled entries,        *
+                            * relative to K's                                                  */
+    double recover_err_amp;/* eps^amp of Sec. 5, the same for the amplitude against |K|      */
 } bf_plan_info;
 
 /* Fill *opt with the defaults listed above. */
 bf_status bf_default_options(bf_options* opt);
+
+/* Algorithm 3 (Sec. 2.2) on the host: rebuilds v from u = v mod 1 (u in [0, 1), n
+ * entries), with the first nseed (0..3) values of v given in seed.  The first value
+ * is u[0]; the second is the one nearest the first; the third keeps the first
+ * difference; every later one makes the third difference smallest.  A second
+ * difference above tau (turns) starts a new piece there.  v is u plus integers.
+ * starts receives the start index of every piece (starts[0] = 0), at most cap of
+ * them; *nstarts is their total count.  Errors: BF_ERR_ARG (n < 0, nseed outside
+ * 0..3 or above n, NULL u/v/nstarts, starts NULL with cap > 0). */
+bf_status bf_unwrap(const double* u, int64_t n, double tau, const double* seed, int nseed, double* v,
+                    int64_t* starts, int64_t cap, int64_t* nstarts);
 
 /* Create a plan for the operator *desc to tolerance eps (the target relative
  * l2 error eps^b of Sec. 5).  With opt->r == 0 the interpolation rank is taken

@@ -17,7 +17,7 @@ STATUS_NAMES = ["BF_OK", "BF_ERR_ARG", "BF_ERR_NOMEM", "BF_ERR_CUDA", "BF_ERR_ST
                 "BF_ERR_ACCURACY", "BF_ERR_IO", "BF_ERR_UNSUPPORTED"]
 
 PREC_F64, PREC_F32, PREC_BF16X3 = 0, 1, 2
-PHASE_DFT, PHASE_FIO, PHASE_FIO_PW, PHASE_ONES, PHASE_SEP, PHASE_USER = 0, 1, 2, 3, 4, 100
+PHASE_DFT, PHASE_FIO, PHASE_FIO_PW, PHASE_ONES, PHASE_SEP, PHASE_USER, PHASE_ENTRIES = 0, 1, 2, 3, 4, 100, 101
 AMP_ONE, AMP_SMOOTH, AMP_USER = 0, 1, 100
 
 PHASE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
@@ -27,13 +27,16 @@ AMP_FN = ctypes.CFUNCTYPE(None, ctypes.c_double, ctypes.c_double, ctypes.c_void_
 
 class KernelDesc(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("phase_kind", ctypes.c_int), ("phase_param", ctypes.c_double),
-                ("amp_kind", ctypes.c_int), ("phi", PHASE_FN), ("alpha", AMP_FN), ("user", ctypes.c_void_p)]
+                ("amp_kind", ctypes.c_int), ("phi", PHASE_FN), ("alpha", AMP_FN), ("user", ctypes.c_void_p),
+                ("entry", AMP_FN)]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int), ("n0", ctypes.c_int), ("split", ctypes.c_int),
                 ("amp_rank", ctypes.c_int), ("amp_oversample", ctypes.c_int), ("amp_tol", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("keep_host", ctypes.c_int), ("device", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("keep_host", ctypes.c_int), ("device", ctypes.c_int),
+                ("indirect", ctypes.c_int), ("phase_rank", ctypes.c_int), ("phase_oversample", ctypes.c_int),
+                ("phase_tol", ctypes.c_double), ("tau", ctypes.c_double)]
 
 
 class BatchItem(ctypes.Structure):
@@ -62,7 +65,9 @@ class PlanInfo(ctypes.Structure):
                 ("h", ctypes.c_int), ("l1", ctypes.c_int), ("r_alpha", ctypes.c_int), ("split", ctypes.c_int),
                 ("host_bytes", ctypes.c_int64), ("dev_bytes_f64", ctypes.c_int64),
                 ("dev_bytes_f32", ctypes.c_int64), ("dev_bytes_bf16", ctypes.c_int64),
-                ("uploaded", ctypes.c_int), ("amp_sigma_ratio", ctypes.c_double)]
+                ("uploaded", ctypes.c_int), ("amp_sigma_ratio", ctypes.c_double),
+                ("phase_rank", ctypes.c_int), ("t_recover_s", ctypes.c_double), ("recover_err_k", ctypes.c_double),
+                ("recover_err_amp", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -87,6 +92,8 @@ _SIGS = {
     "bf_destroy": (None, [_P]),
     "bf_grid_indices": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int)]),
+    "bf_unwrap": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, ctypes.c_int, _P, _P, ctypes.c_int64,
+                                 ctypes.POINTER(ctypes.c_int64)]),
     "bf_last_error": (ctypes.c_char_p, []),
     "bf_profile_begin": (ctypes.c_int, []),
     "bf_profile_end": (ctypes.c_int, []),

@@ -27,6 +27,18 @@ def default_options():
     return o
 
 
+def unwrap(u, tau=0.25, seed=()):
+    """Algorithm 3 (bf_unwrap): (v, starts) with v = u + integers, from u = v mod 1."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    sd = np.ascontiguousarray(seed, dtype=np.float64)
+    v = np.empty_like(u)
+    starts = np.zeros(max(16, u.size // 2 + 1), dtype=np.int64)
+    cnt = ctypes.c_int64()
+    L.check(L.lib().bf_unwrap(u.ctypes.data, u.size, tau, sd.ctypes.data if sd.size else None, sd.size,
+                              v.ctypes.data, starts.ctypes.data, starts.size, ctypes.byref(cnt)), "bf_unwrap")
+    return v, [int(t) for t in starts[:cnt.value]]
+
+
 def _stream_ptr(stream):
     if stream is None:
         import torch
@@ -41,7 +53,10 @@ class Plan:
 
     def __init__(self, N, eps=1e-6, phase_kind=L.PHASE_FIO, phase_param=1.0, amp_kind=L.AMP_ONE,
                  r=0, n0=1, split=1, seed=0, keep_host=True, device=0, factor=True, phi=None, alpha=None,
-                 factor_on_device=False, on_the_fly=False, _handle=None):
+                 factor_on_device=False, on_the_fly=False, indirect=False, entry=None, _handle=None):
+        """``indirect``: factor from the kernel's entries alone (amplitude and phase
+        recovered, Algorithms 1 and 3-5); ``entry(x, xi) -> complex`` gives K when the
+        kernel has no built-in kind (implies indirect)."""
         self._lib = L.lib()
         self._h = ctypes.c_void_p()
         self._keep = []
@@ -64,8 +79,17 @@ class Plan:
                 cb2 = L.AMP_FN(_amp)
                 self._keep.append(cb2)
                 d.alpha = cb2
+            if entry is not None:
+                def _ent(x, xi, u, re, im):
+                    v = complex(entry(x, xi))
+                    re[0], im[0] = v.real, v.imag
+                cb3 = L.AMP_FN(_ent)
+                self._keep.append(cb3)
+                d.entry = cb3
+                d.phase_kind = L.PHASE_ENTRIES
             o = default_options()
             o.r, o.n0, o.split, o.seed, o.keep_host, o.device = r, n0, split, seed, int(keep_host), device
+            o.indirect = int(indirect or entry is not None)
             L.check(self._lib.bf_plan_create(ctypes.byref(d), eps, ctypes.byref(o), ctypes.byref(self._h)),
                     "bf_plan_create")
             if on_the_fly:

@@ -28,6 +28,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <omp.h>
+
 #include "bf_internal.h"
 
 namespace bfi {
@@ -40,7 +42,45 @@ static int64_t mod_pos(int64_t a, int64_t n)
     return r < 0 ? r + n : r;
 }
 
+static inline cd expi(double frac) { return cd(std::cos(kTwoPi * frac), std::sin(kTwoPi * frac)); }
+
+double PhaseLR::value(int64_t i, int64_t j) const
+{
+    const int64_t il = i - row0, jl = j - col0;
+    double v = 0.0;
+    for (int k = 0; k < rank; ++k) {
+        const cd a = p[(size_t)k * N + il], b = q[(size_t)k * N + jl];
+        v += a.real() * b.real() - a.imag() * b.imag();
+    }
+    return v;
+}
+
 double KernelFn::phase_frac(int64_t i, int64_t j) const
+{
+    if (indirect) {
+        double t = lr ? lr->value(i, j) : std::arg(entry(i, j)) / kTwoPi;
+        t -= std::floor(t);
+        return t - std::nearbyint(t);
+    }
+    return phase_frac_explicit(i, j);
+}
+
+cd KernelFn::amplitude(int64_t i, int64_t j) const
+{
+    return indirect ? cd(std::abs(entry(i, j))) : amplitude_explicit(i, j);
+}
+
+cd KernelFn::entry(int64_t i, int64_t j) const
+{
+    if (d.phase_kind == BF_PHASE_ENTRIES) {
+        double re = 0, im = 0;
+        d.entry((double)i / (double)n_global, (double)(j - n_global / 2), d.user, &re, &im);
+        return cd(re, im);
+    }
+    return amplitude_explicit(i, j) * expi(phase_frac_explicit(i, j));
+}
+
+double KernelFn::phase_frac_explicit(int64_t i, int64_t j) const
 {
     const int64_t Ng = n_global;
     const int64_t xi = j - Ng / 2;
@@ -79,6 +119,7 @@ double KernelFn::phase_frac(int64_t i, int64_t j) const
 
 bool KernelFn::row_terms(int64_t i, double* kappa, double* rho, int* xxi, int* sq) const
 {
+    if (indirect) return false;
     const double x = (double)i / (double)n_global;
     const double s = d.phase_param;
     *kappa = *rho = 0.0;
@@ -108,7 +149,7 @@ bool KernelFn::row_terms(int64_t i, double* kappa, double* rho, int* xxi, int* s
     }
 }
 
-cd KernelFn::amplitude(int64_t i, int64_t j) const
+cd KernelFn::amplitude_explicit(int64_t i, int64_t j) const
 {
     const int64_t Ng = n_global;
     const double x = (double)i / (double)Ng;
@@ -125,8 +166,6 @@ cd KernelFn::amplitude(int64_t i, int64_t j) const
     }
     }
 }
-
-static inline cd expi(double frac) { return cd(std::cos(kTwoPi * frac), std::sin(kTwoPi * frac)); }
 
 // ---------------------------------------------------------------------------
 std::vector<int64_t> grid_rel(int64_t n, int r)
@@ -179,7 +218,6 @@ size_t BlockFactors::host_bytes() const
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 1 on the amplitude window [row0, row0+N) x [col0, col0+N).
 namespace {
 struct SplitMix {
     uint64_t s;
@@ -210,30 +248,16 @@ std::vector<int64_t> sample_union(SplitMix& rng, int64_t n, int64_t k, const std
 }
 }  // namespace
 
-bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0, int64_t col0,
-                          int64_t N, std::vector<cd>& a, std::vector<cd>& b, int& ra,
+// Algorithm 1 (Sec. 2.1) on an N x N matrix seen through entries(I, J) (the submatrix)
+// and entries_adj(I, J) (its adjoint): a = U0 Sigma0 and b = V0^* as [rank][N], with the
+// rank cut at the singular values above tol * sigma_1.  seed_state starts the sampler.
+bf_status lowrank_sampled(const EntriesFn& entries, const EntriesFn& entries_adj, int64_t N, int r, int q,
+                          double tol, uint64_t seed_state, std::vector<cd>& a, std::vector<cd>& b, int& rank,
                           double& sigma_ratio)
 {
-    const int r = std::max(1, opt.amp_rank);
-    const int64_t rq = (int64_t)r * std::max(1, opt.amp_oversample);
-    SplitMix rng{opt.seed * 0x9E3779B97F4A7C15ull + 12345};
-    auto entries = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J) {
-        CMat M((int64_t)I.size(), (int64_t)J.size());
-#pragma omp parallel for schedule(static)
-        for (int64_t jj = 0; jj < (int64_t)J.size(); ++jj)
-            for (size_t ii = 0; ii < I.size(); ++ii)
-                M((int64_t)ii, jj) = k.amplitude(row0 + I[ii], col0 + J[(size_t)jj]);
-        return M;
-    };
-    // adjoint(entries(I, J)) built directly, in parallel over the rows I
-    auto entries_adj = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J) {
-        CMat M((int64_t)J.size(), (int64_t)I.size());
-#pragma omp parallel for schedule(static)
-        for (int64_t ii = 0; ii < (int64_t)I.size(); ++ii)
-            for (size_t jj = 0; jj < J.size(); ++jj)
-                M((int64_t)jj, ii) = std::conj(k.amplitude(row0 + I[(size_t)ii], col0 + J[jj]));
-        return M;
-    };
+    r = std::max(1, r);
+    const int64_t rq = (int64_t)r * std::max(1, q);
+    SplitMix rng{seed_state};
     std::vector<int64_t> all((size_t)N);
     for (int64_t i = 0; i < N; ++i) all[(size_t)i] = i;
     std::vector<int64_t> pi_col, pi_row, piv;
@@ -254,8 +278,8 @@ bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0
     CMat Qc, Qr;
     int kc = pivoted_qr(entries(all, pi_col), r, qr_tol, Qc, piv);
     int kr = pivoted_qr(entries_adj(pi_row, all), r, qr_tol, Qr, piv);
-    if (kc == 0 || kr == 0) {  // zero amplitude
-        ra = 0;
+    if (kc == 0 || kr == 0) {  // zero matrix
+        rank = 0;
         a.clear();
         b.clear();
         sigma_ratio = 0;
@@ -273,19 +297,45 @@ bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0
     std::vector<double> SM;
     jacobi_svd(M, UM, SM, VM);
     int keep = 0;
-    const double tol = opt.amp_tol > 0 ? opt.amp_tol : 1e-13;
     while (keep < (int)SM.size() && SM[(size_t)keep] > tol * SM[0]) ++keep;
     sigma_ratio = keep < (int)SM.size() ? SM[(size_t)keep] / SM[0] : 0.0;
-    ra = keep;
+    rank = keep;
     CMat U0 = matmul(Qc, UM), V0 = matmul(Qr, VM);
-    a.assign((size_t)(ra * N), cd(0));
-    b.assign((size_t)(ra * N), cd(0));
-    for (int kk = 0; kk < ra; ++kk)
+    a.assign((size_t)(rank * N), cd(0));
+    b.assign((size_t)(rank * N), cd(0));
+    for (int kk = 0; kk < rank; ++kk)
         for (int64_t i = 0; i < N; ++i) {
             a[(size_t)(kk * N + i)] = U0(i, kk) * SM[(size_t)kk];
             b[(size_t)(kk * N + i)] = std::conj(V0(i, kk));
         }
     return BF_OK;
+}
+
+// Algorithm 1 on the amplitude window [row0, row0+N) x [col0, col0+N).
+bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0, int64_t col0,
+                          int64_t N, std::vector<cd>& a, std::vector<cd>& b, int& ra,
+                          double& sigma_ratio)
+{
+    auto entries = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J) {
+        CMat M((int64_t)I.size(), (int64_t)J.size());
+#pragma omp parallel for schedule(static)
+        for (int64_t jj = 0; jj < (int64_t)J.size(); ++jj)
+            for (size_t ii = 0; ii < I.size(); ++ii)
+                M((int64_t)ii, jj) = k.amplitude(row0 + I[ii], col0 + J[(size_t)jj]);
+        return M;
+    };
+    // adjoint(entries(I, J)) built directly, in parallel over the rows I
+    auto entries_adj = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J) {
+        CMat M((int64_t)J.size(), (int64_t)I.size());
+#pragma omp parallel for schedule(static)
+        for (int64_t ii = 0; ii < (int64_t)I.size(); ++ii)
+            for (size_t jj = 0; jj < J.size(); ++jj)
+                M((int64_t)jj, ii) = std::conj(k.amplitude(row0 + I[(size_t)ii], col0 + J[jj]));
+        return M;
+    };
+    return lowrank_sampled(entries, entries_adj, N, opt.amp_rank, opt.amp_oversample,
+                           opt.amp_tol > 0 ? opt.amp_tol : 1e-13, opt.seed * 0x9E3779B97F4A7C15ull + 12345, a, b,
+                           ra, sigma_ratio);
 }
 
 // ---------------------------------------------------------------------------
@@ -306,7 +356,9 @@ bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B
     const int64_t P = N / n0;
     auto F = [&](int64_t i, int64_t j) { return k.phase_frac(B.row0 + i, B.col0 + j); };
 
+    const double t0 = omp_get_wtime();
     bf_status st = amplitude_split(k, opt, B.row0, B.col0, N, B.a, B.b, B.ra, B.amp_sigma_ratio);
+    B.t_amp = omp_get_wtime() - t0;
     if (st != BF_OK) return st;
 
     // V at level l1 (Eq. 1 with the copy levels 1..l1-1 folded in)

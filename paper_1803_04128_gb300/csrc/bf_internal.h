@@ -2,6 +2,7 @@
 #pragma once
 
 #include <complex>
+#include <functional>
 #include <map>
 #include <cstdint>
 #include <string>
@@ -16,16 +17,35 @@ using cd = std::complex<double>;
 void set_error(const char* fmt, ...);
 
 // ---------------------------------------------------------------------------
+// A phase recovered from kernel entries on one sub-BF window (Algorithm 5):
+// Psi(row0 + i, col0 + j) = Re sum_k p[k][i] q[k][j], with e^{2 pi i Psi} = e^{2 pi i Phi}.
+struct PhaseLR {
+    int64_t row0 = 0, col0 = 0, N = 0;
+    int rank = 0;
+    std::vector<cd> p, q;  // [rank][N]
+    double value(int64_t i, int64_t j) const;  // global indices
+};
+
 // The operator: entries of alpha and of e^{2 pi i Phi} at global grid indices.
 struct KernelFn {
     bf_kernel_desc d{};
     int64_t n_global = 0;  // grid size of x_i = i/n_global, xi_j = j - n_global/2
+    // Indirect access (Scenario 1): the construction sees K only through entry();
+    // amplitude() is then |K| and phase_frac() the recovered phase lr (per sub-BF window).
+    bool indirect = false;
+    const PhaseLR* lr = nullptr;
     // Phi(x_i, xi_j) reduced mod 1 (exactly for the built-in kinds).
     double phase_frac(int64_t i, int64_t j) const;
     // For the built-in kinds, phase_frac(i, j) = xxi (i xi mod Ng) / Ng + kappa_i |xi| + rho_i
-    // + sq (xi^2 mod 4 Ng) / (4 Ng) mod 1 (xi = j - Ng/2); false for user phases.
+    // + sq (xi^2 mod 4 Ng) / (4 Ng) mod 1 (xi = j - Ng/2); false for user phases and
+    // indirect plans.
     bool row_terms(int64_t i, double* kappa, double* rho, int* xxi, int* sq) const;
     cd amplitude(int64_t i, int64_t j) const;
+    // K(x_i, xi_j): the entry callback (BF_PHASE_ENTRIES) or the explicit alpha e^{2 pi i Phi}
+    cd entry(int64_t i, int64_t j) const;
+    // the explicit definitions (kinds and callbacks of d), whatever indirect says
+    double phase_frac_explicit(int64_t i, int64_t j) const;
+    cd amplitude_explicit(int64_t i, int64_t j) const;
 };
 
 // ---------------------------------------------------------------------------
@@ -48,6 +68,10 @@ struct BlockFactors {
     std::vector<double> MU;               // [nu][r]
     std::vector<cd> EU;                   // [2^l1][N]
     double amp_sigma_ratio = 0.0;
+    double t_amp = 0.0;  // host seconds of the amplitude split
+    // indirect plans: the recovered phase and the recovery's accuracy and time
+    PhaseLR lr;
+    double t_recover = 0.0, recover_err_k = 0.0, recover_err_amp = 0.0;
     int64_t P() const { return N / n0; }
     int nH() const { return h - l1; }
     int nG() const { return L - l1 - h; }
@@ -111,6 +135,20 @@ void jacobi_svd(const CMat& A, CMat& U, std::vector<double>& S, CMat& V);
 CMat pinv(const CMat& A, double rcond);
 CMat matmul(const CMat& A, const CMat& B);
 CMat adjoint(const CMat& A);
+
+// Algorithm 1 (Sec. 2.1) on an N x N matrix seen through submatrices: entries(I, J) and
+// its adjoint entries_adj(I, J) (then J x I); a = U0 Sigma0, b = V0^* as [rank][N]
+using EntriesFn = std::function<CMat(const std::vector<int64_t>&, const std::vector<int64_t>&)>;
+bf_status lowrank_sampled(const EntriesFn& entries, const EntriesFn& entries_adj, int64_t N, int r, int q,
+                          double tol, uint64_t seed_state, std::vector<cd>& a, std::vector<cd>& b, int& rank,
+                          double& sigma_ratio);
+// indirect access (bf_recover.cpp): Algorithm 3 on one vector, and the phase of one
+// sub-BF window by Algorithms 3-5; recovery_errors fills eps^K and eps^amp of Sec. 5
+void unwrap(const double* u, int64_t n, double tau, const double* seed, int nseed, double* v,
+            std::vector<int64_t>* starts);
+bf_status recover_phase(const KernelFn& k, const bf_options& opt, int64_t row0, int64_t col0, int64_t N,
+                        PhaseLR& lr);
+void recovery_errors(const KernelFn& k, BlockFactors& B, uint64_t seed);
 
 // device side (bf_device.cu)
 bf_status device_upload(bf_plan* p);

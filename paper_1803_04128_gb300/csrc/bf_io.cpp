@@ -145,7 +145,8 @@ bf_status bf_plan_load(const char* path, const bf_options* opt, bf_plan** out)
     p->kern.d.amp_kind = rd.val<int32_t>();
     p->kern.n_global = p->N;
     p->eps = rd.val<double>();
-    p->user_kinds_lost = p->kern.d.phase_kind == BF_PHASE_USER || p->kern.d.amp_kind == BF_AMP_USER;
+    p->user_kinds_lost = p->kern.d.phase_kind == BF_PHASE_USER || p->kern.d.amp_kind == BF_AMP_USER ||
+                         p->kern.d.phase_kind == BF_PHASE_ENTRIES;
     uint32_t nb = rd.val<uint32_t>();
     try {
         if (!rd.ok || nb > 4) throw std::bad_alloc();

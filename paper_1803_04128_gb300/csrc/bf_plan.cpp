@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 
+#include <omp.h>
+
 #include "bf_internal.h"
 
 namespace bfi {
@@ -45,6 +47,11 @@ bf_status bf_default_options(bf_options* opt)
     opt->seed = 0;
     opt->keep_host = 1;
     opt->device = 0;
+    opt->indirect = 0;
+    opt->phase_rank = 20;
+    opt->phase_oversample = 5;
+    opt->phase_tol = 1e-13;
+    opt->tau = 0.25;
     return BF_OK;
 }
 
@@ -73,6 +80,10 @@ bf_status bf_plan_create(const bf_kernel_desc* desc, double eps, const bf_option
     if (o.split <= 0) o.split = 1;
     if (o.amp_rank <= 0) o.amp_rank = 8;
     if (o.amp_oversample <= 0) o.amp_oversample = 3;
+    if (o.phase_rank <= 0) o.phase_rank = 20;
+    if (o.phase_oversample <= 0) o.phase_oversample = 5;
+    if (!(o.phase_tol > 0)) o.phase_tol = 1e-13;
+    if (!(o.tau > 0)) o.tau = 0.25;
     const int64_t N = desc->N;
     if (N < 4 || (N & (N - 1)) != 0) {
         set_error("bf_plan_create: N=%lld is not a power of two >= 4", (long long)N);
@@ -91,11 +102,12 @@ bf_status bf_plan_create(const bf_kernel_desc* desc, double eps, const bf_option
         return BF_ERR_ARG;
     }
     int pk = desc->phase_kind, ak = desc->amp_kind;
-    if (!(pk >= 0 && pk <= 4) && !(pk == BF_PHASE_USER && desc->phi)) {
-        set_error("bf_plan_create: bad phase_kind %d (or missing phi callback)", pk);
+    const bool entries = pk == BF_PHASE_ENTRIES;
+    if (!(pk >= 0 && pk <= 4) && !(pk == BF_PHASE_USER && desc->phi) && !(entries && desc->entry)) {
+        set_error("bf_plan_create: bad phase_kind %d (or missing phi / entry callback)", pk);
         return BF_ERR_ARG;
     }
-    if (!(ak == 0 || ak == 1) && !(ak == BF_AMP_USER && desc->alpha)) {
+    if (!entries && !(ak == 0 || ak == 1) && !(ak == BF_AMP_USER && desc->alpha)) {
         set_error("bf_plan_create: bad amp_kind %d (or missing alpha callback)", ak);
         return BF_ERR_ARG;
     }
@@ -126,6 +138,7 @@ bf_status bf_plan_create(const bf_kernel_desc* desc, double eps, const bf_option
     p->kern.d = *desc;
     if (p->kern.d.phase_param == 0.0) p->kern.d.phase_param = 1.0;
     p->kern.n_global = N;
+    p->kern.indirect = entries || o.indirect != 0;
     p->opt = o;
     p->eps = eps;
     p->N = N;
@@ -161,8 +174,22 @@ bf_status bf_factor(bf_plan* p)
                 B.col0 = ch * Nb;
                 B.r = p->r;
                 B.n0 = p->n0;
-                bf_status st = factor_block(p->kern, p->opt, B);
+                // indirect access: the phase of this window recovered from entries first
+                // (Algorithms 3-5); the amplitude split inside factor_block then runs on |K|
+                bfi::KernelFn kb = p->kern;
+                if (kb.indirect) {
+                    const double t0 = omp_get_wtime();
+                    bf_status rs = bfi::recover_phase(kb, p->opt, B.row0, B.col0, Nb, B.lr);
+                    B.t_recover = omp_get_wtime() - t0;
+                    if (rs != BF_OK) return rs;
+                    kb.lr = &B.lr;
+                }
+                bf_status st = factor_block(kb, p->opt, B);
                 if (st != BF_OK) return st;
+                if (kb.indirect) {
+                    B.t_recover += B.t_amp;
+                    bfi::recovery_errors(kb, B, p->opt.seed);
+                }
             }
     } catch (const std::bad_alloc&) {
         p->blocks.clear();
@@ -218,8 +245,9 @@ bf_status bf_factor_device(bf_plan* p)
         set_error("bf_factor_device: plan was loaded without its callbacks");
         return BF_ERR_STATE;
     }
-    if (!bfi::construct_supported(p->kern.d.phase_kind)) {
-        set_error("bf_factor_device: phase kind %d has no device form (use bf_factor)", p->kern.d.phase_kind);
+    if (!bfi::construct_supported(p->kern.d.phase_kind) || p->kern.indirect) {
+        set_error("bf_factor_device: phase kind %d%s has no device form (use bf_factor)", p->kern.d.phase_kind,
+                  p->kern.indirect ? " seen through its entries" : "");
         return BF_ERR_UNSUPPORTED;
     }
     const bf_status hs = factor_host_parts(p, "bf_factor_device");
@@ -247,8 +275,9 @@ bf_status bf_factor_otf(bf_plan* p)
         set_error("bf_factor_otf: plan was loaded without its callbacks");
         return BF_ERR_STATE;
     }
-    if (!bfi::construct_supported(p->kern.d.phase_kind)) {
-        set_error("bf_factor_otf: phase kind %d has no closed form on the device", p->kern.d.phase_kind);
+    if (!bfi::construct_supported(p->kern.d.phase_kind) || p->kern.indirect) {
+        set_error("bf_factor_otf: phase kind %d%s has no closed form on the device", p->kern.d.phase_kind,
+                  p->kern.indirect ? " seen through its entries" : "");
         return BF_ERR_UNSUPPORTED;
     }
     const bf_status hs = factor_host_parts(p, "bf_factor_otf");
@@ -353,6 +382,12 @@ bf_status bf_plan_get_info(const bf_plan* p, bf_plan_info* info)
         info->r_alpha = ra;
         info->amp_sigma_ratio = sr;
         info->host_bytes = hb;
+        for (auto& B : p->blocks) {
+            info->phase_rank = std::max(info->phase_rank, B.lr.rank);
+            info->t_recover_s += B.t_recover;
+            info->recover_err_k = std::max(info->recover_err_k, B.recover_err_k);
+            info->recover_err_amp = std::max(info->recover_err_amp, B.recover_err_amp);
+        }
     }
     device_info(p, info);
     return BF_OK;

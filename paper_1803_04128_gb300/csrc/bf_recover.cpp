@@ -1,0 +1,321 @@
+// Indirect access (Scenario 1 of Table sc, Sec. 2.2): the amplitude and phase of K
+// recovered from its entries alone, off the timed path.
+//
+//  * unwrap: Algorithm 3.  A vector v is rebuilt from u = v mod 1: the first entry
+//    is u itself, the second the one nearest the first, the third keeps the first
+//    difference, every later one makes the third difference smallest; a second
+//    difference above tau starts a new smooth piece.
+//  * PsiSampler: Algorithm 4 on one sub-BF window.  The discontinuities of one
+//    column and one row cut the window into blocks.  In each block the first row
+//    is unwrapped.  Then the first three columns are unwrapped along x: the first
+//    from the first row's value, the next two through their differences with the
+//    column before, so the three stay continuous along every row.  Every row
+//    continues from its values in those three columns, and every column from its
+//    values in the block's first three rows.  So any row or column of one Psi,
+//    with e^{2 pi i Psi} = K / |K|, can be rebuilt on demand, and rows and
+//    columns agree where they cross.
+//  * recover_phase: Algorithm 5.  Algorithm 1 (lowrank_sampled) runs on Psi
+//    through the sampler and gives Psi ~ Re sum_k p_k(x) q_k(xi).
+// The amplitude is Algorithm 1 on |K| (amplitude_split with KernelFn::indirect).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <omp.h>
+
+#include "bf_internal.h"
+
+namespace bfi {
+
+namespace {
+
+const double kTwoPi = 6.283185307179586476925286766559;
+
+struct Mix64 {  // splitmix64 (Steele, Lea, Flood 2014)
+    uint64_t s;
+    uint64_t next()
+    {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+};
+
+// One sub-BF window [row0, row0 + N) x [col0, col0 + N) of Psi, Algorithm 4.
+class PsiSampler {
+  public:
+    PsiSampler(const KernelFn& k, int64_t row0, int64_t col0, int64_t N, int64_t cfirst, int64_t rfirst,
+               double tau, double tau_block)
+        : k_(k), row0_(row0), col0_(col0), N_(N), tb_(tau_block)
+    {
+        std::vector<double> u((size_t)N), v((size_t)N);
+        // discontinuities along one column (row cuts) and one row (column cuts)
+        for (int64_t i = 0; i < N; ++i) u[(size_t)i] = turns(i, cfirst);
+        unwrap(u.data(), N, tau, nullptr, 0, v.data(), &rb_);
+        for (int64_t j = 0; j < N; ++j) u[(size_t)j] = turns(rfirst, j);
+        unwrap(u.data(), N, tau, nullptr, 0, v.data(), &cb_);
+        rb_.push_back(N);
+        cb_.push_back(N);
+        const int nbr = (int)rb_.size() - 1, nbc = (int)cb_.size() - 1;
+        colseed_.assign((size_t)(nbr * nbc), {});
+        rowseed_.assign((size_t)(nbr * nbc), {});
+        for (int bi = 0; bi < nbr; ++bi)
+            for (int bj = 0; bj < nbc; ++bj) {
+                const int64_t r0 = rb_[(size_t)bi], r1 = rb_[(size_t)bi + 1];
+                const int64_t c0 = cb_[(size_t)bj], c1 = cb_[(size_t)bj + 1];
+                const int64_t nr = r1 - r0, ncb = c1 - c0;
+                // the block's first row
+                std::vector<double> ur((size_t)ncb), first((size_t)ncb);
+                for (int64_t j = 0; j < ncb; ++j) ur[(size_t)j] = turns(r0, c0 + j);
+                unwrap(ur.data(), ncb, tb_, nullptr, 0, first.data(), nullptr);
+                // its first three columns along x
+                const int nc = (int)std::min<int64_t>(3, ncb);
+                std::vector<double>& cs = colseed_[(size_t)(bi * nbc + bj)];
+                cs.assign((size_t)(nc * nr), 0.0);
+                std::vector<double> uc((size_t)(nc * nr)), dt((size_t)nr), w((size_t)nr);
+                for (int t = 0; t < nc; ++t)
+                    for (int64_t i = 0; i < nr; ++i) uc[(size_t)(t * nr + i)] = turns(r0 + i, c0 + t);
+                unwrap(uc.data(), nr, tb_, &first[0], 1, cs.data(), nullptr);
+                for (int t = 1; t < nc; ++t) {
+                    for (int64_t i = 0; i < nr; ++i) {
+                        double d = uc[(size_t)(t * nr + i)] - uc[(size_t)((t - 1) * nr + i)];
+                        dt[(size_t)i] = d - std::floor(d);
+                    }
+                    const double d0 = first[(size_t)t] - first[(size_t)t - 1];
+                    unwrap(dt.data(), nr, tb_, &d0, 1, w.data(), nullptr);
+                    for (int64_t i = 0; i < nr; ++i)
+                        cs[(size_t)(t * nr + i)] = cs[(size_t)((t - 1) * nr + i)] + w[(size_t)i];
+                }
+                // its first three rows, from those columns
+                const int nrr = (int)std::min<int64_t>(3, nr);
+                std::vector<double>& rs = rowseed_[(size_t)(bi * nbc + bj)];
+                rs.assign((size_t)(nrr * ncb), 0.0);
+                for (int t = 0; t < nrr; ++t) {
+                    for (int64_t j = 0; j < ncb; ++j) ur[(size_t)j] = turns(r0 + t, c0 + j);
+                    row_block(r0 + t, bi, bj, ur.data(), rs.data() + (size_t)t * ncb);
+                }
+            }
+    }
+
+    // local row i (N values of Psi); work: N doubles
+    void row(int64_t i, double* out, double* work) const
+    {
+        const int bi = block_of(rb_, i), nbc = (int)cb_.size() - 1;
+        for (int64_t j = 0; j < N_; ++j) work[j] = turns(i, j);
+        for (int bj = 0; bj < nbc; ++bj) {
+            const int64_t c0 = cb_[(size_t)bj];
+            row_block(i, bi, bj, work + c0, out + c0);
+        }
+    }
+
+    // local column j (N values of Psi); work: N doubles
+    void col(int64_t j, double* out, double* work) const
+    {
+        const int bj = block_of(cb_, j), nbr = (int)rb_.size() - 1, nbc = (int)cb_.size() - 1;
+        const int64_t c0 = cb_[(size_t)bj], ncb = cb_[(size_t)bj + 1] - c0;
+        for (int64_t i = 0; i < N_; ++i) work[i] = turns(i, j);
+        for (int bi = 0; bi < nbr; ++bi) {
+            const int64_t r0 = rb_[(size_t)bi], nr = rb_[(size_t)bi + 1] - r0;
+            const std::vector<double>& rs = rowseed_[(size_t)(bi * nbc + bj)];
+            const int ns = (int)(rs.size() / (size_t)ncb);
+            double seed[3];
+            for (int t = 0; t < ns; ++t) seed[t] = rs[(size_t)t * ncb + (j - c0)];
+            unwrap(work + r0, nr, tb_, seed, ns, out + r0, nullptr);
+        }
+    }
+
+  private:
+    // Phi(row0 + i, col0 + j) mod 1 in [0, 1), read off K / |K|
+    double turns(int64_t i, int64_t j) const
+    {
+        const double t = std::arg(k_.entry(row0_ + i, col0_ + j)) / kTwoPi;
+        return t - std::floor(t);
+    }
+    static int block_of(const std::vector<int64_t>& edges, int64_t x)
+    {
+        return (int)(std::upper_bound(edges.begin(), edges.end(), x) - edges.begin()) - 1;
+    }
+    // row i on block (bi, bj): u = its observations on the block's columns
+    void row_block(int64_t i, int bi, int bj, const double* u, double* out) const
+    {
+        const int nbc = (int)cb_.size() - 1;
+        const int64_t r0 = rb_[(size_t)bi], nr = rb_[(size_t)bi + 1] - r0;
+        const int64_t ncb = cb_[(size_t)bj + 1] - cb_[(size_t)bj];
+        const std::vector<double>& cs = colseed_[(size_t)(bi * nbc + bj)];
+        const int ns = (int)(cs.size() / (size_t)nr);
+        double seed[3];
+        for (int t = 0; t < ns; ++t) seed[t] = cs[(size_t)t * nr + (i - r0)];
+        unwrap(u, ncb, tb_, seed, ns, out, nullptr);
+    }
+
+    const KernelFn& k_;
+    int64_t row0_, col0_, N_;
+    double tb_;
+    std::vector<int64_t> rb_, cb_;                // block edges (last = N)
+    std::vector<std::vector<double>> colseed_;    // per block: first three columns [t][rows]
+    std::vector<std::vector<double>> rowseed_;    // per block: first three rows [t][cols]
+};
+
+// largest singular value of a small complex matrix: power iteration on A^* A from a
+// fixed start, sigma = sqrt(|A^* A x|) for the unit iterate x
+double norm2(const CMat& A)
+{
+    std::vector<cd> x((size_t)A.n), y((size_t)A.m);
+    double nx = 0;
+    for (int64_t j = 0; j < A.n; ++j) {
+        x[(size_t)j] = cd(1.0 + 0.01 * (double)(j % 7), 0.003 * (double)(j % 5));
+        nx += std::norm(x[(size_t)j]);
+    }
+    for (auto& t : x) t /= std::sqrt(nx);
+    double s = 0.0;
+    for (int it = 0; it < 200; ++it) {
+        for (int64_t i = 0; i < A.m; ++i) {
+            cd t = 0;
+            for (int64_t j = 0; j < A.n; ++j) t += A(i, j) * x[(size_t)j];
+            y[(size_t)i] = t;
+        }
+        double nz = 0;
+        for (int64_t j = 0; j < A.n; ++j) {
+            cd t = 0;
+            for (int64_t i = 0; i < A.m; ++i) t += std::conj(A(i, j)) * y[(size_t)i];
+            x[(size_t)j] = t;
+            nz += std::norm(t);
+        }
+        nz = std::sqrt(nz);
+        if (nz == 0.0) return 0.0;
+        for (auto& t : x) t /= nz;
+        const double s_new = std::sqrt(nz);
+        if (it > 5 && std::fabs(s_new - s) <= 1e-12 * s_new) return s_new;
+        s = s_new;
+    }
+    return s;
+}
+
+}  // namespace
+
+// Algorithm 3.  Compiled without FMA contraction, so that the nearest-integer choices are
+// the same on every host and as in an evaluation step by step.
+__attribute__((optimize("fp-contract=off"))) void unwrap(const double* u, int64_t n, double tau, const double* seed,
+                                                         int nseed, double* v, std::vector<int64_t>* starts)
+{
+    if (starts) {
+        starts->clear();
+        starts->push_back(0);
+    }
+    if (n <= 0) return;
+    auto near = [&](double p, int64_t a) { return u[a] + std::nearbyint(p - u[a]); };
+    v[0] = nseed >= 1 ? seed[0] : u[0];
+    if (n > 1) v[1] = nseed >= 2 ? seed[1] : near(v[0], 1);
+    if (n > 2) v[2] = nseed >= 3 ? seed[2] : near(2 * v[1] - v[0], 2);
+    int64_t a = 3;
+    while (a < n) {
+        v[a] = near(3 * v[a - 1] - 3 * v[a - 2] + v[a - 3], a);
+        if (std::fabs(v[a] + v[a - 2] - 2 * v[a - 1]) > tau) {
+            // a discontinuity: a new piece starts at a
+            if (starts) starts->push_back(a);
+            const int64_t st = a;
+            v[st] = near(v[st - 1], st);
+            if (st + 1 < n) v[st + 1] = near(2 * v[st] - v[st - 1], st + 1);
+            a = st + 2;
+            continue;
+        }
+        ++a;
+    }
+}
+
+bf_status recover_phase(const KernelFn& k, const bf_options& opt, int64_t row0, int64_t col0, int64_t N,
+                        PhaseLR& lr)
+{
+    // the column and row whose discontinuities cut the window (Algorithm 4's first samples)
+    Mix64 rng{opt.seed * 0x9E3779B97F4A7C15ull + 777};
+    const int64_t cfirst = (int64_t)(rng.next() % (uint64_t)N), rfirst = (int64_t)(rng.next() % (uint64_t)N);
+    const double tau = opt.tau > 0 ? opt.tau : 0.25;
+    PsiSampler smp(k, row0, col0, N, cfirst, rfirst, tau, 1.0);
+    // Psi[I][:, J] from whole rows (or whole columns when there are fewer of them)
+    auto fill = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J, bool adj) {
+        const int64_t ni = (int64_t)I.size(), nj = (int64_t)J.size();
+        CMat M(adj ? nj : ni, adj ? ni : nj);
+        const bool by_rows = ni <= nj;
+        const int64_t nv = by_rows ? ni : nj;
+#pragma omp parallel
+        {
+            std::vector<double> buf((size_t)N), work((size_t)N);
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t t = 0; t < nv; ++t) {
+                if (by_rows) {
+                    smp.row(I[(size_t)t], buf.data(), work.data());
+                    for (int64_t jj = 0; jj < nj; ++jj) {
+                        const double x = buf[(size_t)J[(size_t)jj]];
+                        if (adj) M(jj, t) = x; else M(t, jj) = x;
+                    }
+                } else {
+                    smp.col(J[(size_t)t], buf.data(), work.data());
+                    for (int64_t ii = 0; ii < ni; ++ii) {
+                        const double x = buf[(size_t)I[(size_t)ii]];
+                        if (adj) M(t, ii) = x; else M(ii, t) = x;
+                    }
+                }
+            }
+        }
+        return M;
+    };
+    EntriesFn ent = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J) { return fill(I, J, false); };
+    EntriesFn ent_adj = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J) { return fill(I, J, true); };
+    double sig = 0;
+    lr.row0 = row0;
+    lr.col0 = col0;
+    lr.N = N;
+    return lowrank_sampled(ent, ent_adj, N, opt.phase_rank > 0 ? opt.phase_rank : 20,
+                           opt.phase_oversample > 0 ? opt.phase_oversample : 5,
+                           opt.phase_tol > 0 ? opt.phase_tol : 1e-13, opt.seed * 0x9E3779B97F4A7C15ull + 4242, lr.p,
+                           lr.q, lr.rank, sig);
+}
+
+// eps^K and eps^amp of Sec. 5 on 256 x 256 sampled entries of the window
+void recovery_errors(const KernelFn& k, BlockFactors& B, uint64_t seed)
+{
+    const int64_t N = B.N, ns = std::min<int64_t>(N, 256);
+    Mix64 rng{seed * 0x9E3779B97F4A7C15ull + 99};
+    std::vector<int64_t> S;
+    while ((int64_t)S.size() < ns) {
+        const int64_t t = (int64_t)(rng.next() % (uint64_t)N);
+        if (std::find(S.begin(), S.end(), t) == S.end()) S.push_back(t);
+    }
+    CMat dK(ns, ns), K(ns, ns), dA(ns, ns), A(ns, ns);
+#pragma omp parallel for schedule(static)
+    for (int64_t jj = 0; jj < ns; ++jj)
+        for (int64_t ii = 0; ii < ns; ++ii) {
+            const int64_t i = B.row0 + S[(size_t)ii], j = B.col0 + S[(size_t)jj];
+            const cd kv = k.entry(i, j);
+            cd amp = 0;
+            for (int q = 0; q < B.ra; ++q)
+                amp += B.a[(size_t)q * N + S[(size_t)ii]] * B.b[(size_t)q * N + S[(size_t)jj]];
+            const double ph = kTwoPi * B.lr.value(i, j);
+            K(ii, jj) = kv;
+            dK(ii, jj) = kv - amp * cd(std::cos(ph), std::sin(ph));
+            A(ii, jj) = std::abs(kv);
+            dA(ii, jj) = std::abs(kv) - amp;
+        }
+    const double nk = norm2(K), na = norm2(A);
+    B.recover_err_k = nk > 0 ? norm2(dK) / nk : 0.0;
+    B.recover_err_amp = na > 0 ? norm2(dA) / na : 0.0;
+}
+
+}  // namespace bfi
+
+extern "C" bf_status bf_unwrap(const double* u, int64_t n, double tau, const double* seed, int nseed, double* v,
+                               int64_t* starts, int64_t cap, int64_t* nstarts)
+{
+    if (n < 0 || nseed < 0 || nseed > 3 || nseed > n || (!u && n > 0) || (!v && n > 0) || !nstarts ||
+        (nseed > 0 && !seed) || (!starts && cap > 0)) {
+        bfi::set_error("bf_unwrap: bad argument (n >= 0, 0 <= nseed <= min(3, n), non-NULL buffers)");
+        return BF_ERR_ARG;
+    }
+    std::vector<int64_t> S;
+    bfi::unwrap(u, n, tau, seed, nseed, v, &S);
+    for (int64_t t = 0; t < (int64_t)S.size() && t < cap; ++t) starts[t] = S[(size_t)t];
+    *nstarts = (int64_t)S.size();
+    return BF_OK;
+}

@@ -1,0 +1,77 @@
+"""GPU parity of plans factored from kernel entries alone (indirect access,
+Scenario 1 of Sec. 2.2: amplitude by Algorithm 1 on |K|, phase by Algorithms
+3-5), through the C ABI.
+
+The butterfly of a recovered phase is the butterfly of the kernel itself: only
+e^{2 pi i Phi} at grid points enters it, and the recovery keeps that to eps^K.
+So the tolerances are those of the explicit plans.  They are 1e-5 (FP32) and
+eps = 1e-6 (FP64) against the direct oracle of the true kernel.  Against the
+explicit plan's FP32 apply the bound is 2e-6: the FP32 rounding of the FP32
+tolerance derivation in test_gpu_parity.py, plus eps^K < 1e-7.
+"""
+import numpy as np
+import pytest
+
+from conftest import relerr
+from oracle import direct as od
+from paper_1803_04128_gb300 import _lib as L
+from paper_1803_04128_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_04128_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def run(plan, F, prec):
+    dt = torch.complex128 if prec == api.F64 else torch.complex64
+    G = plan.apply(torch.from_numpy(np.ascontiguousarray(F)).to(dt).cuda(), prec=prec)
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    return G.cpu().numpy().astype(np.complex128)
+
+
+def test_indirect_fio2_size_matches_direct_and_explicit():
+    N, m = 65536, 8
+    pi = api.Plan(N, eps=1e-6, amp_kind=L.AMP_SMOOTH, indirect=True)
+    info = pi.info()
+    assert info["phase_rank"] == 3 and info["recover_err_k"] < 1e-7
+    F = inputs.complex_gaussian(N, m, seed=41)
+    rows = inputs.sample_rows(N, 128, seed=41)
+    gd = od.direct(od.FIO, N, F, rows, amp=1)
+    g32 = run(pi, F, api.F32)
+    assert relerr(g32[rows], gd) < 1e-5
+    assert relerr(run(pi, F, api.F64)[rows], gd) < 1e-6
+    pe = api.Plan(N, eps=1e-6, amp_kind=L.AMP_SMOOTH)
+    assert relerr(g32, run(pe, F, api.F32)) < 2e-6
+
+
+def test_entry_callback_plan_on_gpu():
+    N, m = 1024, 5
+
+    def K(x, xi):
+        c = (2 + np.sin(2 * np.pi * x)) / 16
+        amp = 1 + 0.25 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * xi / N)
+        return amp * np.exp(2j * np.pi * (x * xi + c * abs(xi)))
+    p = api.Plan(N, eps=1e-6, entry=K)
+    F = inputs.complex_gaussian(N, m, seed=42)
+    gd = od.direct(od.FIO, N, F, amp=1)
+    assert relerr(run(p, F, api.F32), gd) < 1e-5
+    assert relerr(run(p, F, api.F64), gd) < 1e-6
+
+
+def test_indirect_piecewise_split_plan_on_gpu():
+    N, m = 65536, 4
+    p = api.Plan(N, eps=1e-6, phase_kind=L.PHASE_FIO_PW, amp_kind=L.AMP_SMOOTH, split=2, indirect=True)
+    assert p.info()["recover_err_k"] < 1e-7
+    F = inputs.complex_gaussian(N, m, seed=43)
+    rows = np.concatenate([inputs.sample_rows(N // 2, 32, seed=44), N // 2 + inputs.sample_rows(N // 2, 32, seed=45)])
+    assert relerr(run(p, F, api.F32)[rows], od.direct(od.FIOPW, N, F, rows, amp=1)) < 1e-5

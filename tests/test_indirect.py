@@ -1,0 +1,116 @@
+"""CPU tests of indirect access (Scenario 1, Sec. 2.2): plans factored from the
+kernel's entries alone, the amplitude recovered by Algorithm 1 on |K| and the
+phase by Algorithms 3-5 (host construction, no GPU work).
+
+* bf_unwrap (Algorithm 3) is bitwise the oracle's unwrap on the same input.
+* The recovered plans' FP64 host factors, applied stage by stage in numpy, meet
+  the BF tolerance against the direct oracle of the true kernel.  They also
+  match the plans built from the explicit phase: a phase known mod 1 gives the
+  same butterfly, since only e^{2 pi i Phi} at grid points enters it.
+* The recovery errors eps^K the library reports stay within the band printed in
+  Table 1D-FIO for the paper's kernel.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from conftest import relerr
+import factored_ref
+from oracle import direct as od
+from oracle import recovery as orc
+from paper_1803_04128_gb300 import _lib as L
+from paper_1803_04128_gb300 import api, inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1803_04128_gb300 import build
+    build.build()
+
+
+def frac(x):
+    return x - np.floor(x)
+
+
+@pytest.mark.parametrize("tau", [0.25, 1.0])
+def test_unwrap_abi_is_bitwise_the_oracle(tau):
+    a = np.arange(6000.0)
+    vs = [0.35 * a ** 2 + 0.37 * a + 3 * np.sin(a / 50),
+          0.2 * a + 0.001 * a ** 2 + np.where(a >= 777, 0.4, 0.0) + np.where(a >= 4000, -0.3, 0.0),
+          np.random.default_rng(2).random(6000) * 40.0]                    # no smoothness at all
+    for v in vs:
+        u = frac(v)
+        for seed in ((), (u[0] + 3.0,), (u[0], u[1] - 1.0, u[2] + 2.0)):
+            w1, s1 = api.unwrap(u, tau, seed)
+            w2, s2 = orc.unwrap(u, tau, seed)
+            assert np.array_equal(w1, w2) and s1 == s2
+
+
+def test_unwrap_bad_arguments():
+    import ctypes
+    lib = L.lib()
+    u = np.zeros(4)
+    n = ctypes.c_int64()
+    assert lib.bf_unwrap(u.ctypes.data, 4, 0.25, None, 4, u.ctypes.data, None, 0, ctypes.byref(n)) == L.BF_ERR_ARG
+    assert lib.bf_unwrap(u.ctypes.data, -1, 0.25, None, 0, u.ctypes.data, None, 0, ctypes.byref(n)) == L.BF_ERR_ARG
+    assert lib.bf_unwrap(u.ctypes.data, 4, 0.25, None, 0, u.ctypes.data, None, 0, None) == L.BF_ERR_ARG
+
+
+def test_indirect_plan_matches_direct_and_explicit_plan():
+    N, m = 4096, 2
+    F = inputs.complex_gaussian(N, m, seed=31)
+    pi = api.Plan(N, eps=1e-6, amp_kind=L.AMP_SMOOTH, indirect=True)
+    pe = api.Plan(N, eps=1e-6, amp_kind=L.AMP_SMOOTH)
+    info = pi.info()
+    # x xi + c(x)|xi| with integer terms a i + b j + c: rank 3; the amplitude is rank 2
+    assert info["phase_rank"] == 3 and info["r_alpha"] == 2
+    assert info["recover_err_k"] < 1e-9 and info["recover_err_amp"] < 1e-12
+    assert 0 < info["t_recover_s"] < 60
+    gi = factored_ref.apply(pi, F)
+    assert relerr(gi, od.direct(od.FIO, N, F, amp=1)) < 1e-6            # eps of the plan
+    assert relerr(gi, factored_ref.apply(pe, F)) < 1e-8                  # same butterfly up to rounding
+    assert pe.info()["phase_rank"] == 0
+
+
+def test_entry_callback_plan():
+    # K given only as a Python callable: the configs' smooth-amplitude FIO kernel
+    N, m = 1024, 3
+
+    def K(x, xi):
+        c = (2 + np.sin(2 * np.pi * x)) / 16
+        amp = 1 + 0.25 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * xi / N)
+        return amp * np.exp(2j * np.pi * (x * xi + c * abs(xi)))
+    p = api.Plan(N, eps=1e-6, entry=K)
+    info = p.info()
+    assert info["phase_rank"] == 3 and info["r_alpha"] == 2
+    F = inputs.complex_gaussian(N, m, seed=32)
+    assert relerr(factored_ref.apply(p, F), od.direct(od.FIO, N, F, amp=1)) < 1e-6
+
+
+def test_indirect_split_plan_piecewise_phase():
+    # the jump at x = 1/2 and the kink at xi = 0 fall on the sub-BF windows' edges
+    N, m = 4096, 2
+    p = api.Plan(N, eps=1e-6, phase_kind=L.PHASE_FIO_PW, amp_kind=L.AMP_SMOOTH, split=2, indirect=True)
+    assert p.info()["recover_err_k"] < 1e-9
+    F = inputs.complex_gaussian(N, m, seed=33)
+    g = factored_ref.apply(p, F)
+    assert relerr(g, od.direct(od.FIOPW, N, F, amp=1)) < 1e-6
+
+
+def test_recovery_error_within_paper_band():
+    # Table 1D-FIO's kernel (alpha = 1, c(x) = (2 + 0.2 sin 2 pi x)/16), rank 20, oversampling 5
+    tab = np.loadtxt(os.path.join(GOLDEN, "table_1dfio_recovery.txt"))
+    for N in (1024, 4096):
+        p = api.Plan(N, eps=1e-6, phase_param=0.2, amp_kind=L.AMP_ONE, indirect=True)
+        info = p.info()
+        assert info["recover_err_k"] < 10 * tab[tab[:, 0] == N, 1].max()
+        assert info["recover_err_amp"] < 1e-13
+
+
+def test_indirect_plans_refuse_device_construction():
+    p = api.Plan(1024, eps=1e-6, amp_kind=L.AMP_SMOOTH, indirect=True, factor=False)
+    assert L.lib().bf_factor_device(p._h) == L.BF_ERR_UNSUPPORTED
+    assert L.lib().bf_factor_otf(p._h) == L.BF_ERR_UNSUPPORTED
