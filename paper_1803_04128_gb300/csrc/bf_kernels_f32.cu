@@ -297,9 +297,12 @@ bool make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int bet
     if (ba->lb != g.h) ba->wl = WLayout{ba->lb, g.L - ba->lb, 0, 0, g.P};
     *sf = front_smem(g, kf, fa->last, g.r, NV, CTp, cfg.mr, cfg.tpc_f);
     if (s_stage) {
+        // two CTAs per SM need dynamic + static shared memory (the tile's small index
+        // tables) + the 1 KB the SM reserves per CTA within 114 KB: stay 1 KB below 113 KB
+        constexpr size_t kStageLimit = 112 * 1024;
         auto fs = [&](bool s, bool b) { return front_smem(g, kf, fa->last, g.r, NV, CTp, cfg.mr, cfg.tpc_f, s, b); };
-        if (fa->last && !g.otf && fs(true, false) <= 113 * 1024) fa->s_smem = 1;
-        if (fs(fa->s_smem, true) <= 113 * 1024) fa->bk_smem = 1;
+        if (fa->last && !g.otf && fs(true, false) <= kStageLimit) fa->s_smem = 1;
+        if (fs(fa->s_smem, true) <= kStageLimit) fa->bk_smem = 1;
         *sf = fs(fa->s_smem, fa->bk_smem);
     }
     *sb = back_smem(g, kb, g.r, NV, CTp, cfg.mr, cfg.tpc_b);
