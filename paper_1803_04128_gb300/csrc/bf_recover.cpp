@@ -59,6 +59,8 @@ class PsiSampler {
         rb_.push_back(N);
         cb_.push_back(N);
         const int nbr = (int)rb_.size() - 1, nbc = (int)cb_.size() - 1;
+        // a phase with more pieces than this is not piecewise smooth at this sampling
+        if (nbr > kMaxPieces || nbc > kMaxPieces) return;
         colseed_.assign((size_t)(nbr * nbc), {});
         rowseed_.assign((size_t)(nbr * nbc), {});
         for (int bi = 0; bi < nbr; ++bi)
@@ -98,6 +100,11 @@ class PsiSampler {
                 }
             }
     }
+
+    static constexpr int kMaxPieces = 64;
+    bool ok() const { return !colseed_.empty(); }
+    int pieces_rows() const { return (int)rb_.size() - 1; }
+    int pieces_cols() const { return (int)cb_.size() - 1; }
 
     // local row i (N values of Psi); work: N doubles
     void row(int64_t i, double* out, double* work) const
@@ -233,6 +240,12 @@ bf_status recover_phase(const KernelFn& k, const bf_options& opt, int64_t row0, 
     const int64_t cfirst = (int64_t)(rng.next() % (uint64_t)N), rfirst = (int64_t)(rng.next() % (uint64_t)N);
     const double tau = opt.tau > 0 ? opt.tau : 0.25;
     PsiSampler smp(k, row0, col0, N, cfirst, rfirst, tau, 1.0);
+    if (!smp.ok()) {
+        set_error("bf_factor: the phase seen through the entries has %d x %d smooth pieces (more than %d along "
+                  "a row or column): not piecewise smooth at this grid",
+                  smp.pieces_rows(), smp.pieces_cols(), PsiSampler::kMaxPieces);
+        return BF_ERR_ACCURACY;
+    }
     // Psi[I][:, J] from whole rows (or whole columns when there are fewer of them)
     auto fill = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J, bool adj) {
         const int64_t ni = (int64_t)I.size(), nj = (int64_t)J.size();

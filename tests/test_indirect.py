@@ -114,3 +114,13 @@ def test_indirect_plans_refuse_device_construction():
     p = api.Plan(1024, eps=1e-6, amp_kind=L.AMP_SMOOTH, indirect=True, factor=False)
     assert L.lib().bf_factor_device(p._h) == L.BF_ERR_UNSUPPORTED
     assert L.lib().bf_factor_otf(p._h) == L.BF_ERR_UNSUPPORTED
+
+
+def test_non_smooth_phase_is_refused():
+    # entries with random phases: Algorithm 3 cuts a row at almost every index
+    N = 1024
+    rng = np.random.default_rng(7)
+    ph = rng.random((N, N))
+    K = lambda x, xi: np.exp(2j * np.pi * ph[int(round(x * N)), int(xi) + N // 2])
+    with pytest.raises(RuntimeError, match="smooth pieces"):
+        api.Plan(N, eps=1e-6, entry=K)
