@@ -84,6 +84,10 @@ typedef enum {
 typedef double (*bf_phase_fn)(double x, double xi, void* user);
 /* User amplitude: writes alpha(x, xi) = *re + i *im. */
 typedef void (*bf_amp_fn)(double x, double xi, void* user, double* re, double* im);
+/* Bulk kernel entries (indirect access): writes K at the n grid index pairs (i[k], j[k]),
+ * 0 <= i, j < N, as out[2k] + i out[2k+1].  Called from one thread at a time, with n up to
+ * 2^20. */
+typedef void (*bf_entries_fn)(const int64_t* i, const int64_t* j, int64_t n, void* user, double* out);
 
 /* The operator: the N x N transform on the grid x_i = i/N, xi_j = j - N/2. */
 typedef struct {
@@ -97,6 +101,9 @@ typedef struct {
     bf_amp_fn entry;      /* used when phase_kind == BF_PHASE_ENTRIES: writes    *
                            * K(x, xi) = alpha e^{2 pi i Phi}, alpha > 0 assumed; *
                            * amp_kind is then ignored                            */
+    bf_entries_fn entries;/* the same in bulk by grid indices; with             *
+                           * BF_PHASE_ENTRIES it is used instead of entry when  *
+                           * not NULL                                            */
 } bf_kernel_desc;
 
 typedef struct {

@@ -23,12 +23,14 @@ AMP_ONE, AMP_SMOOTH, AMP_USER = 0, 1, 100
 PHASE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
 AMP_FN = ctypes.CFUNCTYPE(None, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
+ENTRIES_FN = ctypes.CFUNCTYPE(None, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                              ctypes.c_void_p, ctypes.POINTER(ctypes.c_double))
 
 
 class KernelDesc(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("phase_kind", ctypes.c_int), ("phase_param", ctypes.c_double),
                 ("amp_kind", ctypes.c_int), ("phi", PHASE_FN), ("alpha", AMP_FN), ("user", ctypes.c_void_p),
-                ("entry", AMP_FN)]
+                ("entry", AMP_FN), ("entries", ENTRIES_FN)]
 
 
 class Options(ctypes.Structure):

@@ -53,10 +53,15 @@ class Plan:
 
     def __init__(self, N, eps=1e-6, phase_kind=L.PHASE_FIO, phase_param=1.0, amp_kind=L.AMP_ONE,
                  r=0, n0=1, split=1, seed=0, keep_host=True, device=0, factor=True, phi=None, alpha=None,
-                 factor_on_device=False, on_the_fly=False, indirect=False, entry=None, _handle=None):
+                 factor_on_device=False, on_the_fly=False, indirect=False, entry=None, entries=None,
+                 amp_rank=0, amp_oversample=0, phase_rank=0, phase_oversample=0, _handle=None):
         """``indirect``: factor from the kernel's entries alone (amplitude and phase
-        recovered, Algorithms 1 and 3-5); ``entry(x, xi) -> complex`` gives K when the
-        kernel has no built-in kind (implies indirect)."""
+        recovered, Algorithms 1 and 3-5).  A kernel without a built-in kind is given by
+        ``entry(x, xi) -> complex`` or, in bulk, ``entries(i, j) -> complex array`` over
+        grid index arrays (x_i = i/N, xi_j = j - N/2); either implies indirect.
+        ``amp_rank``, ``amp_oversample`` (``phase_rank``, ``phase_oversample``): Algorithm 1's
+        rank parameter and oversampling for the amplitude (the recovered phase); 0: the
+        library's defaults."""
         self._lib = L.lib()
         self._h = ctypes.c_void_p()
         self._keep = []
@@ -87,9 +92,27 @@ class Plan:
                 self._keep.append(cb3)
                 d.entry = cb3
                 d.phase_kind = L.PHASE_ENTRIES
+            if entries is not None:
+                def _ents(ip, jp, n, u, out):
+                    I = np.ctypeslib.as_array(ip, shape=(n,))
+                    J = np.ctypeslib.as_array(jp, shape=(n,))
+                    o = np.ctypeslib.as_array(out, shape=(2 * n,)).view(np.complex128)
+                    o[:] = np.asarray(entries(I, J), dtype=np.complex128).reshape(n)
+                cb4 = L.ENTRIES_FN(_ents)
+                self._keep.append(cb4)
+                d.entries = cb4
+                d.phase_kind = L.PHASE_ENTRIES
             o = default_options()
             o.r, o.n0, o.split, o.seed, o.keep_host, o.device = r, n0, split, seed, int(keep_host), device
-            o.indirect = int(indirect or entry is not None)
+            o.indirect = int(indirect or entry is not None or entries is not None)
+            if amp_rank:
+                o.amp_rank = amp_rank
+            if amp_oversample:
+                o.amp_oversample = amp_oversample
+            if phase_rank:
+                o.phase_rank = phase_rank
+            if phase_oversample:
+                o.phase_oversample = phase_oversample
             L.check(self._lib.bf_plan_create(ctypes.byref(d), eps, ctypes.byref(o), ctypes.byref(self._h)),
                     "bf_plan_create")
             if on_the_fly:

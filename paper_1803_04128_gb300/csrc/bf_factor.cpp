@@ -70,8 +70,25 @@ cd KernelFn::amplitude(int64_t i, int64_t j) const
     return indirect ? cd(std::abs(entry(i, j))) : amplitude_explicit(i, j);
 }
 
+void KernelFn::entries(const int64_t* I, const int64_t* J, int64_t n, cd* out) const
+{
+    if (bulk()) {
+        constexpr int64_t kPiece = (int64_t)1 << 20;
+        for (int64_t s = 0; s < n; s += kPiece)
+            d.entries(I + s, J + s, std::min(kPiece, n - s), d.user, reinterpret_cast<double*>(out + s));
+        return;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < n; ++t) out[t] = entry(I[t], J[t]);
+}
+
 cd KernelFn::entry(int64_t i, int64_t j) const
 {
+    if (bulk()) {
+        cd v;
+        d.entries(&i, &j, 1, d.user, reinterpret_cast<double*>(&v));
+        return v;
+    }
     if (d.phase_kind == BF_PHASE_ENTRIES) {
         double re = 0, im = 0;
         d.entry((double)i / (double)n_global, (double)(j - n_global / 2), d.user, &re, &im);
@@ -253,9 +270,17 @@ std::vector<int64_t> sample_union(SplitMix& rng, int64_t n, int64_t k, const std
 // rank cut at the singular values above tol * sigma_1.  seed_state starts the sampler.
 bf_status lowrank_sampled(const EntriesFn& entries, const EntriesFn& entries_adj, int64_t N, int r, int q,
                           double tol, uint64_t seed_state, std::vector<cd>& a, std::vector<cd>& b, int& rank,
-                          double& sigma_ratio)
+                          double& sigma_ratio, const std::vector<int64_t>& fixed_rows,
+                          const std::vector<int64_t>& fixed_cols)
 {
     r = std::max(1, r);
+    // sample sets always hold the important rows / columns and the fixed ones
+    auto with = [](std::vector<int64_t> v, const std::vector<int64_t>& extra) {
+        v.insert(v.end(), extra.begin(), extra.end());
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        return v;
+    };
     const int64_t rq = (int64_t)r * std::max(1, q);
     SplitMix rng{seed_state};
     std::vector<int64_t> all((size_t)N);
@@ -265,12 +290,12 @@ bf_status lowrank_sampled(const EntriesFn& entries, const EntriesFn& entries_adj
     const double qr_tol = 1e-15;
     for (int sweep = 0; sweep < 2; ++sweep) {
         // rq random rows + important rows; pivoted QR of K(I, :) picks columns
-        auto I = sample_union(rng, N, rq, pi_row);
+        auto I = sample_union(rng, N, rq, with(pi_row, fixed_rows));
         int kr = pivoted_qr(entries(I, all), r, qr_tol, Q, piv);
         pi_col.assign(piv.begin(), piv.begin() + std::max(kr, 1));
         std::sort(pi_col.begin(), pi_col.end());
         // rq random columns + important columns; pivoted LQ of K(:, J) picks rows
-        auto J = sample_union(rng, N, rq, pi_col);
+        auto J = sample_union(rng, N, rq, with(pi_col, fixed_cols));
         kr = pivoted_qr(entries_adj(all, J), r, qr_tol, Q, piv);
         pi_row.assign(piv.begin(), piv.begin() + std::max(kr, 1));
         std::sort(pi_row.begin(), pi_row.end());
@@ -285,8 +310,8 @@ bf_status lowrank_sampled(const EntriesFn& entries, const EntriesFn& entries_adj
         sigma_ratio = 0;
         return BF_OK;
     }
-    auto J = sample_union(rng, N, rq, pi_col);
-    auto I = sample_union(rng, N, rq, pi_row);
+    auto J = sample_union(rng, N, rq, with(pi_col, fixed_cols));
+    auto I = sample_union(rng, N, rq, with(pi_row, fixed_rows));
     CMat QcI((int64_t)I.size(), kc), QrJ(kr, (int64_t)J.size());
     for (size_t ii = 0; ii < I.size(); ++ii)
         for (int64_t c = 0; c < kc; ++c) QcI((int64_t)ii, c) = Qc(I[ii], c);
@@ -316,7 +341,27 @@ bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0
                           int64_t N, std::vector<cd>& a, std::vector<cd>& b, int& ra,
                           double& sigma_ratio)
 {
+    // indirect kernels: |K| on the whole block, fetched through KernelFn::entries
+    auto block_abs = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J, bool adj) {
+        const int64_t ni = (int64_t)I.size(), nj = (int64_t)J.size();
+        std::vector<int64_t> ri((size_t)(ni * nj)), cj((size_t)(ni * nj));
+        for (int64_t jj = 0; jj < nj; ++jj)
+            for (int64_t ii = 0; ii < ni; ++ii) {
+                ri[(size_t)(jj * ni + ii)] = row0 + I[(size_t)ii];
+                cj[(size_t)(jj * ni + ii)] = col0 + J[(size_t)jj];
+            }
+        std::vector<cd> kv((size_t)(ni * nj));
+        k.entries(ri.data(), cj.data(), ni * nj, kv.data());
+        CMat M(adj ? nj : ni, adj ? ni : nj);
+        for (int64_t jj = 0; jj < nj; ++jj)
+            for (int64_t ii = 0; ii < ni; ++ii) {
+                const double a = std::abs(kv[(size_t)(jj * ni + ii)]);
+                if (adj) M(jj, ii) = a; else M(ii, jj) = a;
+            }
+        return M;
+    };
     auto entries = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J) {
+        if (k.indirect) return block_abs(I, J, false);
         CMat M((int64_t)I.size(), (int64_t)J.size());
 #pragma omp parallel for schedule(static)
         for (int64_t jj = 0; jj < (int64_t)J.size(); ++jj)
@@ -326,6 +371,7 @@ bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0
     };
     // adjoint(entries(I, J)) built directly, in parallel over the rows I
     auto entries_adj = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J) {
+        if (k.indirect) return block_abs(I, J, true);
         CMat M((int64_t)J.size(), (int64_t)I.size());
 #pragma omp parallel for schedule(static)
         for (int64_t ii = 0; ii < (int64_t)I.size(); ++ii)
@@ -335,7 +381,7 @@ bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0
     };
     return lowrank_sampled(entries, entries_adj, N, opt.amp_rank, opt.amp_oversample,
                            opt.amp_tol > 0 ? opt.amp_tol : 1e-13, opt.seed * 0x9E3779B97F4A7C15ull + 12345, a, b,
-                           ra, sigma_ratio);
+                           ra, sigma_ratio, {}, {});
 }
 
 // ---------------------------------------------------------------------------

@@ -43,6 +43,10 @@ struct KernelFn {
     cd amplitude(int64_t i, int64_t j) const;
     // K(x_i, xi_j): the entry callback (BF_PHASE_ENTRIES) or the explicit alpha e^{2 pi i Phi}
     cd entry(int64_t i, int64_t j) const;
+    // K at n index pairs; a bulk callback is called from this thread in pieces of at most
+    // 2^20 entries, other sources are evaluated in parallel
+    void entries(const int64_t* I, const int64_t* J, int64_t n, cd* out) const;
+    bool bulk() const { return d.phase_kind == BF_PHASE_ENTRIES && d.entries; }
     // the explicit definitions (kinds and callbacks of d), whatever indirect says
     double phase_frac_explicit(int64_t i, int64_t j) const;
     cd amplitude_explicit(int64_t i, int64_t j) const;
@@ -139,9 +143,11 @@ CMat adjoint(const CMat& A);
 // Algorithm 1 (Sec. 2.1) on an N x N matrix seen through submatrices: entries(I, J) and
 // its adjoint entries_adj(I, J) (then J x I); a = U0 Sigma0, b = V0^* as [rank][N]
 using EntriesFn = std::function<CMat(const std::vector<int64_t>&, const std::vector<int64_t>&)>;
+// fixed_rows / fixed_cols join every sample set (e.g. where the matrix is least smooth)
 bf_status lowrank_sampled(const EntriesFn& entries, const EntriesFn& entries_adj, int64_t N, int r, int q,
                           double tol, uint64_t seed_state, std::vector<cd>& a, std::vector<cd>& b, int& rank,
-                          double& sigma_ratio);
+                          double& sigma_ratio, const std::vector<int64_t>& fixed_rows,
+                          const std::vector<int64_t>& fixed_cols);
 // indirect access (bf_recover.cpp): Algorithm 3 on one vector, and the phase of one
 // sub-BF window by Algorithms 3-5; recovery_errors fills eps^K and eps^amp of Sec. 5
 void unwrap(const double* u, int64_t n, double tau, const double* seed, int nseed, double* v,

@@ -52,9 +52,9 @@ class PsiSampler {
     {
         std::vector<double> u((size_t)N), v((size_t)N);
         // discontinuities along one column (row cuts) and one row (column cuts)
-        for (int64_t i = 0; i < N; ++i) u[(size_t)i] = turns(i, cfirst);
+        turns_col(cfirst, 0, N, u.data());
         unwrap(u.data(), N, tau, nullptr, 0, v.data(), &rb_);
-        for (int64_t j = 0; j < N; ++j) u[(size_t)j] = turns(rfirst, j);
+        turns_row(rfirst, 0, N, u.data());
         unwrap(u.data(), N, tau, nullptr, 0, v.data(), &cb_);
         rb_.push_back(N);
         cb_.push_back(N);
@@ -70,15 +70,14 @@ class PsiSampler {
                 const int64_t nr = r1 - r0, ncb = c1 - c0;
                 // the block's first row
                 std::vector<double> ur((size_t)ncb), first((size_t)ncb);
-                for (int64_t j = 0; j < ncb; ++j) ur[(size_t)j] = turns(r0, c0 + j);
+                turns_row(r0, c0, ncb, ur.data());
                 unwrap(ur.data(), ncb, tb_, nullptr, 0, first.data(), nullptr);
                 // its first three columns along x
                 const int nc = (int)std::min<int64_t>(3, ncb);
                 std::vector<double>& cs = colseed_[(size_t)(bi * nbc + bj)];
                 cs.assign((size_t)(nc * nr), 0.0);
                 std::vector<double> uc((size_t)(nc * nr)), dt((size_t)nr), w((size_t)nr);
-                for (int t = 0; t < nc; ++t)
-                    for (int64_t i = 0; i < nr; ++i) uc[(size_t)(t * nr + i)] = turns(r0 + i, c0 + t);
+                for (int t = 0; t < nc; ++t) turns_col(c0 + t, r0, nr, uc.data() + (size_t)t * nr);
                 unwrap(uc.data(), nr, tb_, &first[0], 1, cs.data(), nullptr);
                 for (int t = 1; t < nc; ++t) {
                     for (int64_t i = 0; i < nr; ++i) {
@@ -95,34 +94,61 @@ class PsiSampler {
                 std::vector<double>& rs = rowseed_[(size_t)(bi * nbc + bj)];
                 rs.assign((size_t)(nrr * ncb), 0.0);
                 for (int t = 0; t < nrr; ++t) {
-                    for (int64_t j = 0; j < ncb; ++j) ur[(size_t)j] = turns(r0 + t, c0 + j);
+                    turns_row(r0 + t, c0, ncb, ur.data());
                     row_block(r0 + t, bi, bj, ur.data(), rs.data() + (size_t)t * ncb);
                 }
             }
     }
 
     static constexpr int kMaxPieces = 64;
+    // the first and last two local indices of every row piece (rows) and column piece (cols)
+    void edge_indices(std::vector<int64_t>& rows, std::vector<int64_t>& cols) const
+    {
+        auto edges = [&](const std::vector<int64_t>& e, std::vector<int64_t>& out) {
+            for (size_t k = 0; k + 1 < e.size(); ++k)
+                for (int64_t t : {e[k], e[k] + 1, e[k + 1] - 2, e[k + 1] - 1})
+                    if (t >= e[k] && t < e[k + 1]) out.push_back(t);
+            std::sort(out.begin(), out.end());
+            out.erase(std::unique(out.begin(), out.end()), out.end());
+        };
+        edges(rb_, rows);
+        edges(cb_, cols);
+    }
     bool ok() const { return !colseed_.empty(); }
     int pieces_rows() const { return (int)rb_.size() - 1; }
     int pieces_cols() const { return (int)cb_.size() - 1; }
 
-    // local row i (N values of Psi); work: N doubles
-    void row(int64_t i, double* out, double* work) const
+    // Phi mod 1 on local row i, columns c0 .. c0 + n (out: n values in [0, 1))
+    void turns_row(int64_t i, int64_t c0, int64_t n, double* out) const
+    {
+        std::vector<int64_t> I((size_t)n, row0_ + i), J((size_t)n);
+        for (int64_t t = 0; t < n; ++t) J[(size_t)t] = col0_ + c0 + t;
+        fetch(I, J, out);
+    }
+    // Phi mod 1 on local column j, rows r0 .. r0 + n
+    void turns_col(int64_t j, int64_t r0, int64_t n, double* out) const
+    {
+        std::vector<int64_t> I((size_t)n), J((size_t)n, col0_ + j);
+        for (int64_t t = 0; t < n; ++t) I[(size_t)t] = row0_ + r0 + t;
+        fetch(I, J, out);
+    }
+
+    // local row i (N values of Psi) from its observations u (N values of Phi mod 1)
+    void row(int64_t i, const double* u, double* out) const
     {
         const int bi = block_of(rb_, i), nbc = (int)cb_.size() - 1;
-        for (int64_t j = 0; j < N_; ++j) work[j] = turns(i, j);
         for (int bj = 0; bj < nbc; ++bj) {
             const int64_t c0 = cb_[(size_t)bj];
-            row_block(i, bi, bj, work + c0, out + c0);
+            row_block(i, bi, bj, u + c0, out + c0);
         }
     }
 
-    // local column j (N values of Psi); work: N doubles
-    void col(int64_t j, double* out, double* work) const
+    // local column j (N values of Psi) from its observations u (N values of Phi mod 1)
+    void col(int64_t j, const double* u, double* out) const
     {
         const int bj = block_of(cb_, j), nbr = (int)rb_.size() - 1, nbc = (int)cb_.size() - 1;
         const int64_t c0 = cb_[(size_t)bj], ncb = cb_[(size_t)bj + 1] - c0;
-        for (int64_t i = 0; i < N_; ++i) work[i] = turns(i, j);
+        const double* work = u;
         for (int bi = 0; bi < nbr; ++bi) {
             const int64_t r0 = rb_[(size_t)bi], nr = rb_[(size_t)bi + 1] - r0;
             const std::vector<double>& rs = rowseed_[(size_t)(bi * nbc + bj)];
@@ -134,11 +160,16 @@ class PsiSampler {
     }
 
   private:
-    // Phi(row0 + i, col0 + j) mod 1 in [0, 1), read off K / |K|
-    double turns(int64_t i, int64_t j) const
+    // Phi mod 1 in [0, 1) at the global index pairs (I[t], J[t]), read off K / |K|
+    void fetch(const std::vector<int64_t>& I, const std::vector<int64_t>& J, double* out) const
     {
-        const double t = std::arg(k_.entry(row0_ + i, col0_ + j)) / kTwoPi;
-        return t - std::floor(t);
+        const int64_t n = (int64_t)I.size();
+        std::vector<cd> kv((size_t)n);
+        k_.entries(I.data(), J.data(), n, kv.data());
+        for (int64_t t = 0; t < n; ++t) {
+            const double a = std::arg(kv[(size_t)t]) / kTwoPi;
+            out[t] = a - std::floor(a);
+        }
     }
     static int block_of(const std::vector<int64_t>& edges, int64_t x)
     {
@@ -246,28 +277,37 @@ bf_status recover_phase(const KernelFn& k, const bf_options& opt, int64_t row0, 
                   smp.pieces_rows(), smp.pieces_cols(), PsiSampler::kMaxPieces);
         return BF_ERR_ACCURACY;
     }
-    // Psi[I][:, J] from whole rows (or whole columns when there are fewer of them)
+    // Psi[I][:, J] from whole rows (or whole columns when there are fewer of them).  The
+    // observations of up to kGroup vectors are fetched at a time from this thread (a bulk
+    // entry callback sees one caller), then unwrapped in parallel.
+    constexpr int64_t kGroup = 16;
     auto fill = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J, bool adj) {
         const int64_t ni = (int64_t)I.size(), nj = (int64_t)J.size();
         CMat M(adj ? nj : ni, adj ? ni : nj);
         const bool by_rows = ni <= nj;
         const int64_t nv = by_rows ? ni : nj;
-#pragma omp parallel
-        {
-            std::vector<double> buf((size_t)N), work((size_t)N);
-#pragma omp for schedule(dynamic, 1)
-            for (int64_t t = 0; t < nv; ++t) {
+        std::vector<double> u((size_t)(kGroup * N)), psi((size_t)(kGroup * N));
+        for (int64_t g0 = 0; g0 < nv; g0 += kGroup) {
+            const int64_t ng = std::min(kGroup, nv - g0);
+            for (int64_t t = 0; t < ng; ++t) {
+                if (by_rows) smp.turns_row(I[(size_t)(g0 + t)], 0, N, u.data() + (size_t)t * N);
+                else smp.turns_col(J[(size_t)(g0 + t)], 0, N, u.data() + (size_t)t * N);
+            }
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int64_t t = 0; t < ng; ++t) {
+                double* buf = psi.data() + (size_t)t * N;
+                const int64_t v = g0 + t;
                 if (by_rows) {
-                    smp.row(I[(size_t)t], buf.data(), work.data());
+                    smp.row(I[(size_t)v], u.data() + (size_t)t * N, buf);
                     for (int64_t jj = 0; jj < nj; ++jj) {
                         const double x = buf[(size_t)J[(size_t)jj]];
-                        if (adj) M(jj, t) = x; else M(t, jj) = x;
+                        if (adj) M(jj, v) = x; else M(v, jj) = x;
                     }
                 } else {
-                    smp.col(J[(size_t)t], buf.data(), work.data());
+                    smp.col(J[(size_t)v], u.data() + (size_t)t * N, buf);
                     for (int64_t ii = 0; ii < ni; ++ii) {
                         const double x = buf[(size_t)I[(size_t)ii]];
-                        if (adj) M(t, ii) = x; else M(ii, t) = x;
+                        if (adj) M(v, ii) = x; else M(ii, v) = x;
                     }
                 }
             }
@@ -280,10 +320,15 @@ bf_status recover_phase(const KernelFn& k, const bf_options& opt, int64_t row0, 
     lr.row0 = row0;
     lr.col0 = col0;
     lr.N = N;
+    // the first and last two rows and columns of every smooth piece join Algorithm 1's
+    // samples: a phase is least smooth at the edges of its pieces (a kernel's turning
+    // points, the window's corners), where random samples rarely fall
+    std::vector<int64_t> fr, fc;
+    smp.edge_indices(fr, fc);
     return lowrank_sampled(ent, ent_adj, N, opt.phase_rank > 0 ? opt.phase_rank : 20,
                            opt.phase_oversample > 0 ? opt.phase_oversample : 5,
                            opt.phase_tol > 0 ? opt.phase_tol : 1e-13, opt.seed * 0x9E3779B97F4A7C15ull + 4242, lr.p,
-                           lr.q, lr.rank, sig);
+                           lr.q, lr.rank, sig, fr, fc);
 }
 
 // eps^K and eps^amp of Sec. 5 on 256 x 256 sampled entries of the window
@@ -297,11 +342,19 @@ void recovery_errors(const KernelFn& k, BlockFactors& B, uint64_t seed)
         if (std::find(S.begin(), S.end(), t) == S.end()) S.push_back(t);
     }
     CMat dK(ns, ns), K(ns, ns), dA(ns, ns), A(ns, ns);
+    std::vector<int64_t> ri((size_t)(ns * ns)), cj((size_t)(ns * ns));
+    for (int64_t jj = 0; jj < ns; ++jj)
+        for (int64_t ii = 0; ii < ns; ++ii) {
+            ri[(size_t)(jj * ns + ii)] = B.row0 + S[(size_t)ii];
+            cj[(size_t)(jj * ns + ii)] = B.col0 + S[(size_t)jj];
+        }
+    std::vector<cd> kvs((size_t)(ns * ns));
+    k.entries(ri.data(), cj.data(), ns * ns, kvs.data());
 #pragma omp parallel for schedule(static)
     for (int64_t jj = 0; jj < ns; ++jj)
         for (int64_t ii = 0; ii < ns; ++ii) {
             const int64_t i = B.row0 + S[(size_t)ii], j = B.col0 + S[(size_t)jj];
-            const cd kv = k.entry(i, j);
+            const cd kv = kvs[(size_t)(jj * ns + ii)];
             cd amp = 0;
             for (int q = 0; q < B.ra; ++q)
                 amp += B.a[(size_t)q * N + S[(size_t)ii]] * B.b[(size_t)q * N + S[(size_t)jj]];

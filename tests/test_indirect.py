@@ -124,3 +124,41 @@ def test_non_smooth_phase_is_refused():
     K = lambda x, xi: np.exp(2j * np.pi * ph[int(round(x * N)), int(xi) + N // 2])
     with pytest.raises(RuntimeError, match="smooth pieces"):
         api.Plan(N, eps=1e-6, entry=K)
+
+
+def test_bulk_entries_equal_single_entries():
+    # the same kernel through the bulk callback and through the per-entry callback
+    N = 512
+
+    def K1(x, xi):
+        c = (2 + np.sin(2 * np.pi * x)) / 16
+        return (1 + 0.25 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * xi / N)) * np.exp(
+            2j * np.pi * (x * xi + c * abs(xi)))
+
+    def Kb(I, J):
+        x, xi = I / N, J - N / 2
+        c = (2 + np.sin(2 * np.pi * x)) / 16
+        return (1 + 0.25 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * xi / N)) * np.exp(
+            2j * np.pi * (x * xi + c * np.abs(xi)))
+    F = inputs.complex_gaussian(N, 2, seed=34)
+    a = factored_ref.apply(api.Plan(N, eps=1e-6, entry=K1), F)
+    b = factored_ref.apply(api.Plan(N, eps=1e-6, entries=Kb), F)
+    assert relerr(a, b) < 1e-12
+
+
+def test_hankel_transform_matches_paper_table():
+    # Eq. HK (Scenario 1): K_ij = H^(1)_j(N + 2 pi i / 3), entries in bulk from the oracle's
+    # evaluator; rank 20 and oversampling 5 for amplitude and phase, as in Table HK
+    from oracle import special as sp
+    tab = np.loadtxt(os.path.join(GOLDEN, "table_hk_N1024.txt"))
+    N = 1024
+    F = inputs.complex_gaussian(N, 1, seed=51)
+    rows = np.sort(np.random.default_rng(52).choice(N, 256, replace=False))   # 256 rows, Sec. 5
+    gd = sp.hankel_direct(N, F, rows)
+    ent = lambda I, J: sp.hankel1(J.astype(float), sp.hankel_x(N, I))      # entries at index pairs
+    for r, eb, ek, ea in tab:
+        p = api.Plan(N, r=int(r), entries=ent, amp_rank=20, amp_oversample=5)
+        info = p.info()
+        e = relerr(factored_ref.apply(p, F)[rows], gd)
+        assert e < 4 * eb, (r, e, eb)
+        assert info["recover_err_amp"] < 10 * tab[:, 3].max()

@@ -247,6 +247,25 @@ def test_ibf_apply_with_amplitude():
     assert relerr(g, d.direct(d.FIO, N, F, amp=1)) < 1e-6
 
 
+# ------------------------------------------------------- Hankel entries ---
+def test_hankel_entries_satisfy_bessel_identities():
+    # oracle/special.py's entries H^(1)_nu(x) = J_nu + i Y_nu on the transform's grid:
+    # the Wronskian J_{nu+1} Y_nu - J_nu Y_{nu+1} = 2 / (pi x) and the three-term
+    # recurrence H_{nu-1} + H_{nu+1} = (2 nu / x) H_nu
+    from oracle import special as sp
+    N = 1024
+    rows = np.array([0, 1, 100, 700, 1023])
+    x = sp.hankel_x(N, rows)
+    H = lambda n: sp.hankel_entries(N, rows, np.asarray(n))
+    nu = np.array([0, 1, 333, 900, 1021])
+    Jn, Yn = H(nu).real, H(nu).imag
+    Jn1, Yn1 = H(nu + 1).real, H(nu + 1).imag
+    wr = (Jn1 * Yn - Jn * Yn1) * (np.pi * x[:, None] / 2)
+    assert np.abs(wr - 1).max() < 1e-10
+    rec = H(nu[1:] - 1) + H(nu[1:] + 1) - (2 * nu[1:][None, :] / x[:, None]) * H(nu[1:])
+    assert np.abs(rec).max() < 1e-10 * np.abs(H(nu[1:])).max()
+
+
 # ----------------------------------------------- planted mistakes ---------
 def test_planted_mistakes_are_caught(monkeypatch):
     """Each plausible oracle mistake below breaks at least one pin above."""
