@@ -345,6 +345,7 @@ bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0
     auto block_abs = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J, bool adj) {
         const int64_t ni = (int64_t)I.size(), nj = (int64_t)J.size();
         std::vector<int64_t> ri((size_t)(ni * nj)), cj((size_t)(ni * nj));
+#pragma omp parallel for schedule(static)
         for (int64_t jj = 0; jj < nj; ++jj)
             for (int64_t ii = 0; ii < ni; ++ii) {
                 ri[(size_t)(jj * ni + ii)] = row0 + I[(size_t)ii];
@@ -353,6 +354,7 @@ bf_status amplitude_split(const KernelFn& k, const bf_options& opt, int64_t row0
         std::vector<cd> kv((size_t)(ni * nj));
         k.entries(ri.data(), cj.data(), ni * nj, kv.data());
         CMat M(adj ? nj : ni, adj ? ni : nj);
+#pragma omp parallel for schedule(static)
         for (int64_t jj = 0; jj < nj; ++jj)
             for (int64_t ii = 0; ii < ni; ++ii) {
                 const double a = std::abs(kv[(size_t)(jj * ni + ii)]);

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <vector>
 
 #include <omp.h>
@@ -132,6 +133,30 @@ class PsiSampler {
         for (int64_t t = 0; t < n; ++t) I[(size_t)t] = row0_ + r0 + t;
         fetch(I, J, out);
     }
+    // Phi mod 1 on the whole local row (by_row) or column idx, entry by entry from the
+    // calling thread (sources that several threads may call at once: not a bulk callback)
+    void turns_line(bool by_row, int64_t idx, double* out) const
+    {
+        for (int64_t t = 0; t < N_; ++t) {
+            const cd v = by_row ? k_.entry(row0_ + idx, col0_ + t) : k_.entry(row0_ + t, col0_ + idx);
+            const double a = std::arg(v) / kTwoPi;
+            out[t] = a - std::floor(a);
+        }
+    }
+    // Phi mod 1 on nv whole local rows (by_rows) or columns idx[0 .. nv), fetched in one
+    // entries() call (out: [nv][N])
+    void turns_lines(bool by_rows, const int64_t* idx, int64_t nv, double* out) const
+    {
+        std::vector<int64_t> I((size_t)(nv * N_)), J((size_t)(nv * N_));
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int64_t v = 0; v < nv; ++v)
+            for (int64_t t = 0; t < N_; ++t) {
+                const size_t e = (size_t)(v * N_ + t);
+                I[e] = row0_ + (by_rows ? idx[v] : t);
+                J[e] = col0_ + (by_rows ? t : idx[v]);
+            }
+        fetch(I, J, out);
+    }
 
     // local row i (N values of Psi) from its observations u (N values of Phi mod 1)
     void row(int64_t i, const double* u, double* out) const
@@ -166,6 +191,7 @@ class PsiSampler {
         const int64_t n = (int64_t)I.size();
         std::vector<cd> kv((size_t)n);
         k_.entries(I.data(), J.data(), n, kv.data());
+#pragma omp parallel for schedule(static)
         for (int64_t t = 0; t < n; ++t) {
             const double a = std::arg(kv[(size_t)t]) / kTwoPi;
             out[t] = a - std::floor(a);
@@ -277,34 +303,39 @@ bf_status recover_phase(const KernelFn& k, const bf_options& opt, int64_t row0, 
                   smp.pieces_rows(), smp.pieces_cols(), PsiSampler::kMaxPieces);
         return BF_ERR_ACCURACY;
     }
-    // Psi[I][:, J] from whole rows (or whole columns when there are fewer of them).  The
-    // observations of up to kGroup vectors are fetched at a time from this thread (a bulk
-    // entry callback sees one caller), then unwrapped in parallel.
-    constexpr int64_t kGroup = 16;
+    // Psi[I][:, J] from whole rows (or whole columns when there are fewer of them).  A bulk
+    // entry callback sees one caller: the observations of up to kGroup vectors are fetched
+    // at a time by one entries() call from this thread, then unwrapped in parallel.  Other
+    // sources are evaluated by the thread that unwraps the vector, in one pass.
+    const bool grouped = k.bulk();
+    const int64_t kGroup = grouped ? 16 : std::numeric_limits<int64_t>::max();
     auto fill = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& J, bool adj) {
         const int64_t ni = (int64_t)I.size(), nj = (int64_t)J.size();
         CMat M(adj ? nj : ni, adj ? ni : nj);
         const bool by_rows = ni <= nj;
         const int64_t nv = by_rows ? ni : nj;
-        std::vector<double> u((size_t)(kGroup * N)), psi((size_t)(kGroup * N));
-        for (int64_t g0 = 0; g0 < nv; g0 += kGroup) {
-            const int64_t ng = std::min(kGroup, nv - g0);
-            for (int64_t t = 0; t < ng; ++t) {
-                if (by_rows) smp.turns_row(I[(size_t)(g0 + t)], 0, N, u.data() + (size_t)t * N);
-                else smp.turns_col(J[(size_t)(g0 + t)], 0, N, u.data() + (size_t)t * N);
-            }
+        const int64_t gmax = std::min(kGroup, nv);
+        const int nth = grouped ? 1 : omp_get_max_threads();
+        // grouped: u, psi hold gmax vectors; otherwise one u and one psi vector per thread
+        std::vector<double> u((size_t)((grouped ? gmax : nth) * N)), psi((size_t)((grouped ? gmax : nth) * N));
+        for (int64_t g0 = 0; g0 < nv; g0 += gmax) {
+            const int64_t ng = std::min(gmax, nv - g0);
+            if (grouped) smp.turns_lines(by_rows, (by_rows ? I : J).data() + g0, ng, u.data());
 #pragma omp parallel for schedule(dynamic, 1)
             for (int64_t t = 0; t < ng; ++t) {
-                double* buf = psi.data() + (size_t)t * N;
                 const int64_t v = g0 + t;
+                const size_t slot = grouped ? (size_t)t : (size_t)omp_get_thread_num();
+                double* buf = psi.data() + slot * N;
+                double* uv = u.data() + slot * N;
+                if (!grouped) smp.turns_line(by_rows, by_rows ? I[(size_t)v] : J[(size_t)v], uv);
                 if (by_rows) {
-                    smp.row(I[(size_t)v], u.data() + (size_t)t * N, buf);
+                    smp.row(I[(size_t)v], uv, buf);
                     for (int64_t jj = 0; jj < nj; ++jj) {
                         const double x = buf[(size_t)J[(size_t)jj]];
                         if (adj) M(jj, v) = x; else M(v, jj) = x;
                     }
                 } else {
-                    smp.col(J[(size_t)v], u.data() + (size_t)t * N, buf);
+                    smp.col(J[(size_t)v], uv, buf);
                     for (int64_t ii = 0; ii < ni; ++ii) {
                         const double x = buf[(size_t)I[(size_t)ii]];
                         if (adj) M(v, ii) = x; else M(ii, v) = x;
