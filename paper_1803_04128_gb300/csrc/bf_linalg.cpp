@@ -3,6 +3,7 @@
 // one-sided Jacobi SVD, pseudo-inverse.  Used by Algorithm 1 (Sec. 2.1).
 #include <algorithm>
 #include <cmath>
+#include <limits>
 
 #include "bf_internal.h"
 
@@ -69,14 +70,25 @@ int pivoted_qr(CMat R, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv)
 {
     const int64_t m = R.m, n = R.n;  // R starts as the input matrix (moved in by callers with temporaries)
     piv.resize((size_t)n);
-    std::vector<double> nrm((size_t)n);
+    // Column norms of the trailing block: nrm holds the downdated estimates, nrm_ex the
+    // norm at the column's last exact evaluation.  Downdating (nrm^2 -= |R(k, j)|^2)
+    // cancels catastrophically once the trailing norm is far below the exact one, so a
+    // column whose estimate has lost about half of its digits is summed again (the
+    // safeguard of Drmac and Bujanovic, ACM TOMS 35(2), 2008).  Without it, the pivots
+    // of a matrix whose singular values span more than ~1e-8 are chosen from rounding
+    // noise, and the rank test below stops early.
+    std::vector<double> nrm((size_t)n), nrm_ex((size_t)n);
     const bool wide = n > 4096;  // many columns: split the column loops over threads
+    auto tail_norm = [&](int64_t j, int64_t i0) {
+        double s = 0;
+        for (int64_t i = i0; i < m; ++i) s += std::norm(R(i, j));
+        return std::sqrt(s);
+    };
+    const double tol3z = std::sqrt(std::numeric_limits<double>::epsilon());
 #pragma omp parallel for schedule(static) if (wide)
     for (int64_t j = 0; j < n; ++j) {
         piv[(size_t)j] = j;
-        double s = 0;
-        for (int64_t i = 0; i < m; ++i) s += std::norm(R(i, j));
-        nrm[(size_t)j] = s;
+        nrm[(size_t)j] = nrm_ex[(size_t)j] = tail_norm(j, 0);
     }
     const int64_t kcap = std::min<int64_t>({(int64_t)kmax, m, n});
     std::vector<std::vector<cd>> vs;
@@ -86,15 +98,14 @@ int pivoted_qr(CMat R, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv)
         int64_t p = k;
         for (int64_t j = k + 1; j < n; ++j)
             if (nrm[(size_t)j] > nrm[(size_t)p]) p = j;
-        // recompute the winner's norm exactly (downdating loses accuracy)
-        double s = 0;
-        for (int64_t i = k; i < m; ++i) s += std::norm(R(i, p));
-        double pn = std::sqrt(s);
+        // recompute the winner's norm exactly
+        const double pn = tail_norm(p, k);
         if (ref < 0) ref = pn;
         if (pn <= tol * ref || pn == 0.0) break;
         if (p != k) {
             for (int64_t i = 0; i < m; ++i) std::swap(R(i, k), R(i, p));
             std::swap(nrm[(size_t)k], nrm[(size_t)p]);
+            std::swap(nrm_ex[(size_t)k], nrm_ex[(size_t)p]);
             std::swap(piv[(size_t)k], piv[(size_t)p]);
         }
         // Householder vector for R[k:, k]
@@ -124,8 +135,16 @@ int pivoted_qr(CMat R, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv)
         }
 #pragma omp parallel for schedule(static) if (wide)
         for (int64_t j = k + 1; j < n; ++j) {
-            nrm[(size_t)j] -= std::norm(R(k, j));
-            if (nrm[(size_t)j] < 0) nrm[(size_t)j] = 0;
+            const double nj = nrm[(size_t)j];
+            if (nj == 0.0) continue;
+            const double t = std::abs(R(k, j)) / nj;
+            const double rest = std::max(0.0, (1.0 - t) * (1.0 + t));   // (trailing / current)^2
+            const double q = nj / nrm_ex[(size_t)j];
+            if (rest * q * q <= tol3z) {
+                nrm[(size_t)j] = nrm_ex[(size_t)j] = tail_norm(j, k + 1);
+            } else {
+                nrm[(size_t)j] = nj * std::sqrt(rest);
+            }
         }
         vs.push_back(std::move(v));
     }

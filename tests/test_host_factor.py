@@ -136,3 +136,23 @@ def test_user_callbacks_match_builtin():
     p_built = api.Plan(N, r=10, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH)
     F = inputs.complex_gaussian(N, 1, seed=5)
     assert relerr(factored_ref.apply(p_user, F), factored_ref.apply(p_built, F)) < 1e-9
+
+
+def test_amplitude_split_graded_spectrum():
+    # Algorithm 1 on an amplitude of rank 12 whose singular values fall from 1 to ~1e-13:
+    # the pivoted QR must keep choosing the dominant trailing column after the trailing
+    # norms have dropped ~8 orders below the first, so the split reproduces alpha to a few
+    # times its relative tolerance 1e-13 (entrywise, on the whole grid)
+    import math
+    N, K, dec = 256, 12, 1.1
+    alpha = lambda x, xi: sum(10.0 ** (-dec * k) * math.cos(2 * math.pi * (k + 1) * x + k)
+                              * math.cos(math.pi * (k + 1) * xi / N + 0.3 * k) for k in range(K))
+    p = api.Plan(N, r=8, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_USER, alpha=alpha, amp_rank=20)
+    ra = p.info()["r_alpha"]
+    x, xi = np.arange(N) / N, np.arange(N) - N / 2
+    A = sum(10.0 ** (-dec * k) * np.cos(2 * np.pi * (k + 1) * x + k)[:, None]
+            * np.cos(np.pi * (k + 1) * xi / N + 0.3 * k)[None, :] for k in range(K))
+    s = np.linalg.svd(A, compute_uv=False)
+    assert ra == int(np.sum(s > 1e-13 * s[0]))
+    R = p.view(0).reshape(ra, N).T @ p.view(1).reshape(ra, N)
+    assert np.abs(R - A).max() < 5e-13 * np.abs(A).max()
