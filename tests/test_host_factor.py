@@ -156,3 +156,42 @@ def test_amplitude_split_graded_spectrum():
     assert ra == int(np.sum(s > 1e-13 * s[0]))
     R = p.view(0).reshape(ra, N).T @ p.view(1).reshape(ra, N)
     assert np.abs(R - A).max() < 5e-13 * np.abs(A).max()
+
+
+_TAB_ALL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table_1dfio_all.txt")
+
+
+@pytest.mark.parametrize("N,rs", [(4096, (6, 8, 10, 12)), (16384, (6, 8, 10, 12)), (65536, (6, 8, 10, 12)),
+                                  (262144, (8, 10))])
+def test_plans_match_paper_table_1dfio(N, rs):
+    # the library's plans for the Table's kernel (c amplitude 0.2), applied from their
+    # host FP64 factors, against the direct oracle on 256 sampled rows (Sec. 5).  For
+    # r <= 10 the interpolation error dominates on both sides, so eps^b must agree with
+    # the printed value within 4x either way; at r = 12 the printed values for N >= 65536
+    # carry the paper's recovery error (eps^K ~ 3e-9 .. 1e-8), so only the upper bound
+    tab = np.loadtxt(_TAB_ALL)
+    F = inputs.complex_gaussian(N, 1, seed=61)
+    rows = inputs.sample_rows(N, 256, seed=62)
+    gd = od.direct(od.FIO, N, F, rows, s=0.2, amp=0)
+    for r in rs:
+        eb = tab[(tab[:, 0] == N) & (tab[:, 1] == r), 2][0]
+        p = api.Plan(N, r=r, phase_param=0.2, amp_kind=L.AMP_ONE)
+        e = relerr(factored_ref.apply(p, F)[rows], gd)
+        assert e < 4 * eb, (N, r, e, eb)
+        if r <= 10:
+            assert e > eb / 4, (N, r, e, eb)
+
+
+def test_indirect_plan_matches_paper_table_1dfio_n65536():
+    # the same operator factored from its entries alone (Scenario 1): eps^K within 10x of
+    # the printed value and eps^b as for the explicit plan
+    tab = np.loadtxt(_TAB_ALL)
+    N, r = 65536, 10
+    eb, ek = tab[(tab[:, 0] == N) & (tab[:, 1] == r), 2:4][0]
+    p = api.Plan(N, r=r, phase_param=0.2, amp_kind=L.AMP_ONE, indirect=True)
+    info = p.info()
+    assert info["recover_err_k"] < 10 * ek, (info["recover_err_k"], ek)
+    F = inputs.complex_gaussian(N, 1, seed=61)
+    rows = inputs.sample_rows(N, 256, seed=62)
+    e = relerr(factored_ref.apply(p, F)[rows], od.direct(od.FIO, N, F, rows, s=0.2, amp=0))
+    assert eb / 4 < e < 4 * eb, (e, eb)
