@@ -265,9 +265,12 @@ bf_status bf_plan_get_info(const bf_plan* plan, bf_plan_info* info);
  * [r_alpha][N] c128), 1 b ([r_alpha][N] c128), 2 Mv ([r][nv] real), 3 EV
  * ([2^l1][N] c128), 4 MH (level, [r][2r] real), 5 EH (level, [P][2][r] c128),
  * 6 S ([P][r][r] c128), 7 MG (level, [2][r][r] real), 8 FG (level, [P][2][r]
- * c128), 9 MU ([nu][r] real), 10 EU ([2^l1][N] c128).  *data points into the
- * plan (valid until bf_destroy), *count = number of doubles.  Requires a
- * factored plan with host factors kept.  For tests and inspection. */
+ * c128), 9 MU ([nu][r] real), 10 EU ([2^l1][N] c128), 11 and 12 the factors
+ * p and q of a phase recovered from entries (Algorithm 5: Psi(i, j) =
+ * Re sum_k p[k][i] q[k][j] on the sub-BF window, local indices; [phase_rank][N]
+ * c128; *count = 0 for explicit phases).  *data points into the plan (valid
+ * until bf_destroy), *count = number of doubles.  Requires a factored plan with
+ * host factors kept.  For tests and inspection. */
 bf_status bf_plan_view(const bf_plan* plan, int block, int what, int level,
                        const double** data, int64_t* count);
 

@@ -170,7 +170,7 @@ class Plan:
         L.check(self._lib.bf_plan_view(self._h, block, what, level, ctypes.byref(ptr), ctypes.byref(cnt)),
                 "bf_plan_view")
         a = np.ctypeslib.as_array(ptr, shape=(cnt.value,)).copy() if cnt.value else np.zeros(0)
-        if what in (0, 1, 3, 5, 6, 8, 10):
+        if what in (0, 1, 3, 5, 6, 8, 10, 11, 12):
             a = a.view(np.complex128)
         return a
 

@@ -34,6 +34,27 @@ CMat adjoint(const CMat& A)
     return T;
 }
 
+// Neumaier-compensated sum (real and imaginary parts apart): the rounding error of every
+// addition is carried separately, so a sum over a column of up to N entries stays within
+// a few units in the last place instead of an error growing with its length.  The QR
+// below needs that to separate a rank from rounding noise (Algorithm 1 on a recovered
+// phase whose entries reach ~N turns).
+struct CSum {
+    double s[2] = {0.0, 0.0}, c[2] = {0.0, 0.0};
+    void add1(int k, double x)
+    {
+        const double t = s[k] + x;
+        c[k] += std::fabs(s[k]) >= std::fabs(x) ? (s[k] - t) + x : (x - t) + s[k];
+        s[k] = t;
+    }
+    void add(cd x)
+    {
+        add1(0, x.real());
+        add1(1, x.imag());
+    }
+    cd value() const { return cd(s[0] + c[0], s[1] + c[1]); }
+};
+
 // sum over i in [i0, m) of conj(v[i - i0]) * X(i, j): in fixed chunks of rows whose
 // partial sums are added in chunk order, so the result does not depend on the
 // number of threads; long columns are split over threads
@@ -42,21 +63,21 @@ static cd col_dot(const std::vector<cd>& v, const CMat& X, int64_t j, int64_t i0
     constexpr int64_t kChunk = 1 << 15;
     const int64_t len = m - i0, nch = (len + kChunk - 1) / kChunk;
     if (nch <= 1) {
-        cd d = 0;
-        for (int64_t i = i0; i < m; ++i) d += std::conj(v[(size_t)(i - i0)]) * X(i, j);
-        return d;
+        CSum d;
+        for (int64_t i = i0; i < m; ++i) d.add(std::conj(v[(size_t)(i - i0)]) * X(i, j));
+        return d.value();
     }
     std::vector<cd> part((size_t)nch);
 #pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < nch; ++c) {
-        cd d = 0;
+        CSum d;
         const int64_t e = std::min(m, i0 + (c + 1) * kChunk);
-        for (int64_t i = i0 + c * kChunk; i < e; ++i) d += std::conj(v[(size_t)(i - i0)]) * X(i, j);
-        part[(size_t)c] = d;
+        for (int64_t i = i0 + c * kChunk; i < e; ++i) d.add(std::conj(v[(size_t)(i - i0)]) * X(i, j));
+        part[(size_t)c] = d.value();
     }
-    cd d = 0;
-    for (auto& x : part) d += x;
-    return d;
+    CSum d;
+    for (auto& x : part) d.add(x);
+    return d.value();
 }
 
 // X(i, j) -= v[i - i0] * s for i in [i0, m), rows split over threads when long
@@ -80,9 +101,9 @@ int pivoted_qr(CMat R, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv)
     std::vector<double> nrm((size_t)n), nrm_ex((size_t)n);
     const bool wide = n > 4096;  // many columns: split the column loops over threads
     auto tail_norm = [&](int64_t j, int64_t i0) {
-        double s = 0;
-        for (int64_t i = i0; i < m; ++i) s += std::norm(R(i, j));
-        return std::sqrt(s);
+        CSum s;
+        for (int64_t i = i0; i < m; ++i) s.add1(0, std::norm(R(i, j)));
+        return std::sqrt(s.value().real());
     };
     const double tol3z = std::sqrt(std::numeric_limits<double>::epsilon());
 #pragma omp parallel for schedule(static) if (wide)
@@ -116,18 +137,18 @@ int pivoted_qr(CMat R, int kmax, double tol, CMat& Q, std::vector<int64_t>& piv)
         cd ph = ax0 > 0 ? x0 / ax0 : cd(1);
         cd alpha = -ph * pn;
         v[0] -= alpha;
-        double vn = 0;
-        for (auto& e : v) vn += std::norm(e);
-        vn = std::sqrt(vn);
+        CSum vs2;
+        for (auto& e : v) vs2.add1(0, std::norm(e));
+        double vn = std::sqrt(vs2.value().real());
         if (vn > 0)
             for (auto& e : v) e /= vn;
         // apply H = I - 2 v v^* to R[k:, k:]
         if (wide) {
 #pragma omp parallel for schedule(static)
             for (int64_t j = k; j < n; ++j) {
-                cd dot = 0;
-                for (int64_t i = k; i < m; ++i) dot += std::conj(v[(size_t)(i - k)]) * R(i, j);
-                dot *= 2.0;
+                CSum ds;
+                for (int64_t i = k; i < m; ++i) ds.add(std::conj(v[(size_t)(i - k)]) * R(i, j));
+                const cd dot = 2.0 * ds.value();
                 for (int64_t i = k; i < m; ++i) R(i, j) -= v[(size_t)(i - k)] * dot;
             }
         } else {

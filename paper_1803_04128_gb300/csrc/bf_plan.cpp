@@ -437,11 +437,13 @@ bf_status bf_plan_view(const bf_plan* p, int block, int what, int level, const d
         break;
     case 9: rv(B.MU); break;
     case 10: cv(B.EU); break;
+    case 11: cv(B.lr.p); break;
+    case 12: cv(B.lr.q); break;
     default:
         set_error("bf_plan_view: unknown array %d", what);
         return BF_ERR_ARG;
     }
-    if (*count == 0 && what != 0 && what != 1) {
+    if (*count == 0 && what >= 2 && what <= 10) {
         set_error("bf_plan_view: host factors were released after upload");
         return BF_ERR_STATE;
     }

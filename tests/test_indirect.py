@@ -18,6 +18,7 @@ import pytest
 from conftest import relerr
 import factored_ref
 from oracle import direct as od
+from oracle import lowrank as olr
 from oracle import recovery as orc
 from paper_1803_04128_gb300 import _lib as L
 from paper_1803_04128_gb300 import api, inputs
@@ -185,3 +186,33 @@ def test_hankel_transform_n4096_matches_paper_table():
         assert e < 4 * eb, (r, e, eb)
         assert info["recover_err_k"] < 10 * ek, (r, info["recover_err_k"], ek)
         assert info["recover_err_amp"] < 10 * ea, (r, info["recover_err_amp"], ea)
+
+
+@pytest.mark.parametrize("N,kind,okind,s,amp", [
+    (1024, L.PHASE_FIO, od.FIO, 1.0, 1), (1024, L.PHASE_FIO, od.FIO, 0.2, 0), (1024, L.PHASE_DFT, od.DFT, 1.0, 0),
+    (1024, L.PHASE_SEP, od.SEP, 1.0, 1), (4096, L.PHASE_FIO, od.FIO, 0.2, 0)])
+def test_recovery_matches_oracle_algorithms_3_to_5(N, kind, okind, s, amp):
+    # The library's recovery (C++) and the oracle's (numpy) run Algorithms 1 and 3-5 on the
+    # same entries.  The phase rank is an integer decided in FP64 on both sides: equal.
+    # The error is held to what FP64 allows for a phase of |Psi| <= 9N/16 turns rebuilt
+    # from r_phi products, 10 r_phi u max|Psi| turns (u = 2^-53), on both sides: eps^K
+    # (relative 2-norm on 256 x 256 sampled entries, Sec. 5) within 2 pi times that, and
+    # the library's recovered Psi (bf_plan_view 11, 12) equal to Phi mod 1 read off the
+    # oracle's entries, up to integers, within it (rms over the sampled entries).
+    p = api.Plan(N, eps=1e-6, phase_kind=kind, phase_param=s, amp_kind=amp, indirect=True)
+    info = p.info()
+    ent = lambda I, J: od.entries(okind, N, np.asarray(I), np.asarray(J), s=s, amp=amp)
+    P, Q, _ = orc.phase_lowrank(ent, N, r=20, q=5, seed=0)
+    a, b = olr.amplitude_split(lambda I, J: np.abs(ent(I, J)).astype(complex), N, N, r=8, q=5, seed=0)
+    assert info["phase_rank"] == P.shape[0]
+    S = np.sort(np.random.default_rng(7).choice(N, 256, replace=False))
+    K = ent(S, S)
+    Kr = (a[:, S].T @ b[:, S]).real * np.exp(2j * np.pi * (P[:, S].T @ Q[:, S]).real)
+    bound = 10 * P.shape[0] * 2.0 ** -53 * (9 * N / 16)
+    assert relerr(Kr, K) < 2 * np.pi * bound
+    assert info["recover_err_k"] < 2 * np.pi * bound
+    Pl = p.view(11).reshape(-1, N).real
+    Ql = p.view(12).reshape(-1, N).real
+    d = Pl[:, S].T @ Ql[:, S] - orc.phase_turns(K)
+    d -= np.round(d)
+    assert np.sqrt(np.mean(d ** 2)) < bound
