@@ -195,3 +195,19 @@ def test_indirect_plan_matches_paper_table_1dfio_n65536():
     rows = inputs.sample_rows(N, 256, seed=62)
     e = relerr(factored_ref.apply(p, F)[rows], od.direct(od.FIO, N, F, rows, s=0.2, amp=0))
     assert eb / 4 < e < 4 * eb, (e, eb)
+
+
+@pytest.mark.parametrize("r,N_min", [(6, 64), (10, 256), (12, 256)])
+def test_smallest_block_per_r(r, N_min):
+    # the smallest N whose trees have floor(L/2) >= l1 (here no H or G level is left: V,
+    # switch and U only) is factored and meets the direct sum to the interpolation error of
+    # r points (Table 1D-FIO: ~3e-4 at r = 6, ~2e-8 at r = 10); half of it is refused
+    p = api.Plan(N_min, r=r, amp_kind=L.AMP_SMOOTH)
+    i = p.info()
+    assert i["h"] == i["l1"]
+    F = inputs.complex_gaussian(N_min, 2, seed=3)
+    e = relerr(factored_ref.apply(p, F), od.direct(od.FIO, N_min, F, amp=1))
+    assert e < {6: 1e-3, 10: 1e-6, 12: 1e-8}[r]
+    with pytest.raises(L.BFError) as exc:
+        api.Plan(N_min // 2, r=r)
+    assert exc.value.status == L.BF_ERR_ARG
