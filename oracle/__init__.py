@@ -15,6 +15,8 @@ Modules
   recovery   -- Algs. 3, 4, 5: a low-rank phase Psi (e^{2 pi i Psi} = e^{2 pi i Phi})
                 recovered from kernel entries alone (Scenario 1 of Table sc).
   special    -- the Hankel-function transform of Sec. 5 (Eq. HK): entries, direct sums.
+  decide     -- Alg. 6 of Sec. 3: may r-dimensional NUFFTs after dimension lifting
+                evaluate the transform, or does it need the butterfly?
   butterfly  -- the butterfly algorithm of Sec. 4 (Algorithm 4.1) in FP64,
                 on the fly, in the paper's step order; and the IBF apply of
                 Eq. (tg): g = sum_k a_k * BF(b_k * f).

@@ -301,3 +301,63 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(bf, "centre", lambda start, n: start + n + (n - 1) // 2)
     e = relerr(bf.butterfly(bf.Kernel(d.FIO, Nf, 0.2), ff, 10), gd)
     assert e > 1.69e-8 * 4
+
+
+# ------------------------------------------------------ Algorithm 6 -------
+def _fio_factors(N):
+    # Phi = x xi + c(x)|xi| is exactly rank 2: p = (x, c(x)), q = (xi, |xi|) (Sec. 3's lifting)
+    x = np.arange(N) / N
+    xi = np.arange(N) - N / 2.0
+    c = (2 + np.sin(2 * np.pi * x)) / 16
+    amp1 = (np.ones((1, N)), np.ones((1, N)))
+    amp2 = (np.stack([np.ones(N), 0.25 * np.sin(2 * np.pi * x)]), np.stack([np.ones(N), np.cos(2 * np.pi * xi / N)]))
+    return np.stack([x, c]), np.stack([xi, np.abs(xi)]), amp1, amp2
+
+
+@pytest.mark.parametrize("N", [1024, 4096])
+def test_decide_exact_lifting_of_fio_phase(N):
+    # with r = 2 the lifting is the whole phase: the residual kernel is alpha itself, so n
+    # and the number of NUFFTs equal the amplitude rank (1 or 2); with r = 1 the residual
+    # phase c(x)|xi| - its projection winds hundreds of turns: every sampled column counts
+    from oracle import decide as dc
+    P1, Q1, amp1, amp2 = _fio_factors(N)
+    assert dc.nufft_decide(P1, Q1, *amp1, r=2, r_eps=20) == (1, 1, 1)
+    assert dc.nufft_decide(P1, Q1, *amp2, r=2, r_eps=20) == (1, 2, 2)
+    assert dc.nufft_decide(P1, Q1, *amp1, r=1, r_eps=20) == (0, 100, 0)
+
+
+@pytest.mark.parametrize("r,r_eps", [(1, 40), (1, 60), (2, 20)])
+def test_decide_matches_brute_force_rank(r, r_eps):
+    # N = 256: the numerical rank of the whole residual kernel by numpy's SVD.  Pivoted QR
+    # reveals it up to the usual factor between |R_kk| and sigma_k, so n lies between the
+    # SVD ranks at 10 eps and eps / 10 (for r = 1: 49 and 53), and y follows that band
+    from oracle import decide as dc
+    N, eps = 256, 1e-10
+    P1, Q1, amp1, _ = _fio_factors(N)
+    P, Q = dc.lifting(P1, Q1, r)
+    K = dc.residual_kernel(P1, Q1, *amp1, P, Q, np.arange(N), np.arange(N))
+    s = np.linalg.svd(K, compute_uv=False)
+    lo, hi = (int(np.sum(s > t * s[0])) for t in (10 * eps, eps / 10))
+    assert lo >= r_eps or hi < r_eps                     # the case is away from the threshold
+    y, n, terms = dc.nufft_decide(P1, Q1, *amp1, r=r, r_eps=r_eps, q=5, eps=eps)
+    assert lo <= n <= hi
+    assert y == int(hi < r_eps)
+    assert (terms > 0) == bool(y) and terms <= r_eps
+    # the lifting is the best rank-r part of the phase (Eckart-Young against numpy's SVD)
+    sv = np.linalg.svd(P1.T @ Q1, compute_uv=False)
+    err = np.linalg.norm(P1.T @ Q1 - P.T @ Q, 2)
+    assert abs(err - (sv[r] if r < sv.size else 0.0)) <= 1e-9 * sv[0]
+
+
+def test_decide_planted_mistakes_are_caught(monkeypatch):
+    # a lifting without its singular values, or a residual phase with the wrong sign,
+    # turns the rank-2 case into a full-rank one
+    from oracle import decide as dc
+    P1, Q1, amp1, _ = _fio_factors(1024)
+    real = dc.lifting
+    monkeypatch.setattr(dc, "lifting", lambda A, B, r: (lambda P, Q: (P / np.linalg.norm(P, axis=1)[:, None], Q))(*real(A, B, r)))
+    assert dc.nufft_decide(P1, Q1, *amp1, r=2, r_eps=20)[0] == 0
+    monkeypatch.setattr(dc, "lifting", real)
+    monkeypatch.setattr(dc, "residual_kernel", lambda P1, Q1, A2, B2, P, Q, I, J:
+                        (A2[:, I].T @ B2[:, J]) * np.exp(2j * np.pi * (P1[:, I].T @ Q1[:, J] + P[:, I].T @ Q[:, J])))
+    assert dc.nufft_decide(P1, Q1, *amp1, r=2, r_eps=20)[0] == 0
