@@ -165,6 +165,27 @@ bf_status bf_default_options(bf_options* opt);
 bf_status bf_unwrap(const double* u, int64_t n, double tau, const double* seed, int nseed, double* v,
                     int64_t* starts, int64_t cap, int64_t* nstarts);
 
+/* Algorithm 6 (Sec. 3): may sub-BF `block` of a plan factored from its entries (indirect
+ * access) be evaluated by r-dimensional NUFFTs after dimension lifting (Eq. tg3), or does
+ * it need the butterfly?  Inputs are the plan's recovered factorizations: the phase
+ * Psi = Re sum_k p_k(x) q_k(xi) of rank r1 = phase_rank (bf_plan_view 11, 12) and the
+ * amplitude alpha = sum_k a_k(x) b_k(xi) (views 0, 1).  Steps:
+ *  1. the r-leading SVD of the phase factorization is the lifting P Q^T (taken exactly:
+ *     QR of both N x r1 factors, then the SVD of the r1 x r1 core; r >= r1 lifts the
+ *     whole phase);
+ *  2. r_eps * q random columns (seeded) of the residual kernel alpha e^{2 pi i (Psi - P Q^T)}
+ *     are factored by QR with column pivoting;
+ *  3. *n = the number of pivots above eps times the first; *y = 1 iff *n < r_eps (the
+ *     printed algorithm's "r q" columns and "n < r" are read with r_eps);
+ *  4. if *y = 1, Algorithm 1 (rank parameter r_eps, oversampling q, tolerance eps)
+ *     factors the residual kernel and *terms receives its rank, the number of NUFFTs of
+ *     Eq. tg3; otherwise *terms = 0.
+ * Host only, O(N (r1^2 + r_eps q (r1 + r_alpha))) work; no NUFFT is run.  Errors:
+ * BF_ERR_ARG (NULL plan or outputs, r, r_eps or q below 1, eps <= 0, bad block),
+ * BF_ERR_STATE (plan not factored, or not factored from its entries), BF_ERR_NOMEM. */
+bf_status bf_nufft_decide(const bf_plan* plan, int block, int r, int r_eps, int q, double eps,
+                          uint64_t seed, int* y, int* n, int* terms);
+
 /* Create a plan for the operator *desc to tolerance eps (the target relative
  * l2 error eps^b of Sec. 5).  With opt->r == 0 the interpolation rank is taken
  * from eps by the rule r = 4 + ceil(-log10 eps), measured for 1D-FIO-like

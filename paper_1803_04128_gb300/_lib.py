@@ -96,6 +96,9 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_int)]),
     "bf_unwrap": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, _P, ctypes.c_int, _P, _P, ctypes.c_int64,
                                  ctypes.POINTER(ctypes.c_int64)]),
+    "bf_nufft_decide": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]),
     "bf_last_error": (ctypes.c_char_p, []),
     "bf_profile_begin": (ctypes.c_int, []),
     "bf_profile_end": (ctypes.c_int, []),

@@ -174,6 +174,15 @@ class Plan:
             a = a.view(np.complex128)
         return a
 
+    def nufft_decide(self, r, r_eps=20, q=5, eps=1e-10, seed=0, block=0):
+        """Algorithm 6 (bf_nufft_decide) on a plan factored from its entries: (y, n, terms),
+        y = 1 if r-dimensional NUFFTs after lifting the phase evaluate the transform, n the
+        numerical rank of the sampled residual columns, terms the number of NUFFTs."""
+        y, n, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        L.check(self._lib.bf_nufft_decide(self._h, block, r, r_eps, q, eps, seed, ctypes.byref(y), ctypes.byref(n),
+                                          ctypes.byref(t)), "bf_nufft_decide")
+        return y.value, n.value, t.value
+
     def save(self, path):
         L.check(self._lib.bf_plan_save(self._h, str(path).encode()), "bf_plan_save")
 

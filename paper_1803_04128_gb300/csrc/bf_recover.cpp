@@ -400,7 +400,121 @@ void recovery_errors(const KernelFn& k, BlockFactors& B, uint64_t seed)
     B.recover_err_amp = na > 0 ? norm2(dA) / na : 0.0;
 }
 
+// Algorithm 6 (Sec. 3) on one sub-BF of a plan factored from its entries: may
+// r-dimensional NUFFTs after dimension lifting evaluate it?  The inputs are the plan's
+// recovered factorizations, Psi = sum_k p_k(x) q_k(xi) (rank r1) and alpha = sum_k
+// a_k(x) b_k(xi).  Steps: (1) the r-leading SVD of the phase factorization, taken exactly
+// (QR of both N x r1 factors, SVD of the r1 x r1 core), is the lifting P Q^T; (2) r_eps q
+// random columns of the residual kernel alpha e^{2 pi i (Psi - P Q^T)} go through QR
+// with column pivoting; (3) n counts the pivots above eps times the first, y = 1 iff
+// n < r_eps; (4) if y = 1, Algorithm 1 (rank parameter r_eps) factors the residual
+// kernel and terms is its rank, the number of NUFFTs.
+bf_status nufft_decide(const BlockFactors& B, int r, int r_eps, int q, double eps, uint64_t seed, int& y,
+                       int& n, int& terms)
+{
+    const int64_t N = B.N;
+    const PhaseLR& lr = B.lr;
+    const int r1 = lr.rank, ra = B.ra;
+    // (1) U1 V1^T = Qa (Ra Rb^T) Qb^T, Ra = Qa^* U1, Rb = Qb^* V1; the core's SVD
+    CMat U1(N, r1), V1(N, r1);
+    for (int k = 0; k < r1; ++k)
+        for (int64_t i = 0; i < N; ++i) {
+            U1(i, k) = lr.p[(size_t)k * N + i].real();
+            V1(i, k) = lr.q[(size_t)k * N + i].real();
+        }
+    CMat Qa, Qb, Uc, Vc;
+    std::vector<int64_t> piv;
+    pivoted_qr(U1, r1, 0.0, Qa, piv);
+    pivoted_qr(V1, r1, 0.0, Qb, piv);
+    const CMat C = matmul(matmul(adjoint(Qa), U1), adjoint(matmul(adjoint(Qb), V1)));
+    std::vector<double> S;
+    jacobi_svd(C, Uc, S, Vc);
+    const int kr = std::min<int>(r, (int)S.size());
+    // lift(i, j) = sum_l P(i, l) Q(j, l), P = Qa Uc S, Q = conj(Qb Vc), first kr columns
+    CMat P = matmul(Qa, Uc), Q = matmul(Qb, Vc);
+    std::vector<double> Pl((size_t)(kr * N)), Ql((size_t)(kr * N));
+    for (int l = 0; l < kr; ++l)
+        for (int64_t i = 0; i < N; ++i) {
+            Pl[(size_t)l * N + i] = (P(i, l) * S[(size_t)l]).real();
+            Ql[(size_t)l * N + i] = std::conj(Q(i, l)).real();
+        }
+    auto residual = [&](int64_t i, int64_t j) {
+        cd amp = 0;
+        for (int k = 0; k < ra; ++k) amp += B.a[(size_t)k * N + i] * B.b[(size_t)k * N + j];
+        double ph = 0;
+        for (int k = 0; k < r1; ++k) ph += lr.p[(size_t)k * N + i].real() * lr.q[(size_t)k * N + j].real();
+        for (int l = 0; l < kr; ++l) ph -= Pl[(size_t)l * N + i] * Ql[(size_t)l * N + j];
+        ph -= std::nearbyint(ph);
+        return amp * cd(std::cos(kTwoPi * ph), std::sin(kTwoPi * ph));
+    };
+    // (2) r_eps q distinct random columns (Floyd's algorithm), in increasing order
+    Mix64 rng{seed * 0x9E3779B97F4A7C15ull + 606};
+    const int64_t nc = std::min<int64_t>(N, (int64_t)r_eps * q);
+    std::vector<int64_t> J;
+    for (int64_t t = N - nc; t < N; ++t) {
+        int64_t c = (int64_t)(rng.next() % (uint64_t)(t + 1));
+        if (std::find(J.begin(), J.end(), c) != J.end()) c = t;
+        J.push_back(c);
+    }
+    std::sort(J.begin(), J.end());
+    CMat M(N, nc);
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < nc; ++t)
+        for (int64_t i = 0; i < N; ++i) M(i, t) = residual(i, J[(size_t)t]);
+    // (3) numerical rank of the sampled columns: pivots above eps |R(1,1)|
+    CMat Qm;
+    n = pivoted_qr(std::move(M), (int)nc, eps, Qm, piv);
+    y = n < r_eps ? 1 : 0;
+    terms = 0;
+    if (!y) return BF_OK;
+    // (4) Algorithm 1 on the residual kernel
+    EntriesFn ent = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& Jc) {
+        CMat R((int64_t)I.size(), (int64_t)Jc.size());
+#pragma omp parallel for schedule(static)
+        for (int64_t jj = 0; jj < (int64_t)Jc.size(); ++jj)
+            for (size_t ii = 0; ii < I.size(); ++ii) R((int64_t)ii, jj) = residual(I[ii], Jc[(size_t)jj]);
+        return R;
+    };
+    EntriesFn ent_adj = [&](const std::vector<int64_t>& I, const std::vector<int64_t>& Jc) {
+        CMat R((int64_t)Jc.size(), (int64_t)I.size());
+#pragma omp parallel for schedule(static)
+        for (int64_t ii = 0; ii < (int64_t)I.size(); ++ii)
+            for (size_t jj = 0; jj < Jc.size(); ++jj) R((int64_t)jj, ii) = std::conj(residual(I[(size_t)ii], Jc[jj]));
+        return R;
+    };
+    std::vector<cd> ua, ub;
+    double sig = 0;
+    bf_status st = lowrank_sampled(ent, ent_adj, N, r_eps, q, eps, seed * 0x9E3779B97F4A7C15ull + 707, ua, ub,
+                                   terms, sig, {}, {});
+    return st;
+}
+
 }  // namespace bfi
+
+extern "C" bf_status bf_nufft_decide(const bf_plan* plan, int block, int r, int r_eps, int q, double eps,
+                                     uint64_t seed, int* y, int* n, int* terms)
+{
+    if (!plan || !y || !n || !terms || r < 1 || r_eps < 1 || q < 1 || !(eps > 0.0)) {
+        bfi::set_error("bf_nufft_decide: bad argument (non-NULL plan and outputs, r, r_eps, q >= 1, eps > 0)");
+        return BF_ERR_ARG;
+    }
+    if (!plan->factored || block < 0 || block >= (int)plan->blocks.size()) {
+        bfi::set_error("bf_nufft_decide: plan not factored or bad block");
+        return plan->factored ? BF_ERR_ARG : BF_ERR_STATE;
+    }
+    const bfi::BlockFactors& B = plan->blocks[(size_t)block];
+    if (B.lr.rank < 1 || B.lr.p.empty() || B.a.empty()) {
+        bfi::set_error("bf_nufft_decide: the plan has no recovered phase (factor it from its entries: "
+                       "bf_options.indirect or BF_PHASE_ENTRIES)");
+        return BF_ERR_STATE;
+    }
+    try {
+        return bfi::nufft_decide(B, r, r_eps, q, eps, seed, *y, *n, *terms);
+    } catch (const std::bad_alloc&) {
+        bfi::set_error("bf_nufft_decide: out of host memory");
+        return BF_ERR_NOMEM;
+    }
+}
 
 extern "C" bf_status bf_unwrap(const double* u, int64_t n, double tau, const double* seed, int nseed, double* v,
                                int64_t* starts, int64_t cap, int64_t* nstarts)

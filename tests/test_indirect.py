@@ -216,3 +216,56 @@ def test_recovery_matches_oracle_algorithms_3_to_5(N, kind, okind, s, amp):
     d = Pl[:, S].T @ Ql[:, S] - orc.phase_turns(K)
     d -= np.round(d)
     assert np.sqrt(np.mean(d ** 2)) < bound
+
+
+def _factors(p, N):
+    return (p.view(11).reshape(-1, N).real, p.view(12).reshape(-1, N).real,
+            p.view(0).reshape(-1, N), p.view(1).reshape(-1, N))
+
+
+@pytest.mark.parametrize("name,N,kw,r,expect_y", [
+    ("DFT", 1024, dict(phase_kind=L.PHASE_DFT, amp_kind=L.AMP_ONE), 1, 1),
+    ("SEP", 1024, dict(phase_kind=L.PHASE_SEP, amp_kind=L.AMP_SMOOTH), 1, 1),
+    ("SEP", 1024, dict(phase_kind=L.PHASE_SEP, amp_kind=L.AMP_SMOOTH), 2, 1),
+    ("FIO", 1024, dict(amp_kind=L.AMP_SMOOTH), 2, 0),
+    ("FIO", 4096, dict(amp_kind=L.AMP_SMOOTH), 3, 1),
+    ("Hankel", 1024, None, 3, 0)])
+def test_nufft_decision_matches_oracle_algorithm_6(name, N, kw, r, expect_y):
+    # Algorithm 6 (Sec. 3) on the plan's recovered factorizations, in the library (C++)
+    # and in the oracle (numpy) on the same factors.  The decision y is unique: equal.  A
+    # low-rank residual (y = 1) has the same numerical rank n and number of NUFFTs on any
+    # column sample: equal too; a full-rank one gives n >= r_eps on both sides.
+    # Expected decisions: the DFT's phase is rank 1 and the separable phase rank 2, so
+    # lifting leaves the amplitude (or a smooth residual); the recovered FIO phase has
+    # rank 3 (x xi, c(x)|xi| and the integer offsets of Algorithm 4's blocks), so r = 2
+    # leaves a winding residual and r = 3 leaves the amplitude (n = r_alpha = 2); the
+    # Hankel phase (rank 14 at N = 1024) needs more than 3 lifted dimensions: butterfly.
+    from oracle import decide as dc
+    if name == "Hankel":
+        from oracle import special as sp
+        ent = lambda I, J: sp.hankel1(J.astype(float), sp.hankel_x(N, I))
+        p = api.Plan(N, r=10, entries=ent, amp_rank=20, amp_oversample=5)
+    else:
+        p = api.Plan(N, eps=1e-6, indirect=True, **kw)
+    r_eps, q, eps = 20, 5, 1e-10
+    y, n, terms = p.nufft_decide(r, r_eps=r_eps, q=q, eps=eps)
+    yo, no, to = dc.nufft_decide(*_factors(p, N), r, r_eps, q, eps)
+    assert y == yo == expect_y
+    if y:
+        assert (n, terms) == (no, to) and 1 <= terms <= r_eps
+    else:
+        assert n >= r_eps and no >= r_eps and terms == to == 0
+    if name == "FIO" and y:
+        assert n == terms == 2
+
+
+def test_nufft_decision_refusals():
+    p = api.Plan(1024, eps=1e-6, amp_kind=L.AMP_SMOOTH)                 # explicit phase: no recovered Psi
+    with pytest.raises(L.BFError) as e:
+        p.nufft_decide(2)
+    assert e.value.status == L.BF_ERR_STATE
+    pi = api.Plan(1024, eps=1e-6, amp_kind=L.AMP_SMOOTH, indirect=True)
+    for bad in (dict(r=0), dict(r=2, r_eps=0), dict(r=2, q=0), dict(r=2, eps=0.0), dict(r=2, block=1)):
+        with pytest.raises(L.BFError) as e:
+            pi.nufft_decide(**bad)
+        assert e.value.status == L.BF_ERR_ARG
