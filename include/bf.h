@@ -88,6 +88,12 @@ typedef void (*bf_amp_fn)(double x, double xi, void* user, double* re, double* i
  * 0 <= i, j < N, as out[2k] + i out[2k+1].  Called from one thread at a time, with n up to
  * 2^20. */
 typedef void (*bf_entries_fn)(const int64_t* i, const int64_t* j, int64_t n, void* user, double* out);
+/* Products with the kernel matrix (indirect access, Scenario 2 of Table sc): writes
+ * Y = K X (transpose = 0) or Y = K^T X (transpose = 1, no conjugation) for m vectors.
+ * X and Y are host arrays [N][m] of complex numbers (re, im interleaved; the right-hand
+ * sides innermost, as F and G of bf_apply).  Called from one thread at a time; the
+ * library applies it to unit vectors to read whole columns (K e_j) and rows (K^T e_i). */
+typedef void (*bf_matvec_fn)(const double* X, int64_t m, int transpose, void* user, double* Y);
 
 /* The operator: the N x N transform on the grid x_i = i/N, xi_j = j - N/2. */
 typedef struct {
@@ -104,6 +110,9 @@ typedef struct {
     bf_entries_fn entries;/* the same in bulk by grid indices; with             *
                            * BF_PHASE_ENTRIES it is used instead of entry when  *
                            * not NULL                                            */
+    bf_matvec_fn matvec;  /* with BF_PHASE_ENTRIES and entries NULL: K known     *
+                           * only through products with K and K^T (Scenario 2);  *
+                           * used instead of entry when not NULL                 */
 } bf_kernel_desc;
 
 typedef struct {

@@ -25,12 +25,14 @@ AMP_FN = ctypes.CFUNCTYPE(None, ctypes.c_double, ctypes.c_double, ctypes.c_void_
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
 ENTRIES_FN = ctypes.CFUNCTYPE(None, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
                               ctypes.c_void_p, ctypes.POINTER(ctypes.c_double))
+MATVEC_FN = ctypes.CFUNCTYPE(None, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                             ctypes.POINTER(ctypes.c_double))
 
 
 class KernelDesc(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("phase_kind", ctypes.c_int), ("phase_param", ctypes.c_double),
                 ("amp_kind", ctypes.c_int), ("phi", PHASE_FN), ("alpha", AMP_FN), ("user", ctypes.c_void_p),
-                ("entry", AMP_FN), ("entries", ENTRIES_FN)]
+                ("entry", AMP_FN), ("entries", ENTRIES_FN), ("matvec", MATVEC_FN)]
 
 
 class Options(ctypes.Structure):

@@ -54,11 +54,13 @@ class Plan:
     def __init__(self, N, eps=1e-6, phase_kind=L.PHASE_FIO, phase_param=1.0, amp_kind=L.AMP_ONE,
                  r=0, n0=1, split=1, seed=0, keep_host=True, device=0, factor=True, phi=None, alpha=None,
                  factor_on_device=False, on_the_fly=False, indirect=False, entry=None, entries=None,
-                 amp_rank=0, amp_oversample=0, phase_rank=0, phase_oversample=0, _handle=None):
+                 matvec=None, amp_rank=0, amp_oversample=0, phase_rank=0, phase_oversample=0, _handle=None):
         """``indirect``: factor from the kernel's entries alone (amplitude and phase
         recovered, Algorithms 1 and 3-5).  A kernel without a built-in kind is given by
         ``entry(x, xi) -> complex`` or, in bulk, ``entries(i, j) -> complex array`` over
-        grid index arrays (x_i = i/N, xi_j = j - N/2); either implies indirect.
+        grid index arrays (x_i = i/N, xi_j = j - N/2); either implies indirect.  A kernel
+        known only through products (Scenario 2) is given by ``matvec(X, transpose) -> Y``,
+        Y = K X or K^T X for a complex array X of shape (N, m); it implies indirect too.
         ``amp_rank``, ``amp_oversample`` (``phase_rank``, ``phase_oversample``): Algorithm 1's
         rank parameter and oversampling for the amplitude (the recovered phase); 0: the
         library's defaults."""
@@ -102,9 +104,18 @@ class Plan:
                 self._keep.append(cb4)
                 d.entries = cb4
                 d.phase_kind = L.PHASE_ENTRIES
+            if matvec is not None:
+                def _mv(xp, m, tr, u, yp):
+                    X = np.ctypeslib.as_array(xp, shape=(2 * N * m,)).view(np.complex128).reshape(N, m)
+                    Y = np.ctypeslib.as_array(yp, shape=(2 * N * m,)).view(np.complex128).reshape(N, m)
+                    Y[:] = np.asarray(matvec(X, bool(tr)), dtype=np.complex128).reshape(N, m)
+                cb5 = L.MATVEC_FN(_mv)
+                self._keep.append(cb5)
+                d.matvec = cb5
+                d.phase_kind = L.PHASE_ENTRIES
             o = default_options()
             o.r, o.n0, o.split, o.seed, o.keep_host, o.device = r, n0, split, seed, int(keep_host), device
-            o.indirect = int(indirect or entry is not None or entries is not None)
+            o.indirect = int(indirect or entry is not None or entries is not None or matvec is not None)
             if amp_rank:
                 o.amp_rank = amp_rank
             if amp_oversample:

@@ -70,8 +70,46 @@ cd KernelFn::amplitude(int64_t i, int64_t j) const
     return indirect ? cd(std::abs(entry(i, j))) : amplitude_explicit(i, j);
 }
 
+void KernelFn::entries_matvec(const int64_t* I, const int64_t* J, int64_t n, cd* out) const
+{
+    // serve the pairs from whole columns when they touch fewer distinct columns than
+    // rows, else from whole rows; unit vectors go through the callback in blocks of nb
+    const int64_t Ng = n_global;
+    std::vector<int64_t> rows(I, I + n), cols(J, J + n);
+    for (auto* v : {&rows, &cols}) {
+        std::sort(v->begin(), v->end());
+        v->erase(std::unique(v->begin(), v->end()), v->end());
+    }
+    const bool by_cols = cols.size() <= rows.size();
+    const std::vector<int64_t>& keys = by_cols ? cols : rows;
+    std::vector<int64_t> kidx((size_t)n);
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < n; ++t)
+        kidx[(size_t)t] = std::lower_bound(keys.begin(), keys.end(), by_cols ? J[t] : I[t]) - keys.begin();
+    const int64_t nk = (int64_t)keys.size();
+    const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(64, ((int64_t)1 << 23) / Ng));  // <= 128 MB per buffer
+    std::vector<cd> X((size_t)(Ng * std::min(nb, nk))), Y(X.size());
+    for (int64_t k0 = 0; k0 < nk; k0 += nb) {
+        const int64_t w = std::min(nb, nk - k0);
+        std::fill(X.begin(), X.begin() + Ng * w, cd(0));
+        for (int64_t c = 0; c < w; ++c) X[(size_t)(keys[(size_t)(k0 + c)] * w + c)] = cd(1);
+        d.matvec(reinterpret_cast<const double*>(X.data()), w, by_cols ? 0 : 1, d.user,
+                 reinterpret_cast<double*>(Y.data()));
+#pragma omp parallel for schedule(static)
+        for (int64_t t = 0; t < n; ++t) {
+            const int64_t c = kidx[(size_t)t] - k0;
+            if (c < 0 || c >= w) continue;
+            out[t] = Y[(size_t)((by_cols ? I[t] : J[t]) * w + c)];   // (K e_j)[i] or (K^T e_i)[j]
+        }
+    }
+}
+
 void KernelFn::entries(const int64_t* I, const int64_t* J, int64_t n, cd* out) const
 {
+    if (bulk() && !d.entries) {
+        entries_matvec(I, J, n, out);
+        return;
+    }
     if (bulk()) {
         constexpr int64_t kPiece = (int64_t)1 << 20;
         for (int64_t s = 0; s < n; s += kPiece)
@@ -86,7 +124,7 @@ cd KernelFn::entry(int64_t i, int64_t j) const
 {
     if (bulk()) {
         cd v;
-        d.entries(&i, &j, 1, d.user, reinterpret_cast<double*>(&v));
+        entries(&i, &j, 1, &v);
         return v;
     }
     if (d.phase_kind == BF_PHASE_ENTRIES) {

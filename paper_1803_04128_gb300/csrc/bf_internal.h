@@ -46,7 +46,9 @@ struct KernelFn {
     // K at n index pairs; a bulk callback is called from this thread in pieces of at most
     // 2^20 entries, other sources are evaluated in parallel
     void entries(const int64_t* I, const int64_t* J, int64_t n, cd* out) const;
-    bool bulk() const { return d.phase_kind == BF_PHASE_ENTRIES && d.entries; }
+    bool bulk() const { return d.phase_kind == BF_PHASE_ENTRIES && (d.entries || d.matvec); }
+    // Scenario 2: the requested entries read off whole columns K e_j or rows K^T e_i
+    void entries_matvec(const int64_t* I, const int64_t* J, int64_t n, cd* out) const;
     // the explicit definitions (kinds and callbacks of d), whatever indirect says
     double phase_frac_explicit(int64_t i, int64_t j) const;
     cd amplitude_explicit(int64_t i, int64_t j) const;

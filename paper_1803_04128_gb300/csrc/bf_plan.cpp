@@ -103,8 +103,8 @@ bf_status bf_plan_create(const bf_kernel_desc* desc, double eps, const bf_option
     }
     int pk = desc->phase_kind, ak = desc->amp_kind;
     const bool entries = pk == BF_PHASE_ENTRIES;
-    if (!(pk >= 0 && pk <= 4) && !(pk == BF_PHASE_USER && desc->phi) && !(entries && (desc->entry || desc->entries))) {
-        set_error("bf_plan_create: bad phase_kind %d (or missing phi / entry callback)", pk);
+    if (!(pk >= 0 && pk <= 4) && !(pk == BF_PHASE_USER && desc->phi) && !(entries && (desc->entry || desc->entries || desc->matvec))) {
+        set_error("bf_plan_create: bad phase_kind %d (or missing phi / entry / matvec callback)", pk);
         return BF_ERR_ARG;
     }
     if (!entries && !(ak == 0 || ak == 1) && !(ak == BF_AMP_USER && desc->alpha)) {

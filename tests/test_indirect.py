@@ -269,3 +269,39 @@ def test_nufft_decision_refusals():
         with pytest.raises(L.BFError) as e:
             pi.nufft_decide(**bad)
         assert e.value.status == L.BF_ERR_ARG
+
+
+def test_scenario2_plan_from_products_only():
+    # Scenario 2 of Table sc (Algorithm 5's second branch): K is reached only through
+    # Y = K X and Y = K^T X; the columns and rows Algorithms 1 and 3-5 ask for are K e_j and
+    # K^T e_i.  The plan must equal the one factored from entries (the same entries reach
+    # both), meet the direct sum to its eps, and use a number of products that does not
+    # grow with N (O(1) matvecs, so O(N log N) work with a fast matvec).
+    used = {}
+    for N in (1024, 4096):
+        K = od.entries(od.FIO, N, np.arange(N), np.arange(N), s=1.0, amp=1)
+        count = [0]
+
+        def mv(X, transpose):
+            count[0] += X.shape[1]
+            return (K.T if transpose else K) @ X
+        p2 = api.Plan(N, eps=1e-6, matvec=mv)
+        p1 = api.Plan(N, eps=1e-6, amp_kind=L.AMP_SMOOTH, indirect=True)
+        i2 = p2.info()
+        assert i2["phase_rank"] == 3 and i2["r_alpha"] == 2
+        F = inputs.complex_gaussian(N, 2, seed=71)
+        g2 = factored_ref.apply(p2, F)
+        assert relerr(g2, factored_ref.apply(p1, F)) < 1e-12
+        assert relerr(g2, od.direct(od.FIO, N, F, amp=1)) < 1e-6
+        used[N] = count[0]
+    assert used[4096] <= 1.1 * used[1024] and used[4096] < 1500
+
+
+def test_scenario2_transpose_reads_rows():
+    # a kernel whose rows differ from its columns (FIO_PW, split at the jump): served only
+    # through products, the four sub-BF plans meet the direct sum
+    N = 2048
+    K = od.entries(od.FIOPW, N, np.arange(N), np.arange(N), s=1.0, amp=1)
+    p = api.Plan(N, eps=1e-6, matvec=lambda X, t: (K.T if t else K) @ X, split=2)
+    F = inputs.complex_gaussian(N, 2, seed=72)
+    assert relerr(factored_ref.apply(p, F), od.direct(od.FIOPW, N, F, amp=1)) < 1e-6
