@@ -174,11 +174,14 @@ bf_status bf_default_options(bf_options* opt);
 bf_status bf_unwrap(const double* u, int64_t n, double tau, const double* seed, int nseed, double* v,
                     int64_t* starts, int64_t cap, int64_t* nstarts);
 
-/* Algorithm 6 (Sec. 3): may sub-BF `block` of a plan factored from its entries (indirect
- * access) be evaluated by r-dimensional NUFFTs after dimension lifting (Eq. tg3), or does
- * it need the butterfly?  Inputs are the plan's recovered factorizations: the phase
- * Psi = Re sum_k p_k(x) q_k(xi) of rank r1 = phase_rank (bf_plan_view 11, 12) and the
- * amplitude alpha = sum_k a_k(x) b_k(xi) (views 0, 1).  Steps:
+/* Algorithm 6 (Sec. 3): may sub-BF `block` of a plan be evaluated by r-dimensional NUFFTs
+ * after dimension lifting (Eq. tg3), or does it need the butterfly?  Inputs are low-rank
+ * factorizations of the phase, Psi = sum_k p_k(x) q_k(xi) of rank r1, and of the amplitude,
+ * alpha = sum_k a_k(x) b_k(xi) (views 0, 1).  For a plan factored from its entries the
+ * phase factors are the recovered ones (views 11, 12; r1 = phase_rank).  For a built-in
+ * phase they are its closed form in turns: DFT (x)(xi); FIO (x, c(x))(xi, |xi|); FIO_PW the
+ * same with c(x) for x < 1/2 and -c(x)/2 above; SEP (0.3 sin 2 pi x, 1)(1, xi^2 / 4N); ONES
+ * none.  Steps:
  *  1. the r-leading SVD of the phase factorization is the lifting P Q^T (taken exactly:
  *     QR of both N x r1 factors, then the SVD of the r1 x r1 core; r >= r1 lifts the
  *     whole phase);
@@ -191,7 +194,8 @@ bf_status bf_unwrap(const double* u, int64_t n, double tau, const double* seed, 
  *     Eq. tg3; otherwise *terms = 0.
  * Host only, O(N (r1^2 + r_eps q (r1 + r_alpha))) work; no NUFFT is run.  Errors:
  * BF_ERR_ARG (NULL plan or outputs, r, r_eps or q below 1, eps <= 0, bad block),
- * BF_ERR_STATE (plan not factored, or not factored from its entries), BF_ERR_NOMEM. */
+ * BF_ERR_STATE (plan not factored, host factors released, or a user phase callback,
+ * whose factorization is unknown), BF_ERR_NOMEM. */
 bf_status bf_nufft_decide(const bf_plan* plan, int block, int r, int r_eps, int q, double eps,
                           uint64_t seed, int* y, int* n, int* terms);
 

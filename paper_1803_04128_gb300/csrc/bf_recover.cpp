@@ -409,11 +409,10 @@ void recovery_errors(const KernelFn& k, BlockFactors& B, uint64_t seed)
 // with column pivoting; (3) n counts the pivots above eps times the first, y = 1 iff
 // n < r_eps; (4) if y = 1, Algorithm 1 (rank parameter r_eps) factors the residual
 // kernel and terms is its rank, the number of NUFFTs.
-bf_status nufft_decide(const BlockFactors& B, int r, int r_eps, int q, double eps, uint64_t seed, int& y,
-                       int& n, int& terms)
+bf_status nufft_decide(const BlockFactors& B, const PhaseLR& lr, int r, int r_eps, int q, double eps,
+                       uint64_t seed, int& y, int& n, int& terms)
 {
     const int64_t N = B.N;
-    const PhaseLR& lr = B.lr;
     const int r1 = lr.rank, ra = B.ra;
     // (1) U1 V1^T = Qa (Ra Rb^T) Qb^T, Ra = Qa^* U1, Rb = Qb^* V1; the core's SVD
     CMat U1(N, r1), V1(N, r1);
@@ -424,14 +423,20 @@ bf_status nufft_decide(const BlockFactors& B, int r, int r_eps, int q, double ep
         }
     CMat Qa, Qb, Uc, Vc;
     std::vector<int64_t> piv;
-    pivoted_qr(U1, r1, 0.0, Qa, piv);
-    pivoted_qr(V1, r1, 0.0, Qb, piv);
-    const CMat C = matmul(matmul(adjoint(Qa), U1), adjoint(matmul(adjoint(Qb), V1)));
     std::vector<double> S;
-    jacobi_svd(C, Uc, S, Vc);
+    if (r1 > 0) {  // a zero phase (rank 0) has nothing to lift
+        pivoted_qr(U1, r1, 0.0, Qa, piv);
+        pivoted_qr(V1, r1, 0.0, Qb, piv);
+        const CMat C = matmul(matmul(adjoint(Qa), U1), adjoint(matmul(adjoint(Qb), V1)));
+        jacobi_svd(C, Uc, S, Vc);
+    }
     const int kr = std::min<int>(r, (int)S.size());
     // lift(i, j) = sum_l P(i, l) Q(j, l), P = Qa Uc S, Q = conj(Qb Vc), first kr columns
-    CMat P = matmul(Qa, Uc), Q = matmul(Qb, Vc);
+    CMat P, Q;
+    if (kr > 0) {
+        P = matmul(Qa, Uc);
+        Q = matmul(Qb, Vc);
+    }
     std::vector<double> Pl((size_t)(kr * N)), Ql((size_t)(kr * N));
     for (int l = 0; l < kr; ++l)
         for (int64_t i = 0; i < N; ++i) {
@@ -503,13 +508,60 @@ extern "C" bf_status bf_nufft_decide(const bf_plan* plan, int block, int r, int 
         return plan->factored ? BF_ERR_ARG : BF_ERR_STATE;
     }
     const bfi::BlockFactors& B = plan->blocks[(size_t)block];
-    if (B.lr.rank < 1 || B.lr.p.empty() || B.a.empty()) {
-        bfi::set_error("bf_nufft_decide: the plan has no recovered phase (factor it from its entries: "
-                       "bf_options.indirect or BF_PHASE_ENTRIES)");
+    if (B.a.empty()) {
+        bfi::set_error("bf_nufft_decide: host factors were released after upload");
         return BF_ERR_STATE;
     }
     try {
-        return bfi::nufft_decide(B, r, r_eps, q, eps, seed, *y, *n, *terms);
+        if (B.lr.rank >= 1) return bfi::nufft_decide(B, B.lr, r, r_eps, q, eps, seed, *y, *n, *terms);
+        // an explicit built-in phase: its factors in closed form (turns, not reduced mod 1)
+        // on the window's rows x_i = i / N_g and columns xi_j = j - N_g / 2
+        const bf_kernel_desc& d = plan->kern.d;
+        const int64_t Nb = B.N, Ng = plan->kern.n_global;
+        const double s = d.phase_param;
+        std::vector<std::vector<double>> pr, qc;  // factor functions of x and of xi
+        auto add = [&](auto fx, auto fxi) {
+            std::vector<double> a((size_t)Nb), b((size_t)Nb);
+            for (int64_t t = 0; t < Nb; ++t) {
+                a[(size_t)t] = fx((double)(B.row0 + t) / (double)Ng);
+                b[(size_t)t] = fxi((double)(B.col0 + t - Ng / 2));
+            }
+            pr.push_back(std::move(a));
+            qc.push_back(std::move(b));
+        };
+        auto cx = [&](double x) { return (2.0 + s * std::sin(bfi::kTwoPi * x)) / 16.0; };
+        switch (d.phase_kind) {
+        case BF_PHASE_DFT: add([](double x) { return x; }, [](double xi) { return xi; }); break;
+        case BF_PHASE_FIO:
+            add([](double x) { return x; }, [](double xi) { return xi; });
+            add(cx, [](double xi) { return std::fabs(xi); });
+            break;
+        case BF_PHASE_FIO_PW:
+            add([](double x) { return x; }, [](double xi) { return xi; });
+            add([&](double x) { return x < 0.5 ? cx(x) : -0.5 * cx(x); }, [](double xi) { return std::fabs(xi); });
+            break;
+        case BF_PHASE_ONES: break;
+        case BF_PHASE_SEP:
+            add([](double x) { return 0.3 * std::sin(bfi::kTwoPi * x); }, [](double) { return 1.0; });
+            add([](double) { return 1.0; }, [&](double xi) { return xi * xi / (4.0 * (double)Ng); });
+            break;
+        default:
+            bfi::set_error("bf_nufft_decide: a user phase has no factorization (factor the plan from its entries)");
+            return BF_ERR_STATE;
+        }
+        bfi::PhaseLR lr;
+        lr.row0 = B.row0;
+        lr.col0 = B.col0;
+        lr.N = Nb;
+        lr.rank = (int)pr.size();
+        for (int k = 0; k < lr.rank; ++k)
+            for (int64_t t = 0; t < Nb; ++t) {
+                lr.p.push_back(pr[(size_t)k][(size_t)t]);
+                lr.q.push_back(0.0);
+            }
+        for (int k = 0; k < lr.rank; ++k)
+            for (int64_t t = 0; t < Nb; ++t) lr.q[(size_t)k * Nb + t] = qc[(size_t)k][(size_t)t];
+        return bfi::nufft_decide(B, lr, r, r_eps, q, eps, seed, *y, *n, *terms);
     } catch (const std::bad_alloc&) {
         bfi::set_error("bf_nufft_decide: out of host memory");
         return BF_ERR_NOMEM;

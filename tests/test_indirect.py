@@ -259,8 +259,28 @@ def test_nufft_decision_matches_oracle_algorithm_6(name, N, kw, r, expect_y):
         assert n == terms == 2
 
 
+@pytest.mark.parametrize("N", [1024, 4096])
+def test_nufft_decision_explicit_phases(N):
+    # explicit built-in phases go in with their closed-form factors: FIO (x, c(x)), (xi, |xi|)
+    # is lifted whole at r = 2 (NUFFTs apply, one per amplitude term) and not at r = 1; the
+    # oracle decides the same on the same factors.  In the split piecewise phase the first
+    # sub-BF (x < 1/2, xi < 0) has Phi = (x - c(x)) xi: rank 1, so r = 1 suffices there.
+    from oracle import decide as dc
+    x, xi = np.arange(N) / N, np.arange(N) - N / 2.0
+    c = (2 + np.sin(2 * np.pi * x)) / 16
+    p = api.Plan(N, eps=1e-6, amp_kind=L.AMP_SMOOTH)
+    a, b = p.view(0).reshape(-1, N), p.view(1).reshape(-1, N)
+    for r, want in ((1, 0), (2, 1)):
+        got = p.nufft_decide(r)
+        assert got[0] == want and got == dc.nufft_decide(np.stack([x, c]), np.stack([xi, np.abs(xi)]), a, b, r, 20)
+    assert p.nufft_decide(2) == (1, 2, 2)
+    pw = api.Plan(N, eps=1e-6, phase_kind=L.PHASE_FIO_PW, amp_kind=L.AMP_SMOOTH, split=2)
+    assert pw.nufft_decide(1, block=0) == (1, 2, 2)
+    assert api.Plan(N, eps=1e-6, phase_kind=L.PHASE_DFT).nufft_decide(1) == (1, 1, 1)
+
+
 def test_nufft_decision_refusals():
-    p = api.Plan(1024, eps=1e-6, amp_kind=L.AMP_SMOOTH)                 # explicit phase: no recovered Psi
+    p = api.Plan(256, r=8, phase_kind=L.PHASE_USER, phi=lambda x, xi: x * xi)     # no factorization known
     with pytest.raises(L.BFError) as e:
         p.nufft_decide(2)
     assert e.value.status == L.BF_ERR_STATE
