@@ -298,8 +298,50 @@ def serve_trace(srv, ops, pools, times, opi, ms, warm_s):
     return st
 
 
-def run_serving(args, w, rank, world, local):
-    """Continuous-batching server vs the plain per-request FP64 form (config 5)."""
+def oracle_rows_err(w, Fh, Gh, nrows, seed=17, G_rows=None):
+    """Relative l2 error (the paper's eps^b over the sampled set) of a GPU result
+    against the FP64 direct oracle on ``nrows`` sampled rows, all RHS."""
+    import numpy as np
+    from oracle import direct as od
+    from paper_1803_04128_gb300 import inputs
+    rows = inputs.sample_rows(w["N"], nrows, seed=seed)
+    gd = od.direct(w["phase"], w["N"], Fh, rows, amp=w["amp"])
+    g = (Gh[rows] if G_rows is None else G_rows).astype(np.complex128)
+    return float(np.linalg.norm(g - gd) / np.linalg.norm(gd)), int(rows.size)
+
+
+def alu_peak_info(local):
+    """FP32 FMA peak: derived from the device's SM count and the measured maximum SM
+    clock (128 FP32 lanes x 2 flop per SM per clock), with the register-only FMA
+    loop's measured figure beside it."""
+    import torch
+    from paper_1803_04128_gb300 import api
+    peaks, src = load_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    derived = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    try:
+        sms2, loop = api.fp32_peak(local)
+    except Exception:
+        loop = None
+    return {"peak": derived, "sms": sms, "sm_max_mhz": mhz, "ffma_loop_tflops": loop,
+            "peak_source": "%d SMs (from the device) x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)"
+                           % (sms, mhz, src)}
+
+
+def alu_roof(kernel, flops, avg_ms, alu, traffic=None, **extra):
+    achieved = flops / (avg_ms * 1e-3) / 1e12
+    d = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": alu["peak"], "unit": "TFLOP/s",
+         "frac": achieved / alu["peak"], "traffic": traffic, "peak_source": alu["peak_source"],
+         "ffma_loop_tflops": alu["ffma_loop_tflops"],
+         "frac_of_ffma_loop": (achieved / alu["ffma_loop_tflops"]) if alu["ffma_loop_tflops"] else None}
+    d.update(extra)
+    return d
+
+
+def run_serving(args, w, rank, world, local, side=False):
+    """Continuous-batching server vs the plain per-request FP64 form (config 5).
+    Returns the JSON line (side=True: shorter windows, for the default run)."""
     import numpy as np
     import torch
 
@@ -308,9 +350,13 @@ def run_serving(args, w, rank, world, local):
     Ns = [2 ** 14, 2 ** 16, 2 ** 18, 2 ** 20]
     mset = (1, 4, 16, 64)
     t0 = time.perf_counter()
-    plans = [api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], device=local) for N in Ns]
+    # phase tables built on the device (same factors as the host build, seconds faster at N = 2^20)
+    plans = [api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], device=local,
+                      factor_on_device=True) for N in Ns]
     t_factor = time.perf_counter() - t0
     warm = 1.0
+    secs, secs_light, secs_plain = ((4.0, 3.0, 2.0) if side else
+                                    (w["seconds"], w["seconds_light"], min(3.0, w["seconds"])))
 
     def pools_for(cdt):
         out = {}
@@ -321,13 +367,14 @@ def run_serving(args, w, rank, world, local):
         return out
 
     results = {}
+    errs = {}
     # the offered rate of the workload (above the GPU's capacity: throughput under
     # overload), a light rate the server sustains (latency), and the plain form
-    runs = (("batched_f32", api.F32, 4, False, torch.complex64, w["rate"], w["seconds"]),
-            ("batched_f32_light", api.F32, 4, False, torch.complex64, w["rate_light"], w["seconds_light"]),
-            ("plain_f64_per_request", api.F64, 1, True, torch.complex128, w["rate"], min(3.0, w["seconds"])))
-    for name, prec, slots, per_req, cdt, rate, secs in runs:
-        window = warm + secs
+    runs = (("batched_f32", api.F32, 4, False, torch.complex64, w["rate"], secs),
+            ("batched_f32_light", api.F32, 4, False, torch.complex64, w["rate_light"], secs_light),
+            ("plain_f64_per_request", api.F64, 1, True, torch.complex128, w["rate"], secs_plain))
+    for name, prec, slots, per_req, cdt, rate, secs_run in runs:
+        window = warm + secs_run
         times, opi, ms = inputs.poisson_requests(rate, window, len(Ns), mset, seed=rank)
         srv = api.Server(n_slots=slots, max_batch_rhs=256, precision=prec, per_request=per_req, device=local)
         ops = [srv.add(p) for p in plans]
@@ -340,8 +387,22 @@ def run_serving(args, w, rank, world, local):
         st["window_s"] = window - warm
         st["served_req_per_s"] = st["completed"] / st["wall_s"] if st["wall_s"] > 0 else 0.0
         results[name] = st
-        srv.close()
+        if name == "batched_f32_light":
+            # the light run's queue empties: once drained, every pool buffer that served a
+            # request holds that request's result (one fixed F per (operator, m)); sampled
+            # rows of the N = 2^16 operator's m = 16 result against the oracle
+            srv.drain()
+            o, mm = 1, 16
+            if any(int(a) == o and int(b) == mm for a, b in zip(opi, ms)):
+                Fh = inputs.complex_gaussian(Ns[o], mm, seed=o * 100 + mm)
+                errs["batched_f32"] = oracle_rows_err(dict(w, N=Ns[o]), Fh, pools[(o, mm)][1].numpy(), 48)[0]
+        srv.close()                        # drops requests still queued (the overloaded runs)
         del pools
+    # the plain form's arithmetic (FP64 stage launches, one request) on the same operator and F
+    Fh = inputs.complex_gaussian(Ns[1], 16, seed=116)
+    Gp = plans[1].apply(torch.from_numpy(Fh).cuda(), prec=api.F64)
+    torch.cuda.synchronize()
+    errs["plain_f64_per_request"] = oracle_rows_err(dict(w, N=Ns[1]), Fh, Gp.cpu().numpy(), 48)[0]
     b = results["batched_f32"]
     bl = results["batched_f32_light"]
     p = results["plain_f64_per_request"]
@@ -351,39 +412,57 @@ def run_serving(args, w, rank, world, local):
         t = torch.tensor([b["units_per_s"]], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         units_all = float(t.item())
-    if rank == 0:
-        cfg = {"workload": w["desc"], "operators_N": Ns, "m_choices": list(mset), "r": plans[0].info()["r"],
-               "eps": w["eps"], "t_factor_s": round(t_factor, 2), "warmup_s": warm,
-               "batched_f32": {k: v for k, v in b.items() if k != "clocks"},
-               "batched_f32_light": {k: v for k, v in bl.items() if k != "clocks"},
-               "plain_f64_per_request": {k: v for k, v in p.items() if k != "clocks"},
-               "throughput_ratio_vs_plain": (b["units_per_s"] / p["units_per_s"]) if p["units_per_s"] else None,
-               "note": "stats over the arrival window after warm-up; requests still queued at its end are "
-                       "counted in 'pending' and not in the latency percentiles.  At the offered 2000 req/s the "
-                       "work arriving exceeds the GPU's capacity, so its p50/p99 measure queue growth over the "
-                       "window; p50_ms/p99_ms of this line are those of the light rate, which the server sustains"}
-        line = {"metric": METRIC, "value": units_all / 1e9, "unit": UNIT, "n_gpus": world,
-                "steps": int(b["completed"]), "warmup": warm, "ms_per_step": b["mean_ms"],
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic (seeded complex Gaussian F; analytic kernel; Poisson arrivals)", "config": cfg,
-                "p50_ms": bl["p50_ms"], "p99_ms": bl["p99_ms"], "p99_ms_at_offered_rate": b["p99_ms"],
-                "roofline": None, "cpu_baseline": None,
-                "e2e": {"value": units_all / 1e9, "unit": UNIT, "h2d_bytes_per_step": None,
-                        "d2h_bytes_per_step": None, "note": "requests are served from host buffers"},
-                "gpu_launches": None, "clocks": b["clocks"]}
-        print(json.dumps(line))
-    return 0
+    # algorithmic flops per served N.RHS unit, averaged over the trace's operator mix
+    flops_per_unit = 0.0
+    for pl, N in zip(plans, Ns):
+        fr, bk, _ = algorithmic(pl.info(), 1, N, 1)
+        flops_per_unit += (fr + bk) / N / len(Ns)
+    r_used = plans[0].info()["r"]
+    for pl in plans:
+        pl.close()
+    cfg = {"workload": w["desc"], "operators_N": Ns, "m_choices": list(mset), "r": r_used,
+           "eps": w["eps"], "t_factor_s": round(t_factor, 2), "warmup_s": warm,
+           "batched_f32": {k: v for k, v in b.items() if k != "clocks"},
+           "batched_f32_light": {k: v for k, v in bl.items() if k != "clocks"},
+           "plain_f64_per_request": {k: v for k, v in p.items() if k != "clocks"},
+           "throughput_ratio_vs_plain": (b["units_per_s"] / p["units_per_s"]) if p["units_per_s"] else None,
+           "rel_err_vs_fp64_oracle": errs,
+           "rel_err_note": "48 sampled rows, all 16 RHS, of an N = 2^16, m = 16 request's result (served by the "
+                           "light run; the plain form's stage launches on the same operator and F)",
+           "note": "stats over the arrival window after warm-up; requests still queued at its end are "
+                   "counted in 'pending' and not in the latency percentiles.  At the offered 2000 req/s the "
+                   "work arriving exceeds the GPU's capacity, so its p50/p99 measure queue growth over the "
+                   "window; p50_ms/p99_ms of this line are those of the light rate, which the server sustains"}
+    alu = alu_peak_info(local)
+    ach = b["units_per_s"] * flops_per_unit / 1e12
+    roof = {"bound": "alu", "kernel": "all kernels of the served applies (front_f32, back_f32, level passes)",
+            "achieved": ach, "peak": alu["peak"], "unit": "TFLOP/s", "frac": ach / alu["peak"], "traffic": None,
+            "note": "algorithmic flops of the served N.RHS units (mean over the 4 operators) per second of the "
+                    "offered-rate window: a whole-server figure, copies and scheduling included",
+            "peak_source": alu["peak_source"]}
+    line = {"metric": METRIC, "value": units_all / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": int(b["completed"]), "warmup": warm, "ms_per_step": b["mean_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded complex Gaussian F; analytic kernel; Poisson arrivals)", "config": cfg,
+            "p50_ms": bl["p50_ms"], "p99_ms": bl["p99_ms"], "p99_ms_at_offered_rate": b["p99_ms"],
+            "roofline": roof, "cpu_baseline": None,
+            "e2e": {"value": units_all / 1e9, "unit": UNIT, "h2d_bytes_per_step": None,
+                    "d2h_bytes_per_step": None, "note": "requests are served from host buffers"},
+            "gpu_launches": int(b["launches"]), "clocks": b["clocks"]}
+    return line
 
 
-def run_batched(args, w, rank, world, local):
-    """32 uneven operators applied in one persistent launch replayed from a CUDA graph."""
+def run_batched(args, w, rank, world, local, steps=None, warmup=None):
+    """32 uneven operators applied in one persistent launch replayed from a CUDA graph.
+    Returns the JSON line."""
     import numpy as np
     import torch
     import torch.distributed as dist
 
-    from paper_1803_04128_gb300 import _lib as L
     from paper_1803_04128_gb300 import api, inputs
 
+    steps = steps or args.steps
+    warmup = warmup if warmup is not None else args.warmup
     shapes = inputs.uneven_batch(w["n_ops"], 12, 18, 1, 128, seed=0)
     t0 = time.perf_counter()
     plans = {}
@@ -408,30 +487,39 @@ def run_batched(args, w, rank, world, local):
     units = sum(N * m for N, m in shapes)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             flush.zero_()
             batch.replay(stream)
     stream.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with ClockSampler(local) as clk:
-        with api.KernelTimer() as kt:
-            with torch.cuda.stream(stream):
-                for i in range(args.steps):
-                    flush.zero_()
-                    ev[i][0].record(stream)
-                    batch.replay(stream)
-                    ev[i][1].record(stream)
-            stream.synchronize()
+        with torch.cuda.stream(stream):
+            for i in range(steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                batch.replay(stream)
+                ev[i][1].record(stream)
+        stream.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     assert batch.status(stream) == 0
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ms_max = max_over_ranks(ms, world, "cuda")
-    value = job_rate(world, units, args.steps, ms_max)
+    value = job_rate(world, units, steps, ms_max)
+    # sampled rows of every operator's result against the FP64 oracle
+    num = den = 0.0
+    for k, ((N, m), (plan, F, G)) in enumerate(zip(shapes, ops)):
+        rows = inputs.sample_rows(N, 8, seed=100 + k)
+        from oracle import direct as od
+        gd = od.direct(w["phase"], N, Fh[k], rows, amp=w["amp"])
+        g = G.cpu().numpy()[rows].astype(np.complex128)
+        num += float(np.linalg.norm(g - gd) ** 2)
+        den += float(np.linalg.norm(gd) ** 2)
+    rel_err = (num / den) ** 0.5
     # kernel time of the persistent launch, issued eagerly (graph replays bypass the launch hooks)
     with api.KernelTimer() as kt_eager:
         with torch.cuda.stream(stream):
@@ -439,18 +527,23 @@ def run_batched(args, w, rank, world, local):
                 flush.zero_()
                 batch.run(stream)
         stream.synchronize()
-    # the same 32 applies issued one operator at a time (2 launches each), for comparison
+    # the same 32 applies issued one operator at a time (2 launches each), for comparison,
+    # with the same L2 flush before each step
     torch.cuda.synchronize()
-    s0 = torch.cuda.Event(enable_timing=True)
-    s1 = torch.cuda.Event(enable_timing=True)
-    s0.record()
-    for _ in range(args.steps):
+    seq = []
+    for _ in range(steps):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record()
         for plan, F, G in ops:
             plan.apply(F, G, api.F32)
-    s1.record()
+        s1.record()
+        seq.append((s0, s1))
     torch.cuda.synchronize()
-    seq_ms = s0.elapsed_time(s1) / args.steps
+    seq_ms = sum(a.elapsed_time(b) for a, b in seq) / steps
     peaks, peak_src = load_peaks()
+    alu = alu_peak_info(local)
     flops = 0
     bytes_apply = 0
     for N, m in shapes:
@@ -458,22 +551,18 @@ def run_batched(args, w, rank, world, local):
         fr, bk, by = algorithmic(info, m, N, 1)
         flops += fr + bk
         bytes_apply += by
-    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     nb, tb = kt_eager.result.get("batch_f32", (0, 0.0))
     roof = None
     if nb:
-        achieved = flops / (tb / nb * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "batch_f32", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": ncu_traffic("batch_f32", args.workload, None),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s)" % (peaks.get("sm_max_mhz", 2070.0), peak_src),
-                "kernel_ms": {k: v[1] / v[0] for k, v in kt_eager.result.items()}}
+        roof = alu_roof("batch_f32", flops, tb / nb, alu, ncu_traffic("batch_f32", "fio4", None),
+                        kernel_ms={k: v[1] / v[0] for k, v in kt_eager.result.items()})
     # end to end: pinned host F in, graph replay, G out
     Fp = [torch.from_numpy(f).to(torch.complex64).pin_memory() for f in Fh]
     Gp = [torch.empty_like(x).pin_memory() for x in Fp]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        for _ in range(args.steps):
+        for _ in range(steps):
             for (plan, F, G), fp in zip(ops, Fp):
                 F.copy_(fp, non_blocking=True)
             batch.replay(stream)
@@ -482,27 +571,27 @@ def run_batched(args, w, rank, world, local):
             stream.synchronize()
     t_e2e = time.perf_counter() - t0
     nbytes = sum(x.numel() * x.element_size() for x in Fp)
-    if rank == 0:
-        cfg = {"workload": w["desc"], "n_ops": len(shapes), "shapes": shapes, "units_per_step": units,
-               "r": plans[shapes[0][0]].info()["r"], "eps": w["eps"], "l2": "flushed (512 MB write) between timed steps",
-               "t_factor_s": round(t_factor, 2), "t_autotune_s": round(t_tune, 2),
-               "sequential_single_op_ms_per_step": seq_ms, "batched_ms_per_step": ms_max / args.steps,
-               "hbm_frac_of_measured": bytes_apply / (ms_max / args.steps * 1e-3) / (peaks["hbm_gbs"] * 1e9),
-               "algorithmic_flops_per_step": flops, "algorithmic_bytes_per_step": bytes_apply,
-               "parallelism": "replicas" if world > 1 else "single GPU"}
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic (seeded complex Gaussian F; analytic kernel)", "config": cfg, "roofline": roof,
-                "cpu_baseline": None,
-                "e2e": {"value": world * units * args.steps / t_e2e / 1e9, "unit": UNIT,
-                        "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-                "gpu_launches": args.steps, "clocks": clk.summary()}
-        print(json.dumps(line))
+    cfg = {"workload": w["desc"], "n_ops": len(shapes), "shapes": shapes, "units_per_step": units,
+           "r": plans[shapes[0][0]].info()["r"], "eps": w["eps"], "l2": "flushed (512 MB write) between timed steps",
+           "t_factor_s": round(t_factor, 2), "t_autotune_s": round(t_tune, 2),
+           "sequential_single_op_ms_per_step": seq_ms, "batched_ms_per_step": ms_max / steps,
+           "speedup_batched_vs_sequential": seq_ms / (ms_max / steps),
+           "hbm_frac_of_measured": bytes_apply / (ms_max / steps * 1e-3) / (peaks["hbm_gbs"] * 1e9),
+           "algorithmic_flops_per_step": flops, "algorithmic_bytes_per_step": bytes_apply,
+           "rel_err_vs_fp64_oracle": rel_err, "rel_err_rows": "8 sampled rows of each of the 32 results, all RHS",
+           "parallelism": "replicas" if world > 1 else "single GPU"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded complex Gaussian F; analytic kernel)", "config": cfg, "roofline": roof,
+            "cpu_baseline": None,
+            "e2e": {"value": world * units * steps / t_e2e / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": steps, "clocks": clk.summary()}
     batch.close()
-    if world > 1:
-        dist.destroy_process_group()
-    return 0
+    for pl in plans.values():
+        pl.close()
+    return line
 
 
 def otf_side(args, w, plan, F, G, flush, stream, world, local, alu_peak, front, back):
@@ -579,6 +668,215 @@ def indirect_side(w, F, G, local):
                     "256 x 256 sampled entries"}
 
 
+def run_single(args, w, rank, world, local, steps, warmup, plan=None, sides=True, cpu_budget=None):
+    """One operator (or one split operator) applied to m right-hand sides: W warm-up
+    applies, then ``steps`` timed applies (CUDA events on the launching stream, L2
+    flushed between them).  Returns the JSON line.  ``plan``: an already factored plan
+    of the same operator (shared by two precisions of one workload)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1803_04128_gb300 import api, inputs
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    N, m = w["N"], w["m"]
+    prec = {"f64": api.F64, "f32": api.F32, "bf16x3": api.BF16X3}[w["prec"]]
+    cdt = torch.complex128 if prec == api.F64 else torch.complex64
+    otf = bool(w.get("otf"))
+    own_plan = plan is None
+    t_factor = t_factor_dev = None
+    if own_plan:
+        t0 = time.perf_counter()
+        plan = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
+                        on_the_fly=otf, factor_on_device=bool(w.get("factor_on_device")))
+        t_factor = time.perf_counter() - t0
+        # the same operator with its phase tables built on the GPU (bf_factor_device), for the record
+        if sides and not otf and not w.get("factor_on_device"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
+                     factor_on_device=True).close()
+            torch.cuda.synchronize()
+            t_factor_dev = time.perf_counter() - t0
+    info = plan.info()
+    mr_tuned = None
+    if prec == api.F32:
+        # column-slice width of the fused FP32 apply chosen by timing (off the timed region)
+        tune_path = os.path.join(tempfile.gettempdir(), "bf_autotune_bench_%d.txt" % os.getpid())
+        mr_tuned = api.autotune(plan, m, tune_path)
+    plan.reserve(prec, m)
+    Fh = inputs.complex_gaussian(N, m, seed=rank)
+    F = torch.from_numpy(Fh).to(cdt).cuda()
+    G = torch.empty_like(F)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(warmup):
+        flush.zero_()
+        plan.apply(F, G, prec)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    fk, bk = ("front_f32_otf", "back_f32_otf") if otf else ("front_f32", "back_f32")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with ClockSampler(local) as clk:
+        with api.KernelTimer() as kt:
+            torch.cuda.nvtx.range_push("timed")    # lets an ncu capture select the timed launches
+            for i in range(steps):
+                flush.zero_()                      # L2 flush between timed steps (not timed)
+                ev[i][0].record(stream)
+                plan.apply(F, G, prec)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+    barrier()
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = job_rate(world, N * m, steps, ms_max)
+
+    peaks, peak_src = load_peaks()
+    alu = alu_peak_info(local)
+    front, back, bytes_apply = algorithmic(info, m, N, w["split"])
+    roof = None
+    launches = sum(n for n, _ in kt.result.values())
+    tot = sum(v[1] for v in kt.result.values())
+    kms = {k: v[1] / v[0] for k, v in kt.result.items()}
+    share = {k: v[1] / tot for k, v in kt.result.items()} if tot else {}
+    if prec == api.F32 and any(k.startswith("mid_") for k in kt.result):
+        # level ranges split into passes (front, middle H and G passes, back): the
+        # apply's algorithmic flops over the summed time of all its passes
+        roof = alu_roof("all passes of one apply (front, mid_h, mid_g, back)", (front + back) * w["split"] ** 2,
+                        tot / steps, alu, None, kernel_ms=kms, share=share)
+    elif prec == api.F32 and fk in kt.result:
+        nf, tf = kt.result[fk]
+        nb, tb = kt.result[bk]
+        dom, n_l, t_l, flops = (fk, nf, tf, front) if tf >= tb else (bk, nb, tb, back)
+        roof = alu_roof(dom, flops, t_l / n_l, alu, ncu_traffic(dom, w["name"], m), kernel_ms=kms, share=share)
+    elif prec == api.BF16X3 and "front_tc" in kt.result:
+        tflops = tensor_flops(info, m, N, w["split"])
+        dom = max(("front_tc", "back_tc"), key=lambda k: kt.result[k][1])
+        n_l, t_l = kt.result[dom]
+        achieved = tflops[dom] / (t_l / n_l * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
+                "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops_sustained"],
+                "traffic": ncu_traffic(dom, w["name"], m),
+                "note": "tensor FLOPs issued (3 BF16 products per split product, zero padding to the MMA shape); "
+                        "peak: sustained cuBLAS BF16 (%s)" % peak_src,
+                "useful_alu_frac": (front + back) * w["split"] ** 2 / (tot / steps * 1e-3) / 1e12 / alu["peak"],
+                "kernel_ms": kms, "share": share}
+    elif kt.result:
+        # plain FP64 form: one launch per stage, state through HBM; the stages together
+        # are the apply, held to the HBM roofline with the apply's algorithmic bytes (c128)
+        achieved = 2 * bytes_apply / (tot / steps * 1e-3) / 1e9  # complex128
+        roof = {"bound": "hbm", "kernel": "plain FP64 stages (v/h/s/g/u_f64) per apply", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "note": "algorithmic bytes of one apply in complex128 over the summed stage-kernel time",
+                "kernel_ms": kms, "share": share}
+    if prec == api.F64:
+        bytes_apply *= 2  # complex128 factors and vectors
+    hbm_frac = bytes_apply / (ms_max / steps * 1e-3) / (peaks["hbm_gbs"] * 1e9)
+
+    # end to end through bf_apply_host with pinned host buffers
+    e2e = None
+    if sides and not args.no_e2e:
+        Fp = torch.from_numpy(Fh).to(cdt).pin_memory()
+        Gp = torch.empty_like(Fp).pin_memory()
+        for _ in range(2):
+            plan.apply_host(Fp, Gp, prec)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            plan.apply_host(Fp, Gp, prec)
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+        nbytes = Fp.numel() * Fp.element_size()
+        e2e = {"value": job_rate(world, N * m, steps, 1e3 * t_e2e), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # the same operator factored for the on-the-fly apply (no phase tables), timed alike
+    otf_d = None
+    if sides and prec == api.F32 and not otf and not args.no_otf_side:
+        otf_d = otf_side(args, w, plan, F, G, flush, stream, world, local, alu["peak"], front, back)
+    ind = None
+    if sides and prec == api.F32 and not otf and not args.no_indirect_side and w["N"] > 0:
+        ind = indirect_side(w, F, G, local)
+
+    Gh = G.cpu().numpy() if rank == 0 else None
+    cpu = None
+    rel_err = None
+    if rank == 0 and world == 1 and sides and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(w, Fh, Gh, cpu_budget or args.cpu_budget)
+        rel_err = (cpu.pop("rel_err_gpu"), cpu.pop("rows_compared"))
+    elif rank == 0:
+        rel_err = oracle_rows_err(w, Fh, Gh, w.get("err_rows", 32))
+
+    cfg = {"workload": w["desc"], "N": N, "m": m, "r": info["r"], "r_alpha": info["r_alpha"],
+           "eps": w["eps"], "L": info["L"], "split": w["split"], "l2": "flushed (512 MB write) between timed steps",
+           "t_factor_s": None if t_factor is None else round(t_factor, 3),
+           "t_factor_device_s": None if t_factor_dev is None else round(t_factor_dev, 3),
+           "plan": "on-the-fly (bf_factor_otf)" if otf else "phase tables",
+           "dev_bytes_f32": info["dev_bytes_f32"], "dev_bytes_f64": info["dev_bytes_f64"],
+           "mr_autotuned": mr_tuned,
+           "parallelism": "replicas" if world > 1 else "single GPU",
+           "hbm_frac_of_measured": hbm_frac, "algorithmic_bytes_per_step": bytes_apply,
+           "algorithmic_flops_per_step": (front + back) * w["split"] ** 2}
+    if rel_err is not None:
+        cfg["rel_err_vs_fp64_oracle"], cfg["rel_err_rows"] = rel_err
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {api.F64: "f64", api.F32: "f32", api.BF16X3: "bf16x3"}[prec],
+            "data": "synthetic (seeded complex Gaussian F; analytic kernel)", "config": cfg,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary()}
+    if otf_d is not None:
+        line["on_the_fly"] = otf_d
+    if ind is not None:
+        line["indirect"] = ind
+    if own_plan:
+        plan.close()
+    del F, G, flush
+    torch.cuda.empty_cache()
+    return line
+
+
+def side_lines(args, rank, world, local):
+    """The other configurations, measured in the default run beside the headline:
+    the plain FP64 per-stage form at the headline's shape, config 3 (split-BF16 and
+    FP32 on the same plan), config 4 (one batched launch against one by one) and
+    config 5 (serving).  Each is a full JSON object with its own roofline and error
+    against the FP64 oracle on sampled rows."""
+    import torch
+    from paper_1803_04128_gb300 import api
+    out = {}
+    st, wu = min(args.steps, 5), 3
+    # the plain form: FP64, one launch per stage, state through HBM, on the fio2 operator
+    w = dict(WORKLOADS["fio2"], name="fio2", prec="f64", factor_on_device=True, err_rows=32)
+    w["desc"] = ("plain FP64 per-stage form (one launch per stage, CUDA-graph replay) at the fio2 shape: "
+                 "N=65536, m=64, eps=1e-6")
+    out["fp64_plain_fio2"] = run_single(args, w, rank, world, local, st, wu, sides=False)
+    # config 3: split-BF16 tensor cores and FP32 on the same four sub-BFs
+    w3 = dict(WORKLOADS["fio3"], name="fio3", factor_on_device=True, err_rows=24)
+    plan3 = api.Plan(w3["N"], eps=w3["eps"], phase_kind=w3["phase"], amp_kind=w3["amp"], split=w3["split"],
+                     device=local, factor_on_device=True)
+    out["fio3_bf16x3"] = run_single(args, w3, rank, world, local, st, wu, plan=plan3, sides=False)
+    w3f = dict(w3, prec="f32", desc=w3["desc"].replace("split-BF16 tensor-core apply (hi/lo operands, FP32 "
+                                                       "accumulation)", "complex FP32 apply"))
+    out["fio3_f32"] = run_single(args, w3f, rank, world, local, st, wu, plan=plan3, sides=False)
+    plan3.close()
+    torch.cuda.empty_cache()
+    out["fio4"] = run_batched(args, dict(WORKLOADS["fio4"], name="fio4"), rank, world, local, steps=st, warmup=wu)
+    torch.cuda.empty_cache()
+    out["serve5"] = run_serving(args, dict(WORKLOADS["serve5"], name="serve5"), rank, world, local, side=True)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -598,8 +896,10 @@ def main():
                     help="time the on-the-fly plan (bf_factor_otf, FP32 only) as the main line")
     ap.add_argument("--no-otf-side", action="store_true",
                     help="skip the on-the-fly side measurement of FP32 workloads")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations' side objects of the default fio2 run")
     args = ap.parse_args()
-    w = dict(WORKLOADS[args.workload])
+    w = dict(WORKLOADS[args.workload], name=args.workload)
     if args.prec and args.prec != w["prec"]:
         w["prec"] = args.prec
         w["desc"] += " [apply precision overridden to %s]" % args.prec
@@ -611,8 +911,8 @@ def main():
         w["desc"] += " [m overridden to %d]" % args.m
     if args.otf and not w.get("otf"):
         w["prec"] = "f32"
+        w["otf"] = True
         w["desc"] += " [on-the-fly plan: phases evaluated in the kernels]"
-    args.otf = args.otf or bool(w.get("otf"))
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -621,197 +921,24 @@ def main():
     if args.impl == "reference":
         return run_reference(args, w, rank, world)
 
-    import numpy as np
     import torch
     import torch.distributed as dist
-
-    from paper_1803_04128_gb300 import _lib as L
-    from paper_1803_04128_gb300 import api, inputs
 
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if args.workload == "fio4":
-        return run_batched(args, w, rank, world, local)
-    if args.workload == "serve5":
-        return run_serving(args, w, rank, world, local)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    N, m = w["N"], w["m"]
-    prec = {"f64": api.F64, "f32": api.F32, "bf16x3": api.BF16X3}[w["prec"]]
-    cdt = torch.complex128 if prec == api.F64 else torch.complex64
-    t0 = time.perf_counter()
-    plan = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
-                    on_the_fly=args.otf)
-    t_factor = time.perf_counter() - t0
-    # the same operator with its phase tables built on the GPU (bf_factor_device), for the record
-    t_factor_dev = None
-    if not w.get("otf"):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
-                 factor_on_device=True).close()
-        torch.cuda.synchronize()
-        t_factor_dev = time.perf_counter() - t0
-    info = plan.info()
-    mr_tuned = None
-    if prec == api.F32:
-        # column-slice width of the fused FP32 apply chosen by timing (off the timed region)
-        tune_path = os.path.join(tempfile.gettempdir(), "bf_autotune_bench_%d.txt" % os.getpid())
-        mr_tuned = api.autotune(plan, m, tune_path)
-    plan.reserve(prec, m)
-    Fh = inputs.complex_gaussian(N, m, seed=rank)
-    F = torch.from_numpy(Fh).to(cdt).cuda()
-    G = torch.empty_like(F)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
-    stream = torch.cuda.current_stream()
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        plan.apply(F, G, prec)
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-
-    fk, bk = ("front_f32_otf", "back_f32_otf") if args.otf else ("front_f32", "back_f32")
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        with api.KernelTimer() as kt:
-            torch.cuda.nvtx.range_push("timed")    # lets an ncu capture select the timed launches
-            for i in range(args.steps):
-                flush.zero_()                      # L2 flush between timed steps (not timed)
-                ev[i][0].record(stream)
-                plan.apply(F, G, prec)
-                ev[i][1].record(stream)
-            torch.cuda.synchronize()
-            torch.cuda.nvtx.range_pop()
-    barrier()
-    torch.cuda.synchronize()
-    assert plan.sync_status() == 0
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    ms_max = max_over_ranks(ms, world, "cuda")
-    value = job_rate(world, N * m, args.steps, ms_max)
-
-    peaks, peak_src = load_peaks()
-    front, back, bytes_apply = algorithmic(info, m, N, w["split"])
-    sm_mhz_max = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12   # TFLOP/s FP32 FMA
-    roof = None
-    launches = sum(n for n, _ in kt.result.values())
-    if prec == api.F32 and any(k.startswith("mid_") for k in kt.result):
-        # level ranges split into passes (front, middle H and G passes, back): the
-        # apply's algorithmic flops over the summed time of all its passes
-        tot = sum(v[1] for v in kt.result.values())
-        per_apply_ms = tot / args.steps
-        achieved = (front + back) * w["split"] ** 2 / (per_apply_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "all passes of one apply (front, mid_h, mid_g, back)",
-                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)" % (sm_mhz_max, peak_src),
-                "kernel_ms": {k: v[1] / v[0] for k, v in kt.result.items()},
-                "share": {k: v[1] / tot for k, v in kt.result.items()}}
-    elif prec == api.F32 and fk in kt.result:
-        nf, tf = kt.result[fk]
-        nb, tb = kt.result[bk]
-        nblk = w["split"] ** 2
-        dom, n_l, t_l, flops = (fk, nf, tf, front) if tf >= tb else (bk, nb, tb, back)
-        avg_ms = t_l / n_l
-        achieved = flops / (avg_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": ncu_traffic(dom, args.workload, m),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)" % (sm_mhz_max, peak_src),
-                "kernel_ms": {k: v[1] / v[0] for k, v in kt.result.items()},
-                "share": {k: v[1] / sum(x[1] for x in kt.result.values()) for k, v in kt.result.items()}}
-        _ = nblk
-    elif prec == api.BF16X3 and "front_tc" in kt.result:
-        tflops = tensor_flops(info, m, N, w["split"])
-        tot = sum(v[1] for v in kt.result.values())
-        dom = max(("front_tc", "back_tc"), key=lambda k: kt.result[k][1])
-        n_l, t_l = kt.result[dom]
-        achieved = tflops[dom] / (t_l / n_l * 1e-3) / 1e12
-        roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
-                "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops_sustained"],
-                "traffic": ncu_traffic(dom, args.workload, m),
-                "note": "tensor FLOPs issued (3 BF16 products per split product, zero padding to the MMA shape); "
-                        "peak: sustained cuBLAS BF16 (%s)" % peak_src,
-                "useful_alu_frac": (front + back) / (tot / n_l * 1e-3) / 1e12 / alu_peak,
-                "kernel_ms": {k: v[1] / v[0] for k, v in kt.result.items()},
-                "share": {k: v[1] / tot for k, v in kt.result.items()}}
-    elif kt.result:
-        # plain FP64 form: one launch per stage, state through HBM; the stages together
-        # are the apply, held to the HBM roofline with the apply's algorithmic bytes (c128)
-        tot = sum(v[1] for v in kt.result.values())
-        dom = max(kt.result, key=lambda k: kt.result[k][1])
-        per_apply_ms = tot / args.steps
-        achieved = 2 * bytes_apply / (per_apply_ms * 1e-3) / 1e9  # complex128
-        roof = {"bound": "hbm", "kernel": "plain FP64 stages (v/h/s/g/u_f64) per apply", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "note": "algorithmic bytes of one apply in complex128 over the summed stage-kernel time",
-                "kernel_ms": {k: v[1] / v[0] for k, v in kt.result.items()},
-                "share": {k: v[1] / tot for k, v in kt.result.items()}}
-    if prec == api.F64:
-        bytes_apply *= 2  # complex128 factors and vectors
-    hbm_frac = bytes_apply / (ms_max / args.steps * 1e-3) / (peaks["hbm_gbs"] * 1e9)
-
-    # end to end through bf_apply_host with pinned host buffers
-    e2e = None
-    if not args.no_e2e:
-        Fp = torch.from_numpy(Fh).to(cdt).pin_memory()
-        Gp = torch.empty_like(Fp).pin_memory()
-        for _ in range(2):
-            plan.apply_host(Fp, Gp, prec)
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            plan.apply_host(Fp, Gp, prec)
-        t_e2e = max_over_ranks(time.perf_counter() - t0, world, "cuda")
-        nbytes = Fp.numel() * Fp.element_size()
-        e2e = {"value": job_rate(world, N * m, args.steps, 1e3 * t_e2e), "unit": UNIT,
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
-
-    # the same operator factored for the on-the-fly apply (no phase tables), timed alike
-    otf = None
-    if prec == api.F32 and not args.otf and not args.no_otf_side:
-        otf = otf_side(args, w, plan, F, G, flush, stream, world, local, alu_peak, front, back)
-    ind = None
-    if prec == api.F32 and not args.otf and not args.no_indirect_side and w["N"] > 0:
-        ind = indirect_side(w, F, G, local)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        Gh = G.cpu().numpy()
-        cpu = cpu_oracle_rate(w, Fh, Gh, args.cpu_budget)
-
+        line = run_batched(args, w, rank, world, local)
+    elif args.workload == "serve5":
+        line = run_serving(args, w, rank, world, local)
+    else:
+        line = run_single(args, w, rank, world, local, args.steps, args.warmup)
+        # the default run also measures the other configurations (one GPU, rank 0 only)
+        default_run = (args.workload == "fio2" and not (args.prec or args.eps or args.m or args.otf))
+        if default_run and world == 1 and not args.no_configs:
+            line["configs"] = side_lines(args, rank, world, local)
     if rank == 0:
-        cfg = {"workload": w["desc"], "N": N, "m": m, "r": info["r"], "r_alpha": info["r_alpha"],
-               "eps": w["eps"], "L": info["L"], "split": w["split"], "l2": "flushed (512 MB write) between timed steps",
-               "t_factor_s": round(t_factor, 3),
-               "t_factor_device_s": None if t_factor_dev is None else round(t_factor_dev, 3),
-               "plan": "on-the-fly (bf_factor_otf)" if args.otf else "phase tables",
-               "dev_bytes_f32": plan.info()["dev_bytes_f32"], "dev_bytes_f64": plan.info()["dev_bytes_f64"],
-               "mr_autotuned": mr_tuned,
-               "parallelism": "replicas" if world > 1 else "single GPU",
-               "hbm_frac_of_measured": hbm_frac, "algorithmic_bytes_per_step": bytes_apply,
-               "algorithmic_flops_per_step": (front + back) * w["split"] ** 2}
-        if cpu is not None and "rel_err_gpu" in cpu:
-            cfg["rel_err_vs_fp64_oracle"] = cpu.pop("rel_err_gpu")
-            cfg["rel_err_rows"] = cpu.pop("rows_compared")
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": {api.F64: "f64", api.F32: "f32", api.BF16X3: "bf16x3"}[prec],
-                "data": "synthetic (seeded complex Gaussian F; analytic kernel)", "config": cfg,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary()}
-        if otf is not None:
-            line["on_the_fly"] = otf
-        if ind is not None:
-            line["indirect"] = ind
         print(json.dumps(line))
-    plan.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -271,7 +271,11 @@ bf_status bf_apply(bf_plan* plan, bf_precision prec, const void* F, int64_t m, v
  * fits in 32 MiB (else BF_ERR_ARG, message gives the size); bf_profile timing
  * is off (else BF_ERR_STATE).  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) and caches it: make that
- * first call before any stream capture.  Calls share the array, so calls
+ * first call before any stream capture.  The cached address belongs to the
+ * device's primary context as it was at that first call: after
+ * cudaDeviceReset (or anything else that destroys and re-creates the primary
+ * context) it is stale, so a process that resets a device must not call this
+ * entry point on that device again.  Calls share the array, so calls
  * that overlap on the GPU race; nothing in it needs clearing between calls.
  * F, G, m, stream as for bf_apply (c64).  Allocates nothing. */
 bf_status bf_apply_f32_noalloc(bf_plan* plan, const void* F, int64_t m, void* G, void* stream);
@@ -338,6 +342,15 @@ bf_status bf_profile_begin(void);
 bf_status bf_profile_end(void);
 int bf_profile_count(void);
 bf_status bf_profile_get(int i, const char** name, int64_t* launches, double* total_ms);
+
+/* Measurement aid (the paper has no counterpart): the FP32 FMA throughput of
+ * `device` from a register-only loop of fused multiply-adds (8 independent
+ * chains per thread, every SM filled), best of 5 timed launches after one
+ * warm-up, in TFLOP/s (2 flops per FMA); *sm_count receives the device's SM
+ * count.  It is the ceiling the FP32 apply kernels, which are bound by FMA
+ * issue, are held to.  Synchronises the device; allocates 256 KB for the
+ * duration of the call.  Errors: BF_ERR_ARG (NULL output), BF_ERR_CUDA. */
+bf_status bf_fp32_peak(int device, int* sm_count, double* tflops);
 
 #ifdef __cplusplus
 }

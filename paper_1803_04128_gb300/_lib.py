@@ -108,6 +108,7 @@ _SIGS = {
     "bf_profile_get": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_double)]),
     "bf_version": (ctypes.c_char_p, []),
+    "bf_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "bf_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_P)]),
     "bf_batch_run": (ctypes.c_int, [_P, _P]),
     "bf_batch_capture_graph": (ctypes.c_int, [_P, _P]),

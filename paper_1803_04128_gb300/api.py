@@ -462,3 +462,10 @@ class KernelTimer:
 
 def version():
     return L.lib().bf_version().decode()
+
+
+def fp32_peak(device=0):
+    """(SM count, measured FP32 FMA TFLOP/s) of ``device`` (bf_fp32_peak)."""
+    sms, tf = ctypes.c_int(), ctypes.c_double()
+    L.check(L.lib().bf_fp32_peak(int(device), ctypes.byref(sms), ctypes.byref(tf)), "bf_fp32_peak")
+    return sms.value, tf.value

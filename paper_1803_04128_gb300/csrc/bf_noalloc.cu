@@ -15,7 +15,9 @@
 // exits.  Host code cannot use the array's name as a device address, so the
 // first call on each device looks the address up with cudaGetSymbolAddress
 // (with that device current) and caches it; make that first call before any
-// stream capture.  All calls share the array and it keeps the last call's
+// stream capture.  The cache is not refreshed: a cudaDeviceReset, which
+// re-creates the primary context and reloads the module, leaves the cached
+// address stale, so this entry point is not for processes that reset devices.  All calls share the array and it keeps the last call's
 // contents: the front kernel writes every element the back kernel reads, so
 // nothing needs clearing, but calls that overlap on the GPU (different
 // streams, or different plans on one device) race on it.

@@ -1,6 +1,7 @@
 // Per-kernel CUDA-event timing of the library's own launches (measurement aid).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -50,11 +51,80 @@ void prof_stop(void* tok, cudaStream_t st)
     if (i < g_recs.size()) cudaEventRecord(g_recs[i].b, st);
 }
 
+// Register-only FP32 FMA loop: 8 independent chains per thread, so every
+// scheduler always has an FMA ready.  The multipliers are close to 1 and the
+// addends small, so the values stay normal and finite; the result is stored
+// only when it is impossible (never), which keeps the loop alive.
+constexpr int kPeakIters = 2048;
+__global__ void __launch_bounds__(256) ffma_peak_kernel(float* sink, float seed)
+{
+    float a[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = seed + 1e-3f * (float)(threadIdx.x + c);
+    const float b = 0.9999999f, d = 1e-7f;
+    for (int i = 0; i < kPeakIters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[c] = fmaf(a[c], b, d);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += a[c];
+    if (s == -1.0f) sink[blockIdx.x] = s;
+}
+
 }  // namespace bfi
 
 using namespace bfi;
 
 extern "C" {
+
+bf_status bf_fp32_peak(int device, int* sm_count, double* tflops)
+{
+    if (!sm_count || !tflops) {
+        set_error("bf_fp32_peak: NULL output");
+        return BF_ERR_ARG;
+    }
+    int cur = -1, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
+        set_error("bf_fp32_peak: cannot select device %d", device);
+        return BF_ERR_CUDA;
+    }
+    bf_status st = BF_OK;
+    float* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t s = nullptr;
+    double best = 0.0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, device) != cudaSuccess ||
+        cudaMalloc(&sink, sizeof(float) * 65536) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error("bf_fp32_peak: CUDA set-up failed");
+        st = BF_ERR_CUDA;
+    } else {
+        const int blocks = sms * (per_sm / 256);
+        const double flops = (double)blocks * 256 * kPeakIters * 8 * 2;
+        for (int rep = 0; rep < 6 && st == BF_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            ffma_peak_kernel<<<blocks, 256, 0, s>>>(sink, 1.0f + 1e-3f * rep);
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                set_error("bf_fp32_peak: kernel or timing failed");
+                st = BF_ERR_CUDA;
+            } else if (rep > 0 && ms > 0.f) {   // the first launch is a warm-up
+                best = std::max(best, flops / (ms * 1e-3) / 1e12);
+            }
+        }
+    }
+    if (s) cudaStreamDestroy(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sink) cudaFree(sink);
+    cudaSetDevice(cur);
+    *sm_count = sms;
+    *tflops = best;
+    return st;
+}
 
 bf_status bf_profile_begin(void)
 {
