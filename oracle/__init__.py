@@ -10,13 +10,14 @@ none of the method's arithmetic) feed both sides, through the tests.
 Modules
   direct     -- the plain definition g = K f in FP64 (C, OpenMP), plus a long
                 double brute-force variant and single entries of K.
-  kernels    -- phase / amplitude definitions of the transforms (numpy side).
   lowrank    -- Alg. 1 (randomised sampling rank-r SVD) for the amplitude split.
   recovery   -- Algs. 3, 4, 5: a low-rank phase Psi (e^{2 pi i Psi} = e^{2 pi i Phi})
                 recovered from kernel entries alone (Scenario 1 of Table sc).
   special    -- the Hankel-function transform of Sec. 5 (Eq. HK): entries, direct sums.
   decide     -- Alg. 6 of Sec. 3: may r-dimensional NUFFTs after dimension lifting
                 evaluate the transform, or does it need the butterfly?
+  nufft      -- Eq. (tg3) of Sec. 3 by 1-D NUFFTs (Gaussian gridding) for phases
+                that are rank 1 on each column half (the split of Eq. FIOwq2).
   butterfly  -- the butterfly algorithm of Sec. 4 (Algorithm 4.1) in FP64,
                 on the fly, in the paper's step order; and the IBF apply of
                 Eq. (tg): g = sum_k a_k * BF(b_k * f).
