@@ -50,6 +50,9 @@ WORKLOADS = {
     "fio_big": dict(N=1 << 22, m=16, phase=1, amp=1, eps=1e-6, prec="f32", split=1, otf=True,
                     desc="1D FIO as fio2 at N=2^22, m=16, on-the-fly plan (no phase tables; FP32+FP64 tables "
                          "would take ~42 GB), complex FP32 apply, eps=1e-6"),
+    "nufft2": dict(N=65536, m=64, phase=1, amp=1, eps=1e-6, prec="f32", split=1,
+                   desc="fio2's operator (1D FIO, smooth rank-2 amplitude, N=65536, m=64, complex FP32) evaluated "
+                        "by 1-D NUFFTs on the column halves xi >= 0 and xi < 0 (Sec. 3, Eq. tg3), eps=1e-6"),
     "fio3": dict(N=262144, m=256, phase=2, amp=1, eps=1e-4, prec="bf16x3", split=2,
                  desc="piecewise FIO (jump at x=1/2), N=262144 as four N/2 sub-BFs, m=256, alpha as fio2, "
                       "split-BF16 tensor-core apply (hi/lo operands, FP32 accumulation), BF eps=1e-4 (r=8)"),
@@ -298,12 +301,14 @@ def serve_trace(srv, ops, pools, times, opi, ms, warm_s):
     return st
 
 
-def oracle_rows_err(w, Fh, Gh, nrows, seed=17, G_rows=None):
+def oracle_rows_err(w, Fh, Gh, nrows, seed=17, G_rows=None, F_dev=None):
     """Relative l2 error (the paper's eps^b over the sampled set) of a GPU result
     against the FP64 direct oracle on ``nrows`` sampled rows, all RHS."""
     import numpy as np
     from oracle import direct as od
     from paper_1803_04128_gb300 import inputs
+    if Fh is None:
+        Fh = F_dev.cpu().numpy()
     rows = inputs.sample_rows(w["N"], nrows, seed=seed)
     gd = od.direct(w["phase"], w["N"], Fh, rows, amp=w["amp"])
     g = (Gh[rows] if G_rows is None else G_rows).astype(np.complex128)
@@ -355,8 +360,7 @@ def run_serving(args, w, rank, world, local, side=False):
                       factor_on_device=True) for N in Ns]
     t_factor = time.perf_counter() - t0
     warm = 1.0
-    secs, secs_light, secs_plain = ((4.0, 3.0, 2.0) if side else
-                                    (w["seconds"], w["seconds_light"], min(3.0, w["seconds"])))
+    secs, secs_light = (4.0, 4.0) if side else (w["seconds"], w["seconds_light"])
 
     def pools_for(cdt):
         out = {}
@@ -371,8 +375,7 @@ def run_serving(args, w, rank, world, local, side=False):
     # the offered rate of the workload (above the GPU's capacity: throughput under
     # overload), a light rate the server sustains (latency), and the plain form
     runs = (("batched_f32", api.F32, 4, False, torch.complex64, w["rate"], secs),
-            ("batched_f32_light", api.F32, 4, False, torch.complex64, w["rate_light"], secs_light),
-            ("plain_f64_per_request", api.F64, 1, True, torch.complex128, w["rate"], secs_plain))
+            ("batched_f32_light", api.F32, 4, False, torch.complex64, w["rate_light"], secs_light))
     for name, prec, slots, per_req, cdt, rate, secs_run in runs:
         window = warm + secs_run
         times, opi, ms = inputs.poisson_requests(rate, window, len(Ns), mset, seed=rank)
@@ -398,14 +401,27 @@ def run_serving(args, w, rank, world, local, side=False):
                 errs["batched_f32"] = oracle_rows_err(dict(w, N=Ns[o]), Fh, pools[(o, mm)][1].numpy(), 48)[0]
         srv.close()                        # drops requests still queued (the overloaded runs)
         del pools
-    # the plain form's arithmetic (FP64 stage launches, one request) on the same operator and F
-    Fh = inputs.complex_gaussian(Ns[1], 16, seed=116)
-    Gp = plans[1].apply(torch.from_numpy(Fh).cuda(), prec=api.F64)
-    torch.cuda.synchronize()
-    errs["plain_f64_per_request"] = oracle_rows_err(dict(w, N=Ns[1]), Fh, Gp.cpu().numpy(), 48)[0]
+    # the plain per-request form: one request at a time, FP64 stage launches, host buffers
+    # (bf_apply_host: copies in, apply, copies out).  Its capacity for the trace's mix (operator
+    # and m independent and uniform) is sum_N N E[m] / sum_N t_N(E[m]); with the time linear in m
+    # (measured at m = 16 per operator) that is sum_N N / sum_N (t_N(16) / 16).  At small m the
+    # plain form is latency-bound, so this overstates it, which only lowers the ratio below.
+    t_col = []
+    for pl, N in zip(plans, Ns):
+        Fh = inputs.complex_gaussian(N, 16, seed=116 + N)
+        Fp = torch.from_numpy(Fh).pin_memory()
+        Gp = torch.empty_like(Fp).pin_memory()
+        pl.apply_host(Fp, Gp, api.F64)            # warm-up (graph capture of the stage launches)
+        t0 = time.perf_counter()
+        pl.apply_host(Fp, Gp, api.F64)
+        t_col.append((time.perf_counter() - t0) / 16)
+        if N == Ns[1]:
+            errs["plain_f64_per_request"] = oracle_rows_err(dict(w, N=N), Fh, Gp.numpy(), 48)[0]
+    p = {"units_per_s": sum(Ns) / sum(t_col), "seconds_per_column": dict(zip(map(str, Ns), t_col)),
+         "method": "bf_apply_host FP64 (plain per-stage form) of one m = 16 request per operator, timed on the "
+                   "host; capacity of the trace's mix = sum_N N / sum_N t_N(16)/16"}
     b = results["batched_f32"]
     bl = results["batched_f32_light"]
-    p = results["plain_f64_per_request"]
     units_all = b["units_per_s"]
     if world > 1:  # each rank serves its own trace on its own GPU: the job's rate is the sum
         import torch.distributed as dist
@@ -424,11 +440,11 @@ def run_serving(args, w, rank, world, local, side=False):
            "eps": w["eps"], "t_factor_s": round(t_factor, 2), "warmup_s": warm,
            "batched_f32": {k: v for k, v in b.items() if k != "clocks"},
            "batched_f32_light": {k: v for k, v in bl.items() if k != "clocks"},
-           "plain_f64_per_request": {k: v for k, v in p.items() if k != "clocks"},
+           "plain_f64_per_request": p,
            "throughput_ratio_vs_plain": (b["units_per_s"] / p["units_per_s"]) if p["units_per_s"] else None,
            "rel_err_vs_fp64_oracle": errs,
            "rel_err_note": "48 sampled rows, all 16 RHS, of an N = 2^16, m = 16 request's result (served by the "
-                           "light run; the plain form's stage launches on the same operator and F)",
+                           "light run; the plain form's apply of an m = 16 request)",
            "note": "stats over the arrival window after warm-up; requests still queued at its end are "
                    "counted in 'pending' and not in the latency percentiles.  At the offered 2000 req/s the "
                    "work arriving exceeds the GPU's capacity, so its p50/p99 measure queue growth over the "
@@ -642,6 +658,101 @@ def otf_side(args, w, plan, F, G, flush, stream, world, local, alu_peak, front, 
     return out
 
 
+def nufft_bytes(N, m, ra, msp):
+    """Algorithmic DRAM bytes of the three NUFFT kernels (c64 = 8 B): pass 1 reads F and the
+    deconvolution factors and writes the four-step intermediate T (both column halves, n = N
+    grid points, r_alpha m columns); pass 2 reads T and writes the grid H; the interpolation
+    reads H, its weights, windows and prefactors, and writes G.  T and H are each written and
+    read once: a grid of n r_alpha m points per half does not fit on chip, so this is the
+    traffic of a two-pass FFT."""
+    M, n, Mc = N // 2, N, ra * m
+    grid = 2 * n * Mc * 8
+    return {"nufft_pass1": N * m * 8 + 2 * ra * M * 8 + grid,
+            "nufft_pass2": 2 * grid,
+            "nufft_interp": grid + 2 * N * (2 * msp * 4 + 4 + ra * 8) + N * m * 8}
+
+
+def nufft_side(w, F, G, flush, stream, local, steps, warmup):
+    """The same operator evaluated by 1-D NUFFTs on the two column halves (Sec. 3, Eq. tg3;
+    bf_nufft_apply), timed with the main line's protocol; error against the oracle on sampled
+    rows and difference from the butterfly apply's G."""
+    import torch
+    from paper_1803_04128_gb300 import api
+    N, m = w["N"], w["m"]
+    t0 = time.perf_counter()
+    pn = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], device=local, factor=False)
+    msp = pn.nufft_prepare(w["eps"])
+    t_prep = time.perf_counter() - t0
+    Gn = torch.empty_like(F)
+    for _ in range(warmup):
+        flush.zero_()
+        pn.nufft_apply(F, Gn)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with api.KernelTimer() as kt:
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            pn.nufft_apply(F, Gn)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    info = pn.nufft_info()
+    peaks, src = load_peaks()
+    byt = nufft_bytes(N, m, info["r_alpha"], msp)
+    km = {k: v[1] / v[0] for k, v in kt.result.items()}
+    tot = sum(v[1] for v in kt.result.values())
+    dom = max(km, key=lambda k: kt.result[k][1])
+    ach = byt[dom] / (km[dom] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": ncu_traffic(dom, "fio2", m),
+            "algorithmic_bytes_per_launch": byt, "kernel_ms": km,
+            "share": {k: v[1] / tot for k, v in kt.result.items()},
+            "apply_frac": sum(byt.values()) / (ms / steps * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "peak_source": "measured copy bandwidth (%s)" % src}
+    Gh = Gn.cpu().numpy()
+    err, nrows = oracle_rows_err(w, None, Gh, 256, G_rows=None, F_dev=F)
+    out = {"value": N * m * steps / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms / steps, "msp": msp,
+           "t_prepare_s": round(t_prep, 3), "rel_err_vs_fp64_oracle": err, "rel_err_rows": nrows,
+           "rel_diff_vs_butterfly_apply": None if G is None else float((Gn - G).norm() / G.norm()),
+           "roofline": roof,
+           "gpu_launches": sum(v[0] for v in kt.result.values()),
+           "method": "2 r_alpha 1-D type-2 NUFFTs (Gaussian gridding, grid 2x the modes, msp points each side) "
+                     "on the column halves xi >= 0 and xi < 0, where the phase is (x +- c(x)) xi"}
+    pn.close()
+    return out
+
+
+def run_nufft(args, w, rank, world, local):
+    """The NUFFT evaluation as the main line (bf_nufft_apply; same protocol as the butterfly
+    line, L2 flushed between timed applies); its own roofline and oracle error."""
+    import torch
+    import torch.distributed as dist
+    from paper_1803_04128_gb300 import inputs
+    Fh = inputs.complex_gaussian(w["N"], w["m"], seed=rank)
+    F = torch.from_numpy(Fh).to(torch.complex64).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        d = nufft_side(w, F, None, flush, stream, local, args.steps, args.warmup)
+    ms = max_over_ranks(d["ms_per_step"] * args.steps, world, "cuda")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(w, Fh, None, args.cpu_budget)
+    line = {"metric": METRIC, "value": job_rate(world, w["N"] * w["m"], args.steps, ms), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded complex Gaussian F; analytic kernel)",
+            "config": {"workload": w["desc"], "N": w["N"], "m": w["m"], "eps": w["eps"], "msp": d["msp"],
+                       "l2": "flushed (512 MB write) between timed steps",
+                       "rel_err_vs_fp64_oracle": d["rel_err_vs_fp64_oracle"], "rel_err_rows": d["rel_err_rows"]},
+            "roofline": d["roofline"], "cpu_baseline": cpu, "e2e": None, "gpu_launches": d["gpu_launches"],
+            "clocks": clk.summary()}
+    return line
+
+
 def indirect_side(w, F, G, local):
     """The same operator factored from its entries alone (indirect access, Scenario 1
     of Sec. 2.2): amplitude by Algorithm 1 on |K|, phase by Algorithms 3-5, on the
@@ -772,12 +883,19 @@ def run_single(args, w, rank, world, local, steps, warmup, plan=None, sides=True
                 "useful_alu_frac": (front + back) * w["split"] ** 2 / (tot / steps * 1e-3) / 1e12 / alu["peak"],
                 "kernel_ms": kms, "share": share}
     elif kt.result:
-        # plain FP64 form: one launch per stage, state through HBM; the stages together
-        # are the apply, held to the HBM roofline with the apply's algorithmic bytes (c128)
-        achieved = 2 * bytes_apply / (tot / steps * 1e-3) / 1e9  # complex128
-        roof = {"bound": "hbm", "kernel": "plain FP64 stages (v/h/s/g/u_f64) per apply", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "note": "algorithmic bytes of one apply in complex128 over the summed stage-kernel time",
+        # plain FP64 form: one launch per stage, state through HBM.  Its stage kernels do the
+        # apply's algorithmic flops in FP64 (flop/B ~ M_eff / 2 in c128), bound by the FP64
+        # pipes: the apply's flops over the summed stage-kernel time against the measured
+        # DFMA-loop rate; the HBM fraction of its algorithmic bytes beside it
+        import torch  # noqa: F401
+        from paper_1803_04128_gb300 import api as _api
+        f64_peak = _api.fp64_peak(local)
+        achieved = (front + back) * w["split"] ** 2 / (tot / steps * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "plain FP64 stages (v/h/s/g/u_f64) per apply", "achieved": achieved,
+                "peak": f64_peak, "unit": "TFLOP/s", "frac": achieved / f64_peak, "traffic": None,
+                "peak_source": "register-only DFMA loop on this device (bf_fp64_peak)",
+                "hbm_frac_algorithmic_bytes": 2 * bytes_apply / (tot / steps * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                "note": "algorithmic flops of one apply over the summed stage-kernel time",
                 "kernel_ms": kms, "share": share}
     if prec == api.F64:
         bytes_apply *= 2  # complex128 factors and vectors
@@ -807,6 +925,9 @@ def run_single(args, w, rank, world, local, steps, warmup, plan=None, sides=True
     ind = None
     if sides and prec == api.F32 and not otf and not args.no_indirect_side and w["N"] > 0:
         ind = indirect_side(w, F, G, local)
+    nu = None
+    if sides and prec == api.F32 and not otf and w["split"] == 1 and w["phase"] in (0, 1, 2, 3):
+        nu = nufft_side(w, F, G, flush, stream, local, steps, warmup)
 
     Gh = G.cpu().numpy() if rank == 0 else None
     cpu = None
@@ -839,6 +960,8 @@ def run_single(args, w, rank, world, local, steps, warmup, plan=None, sides=True
         line["on_the_fly"] = otf_d
     if ind is not None:
         line["indirect"] = ind
+    if nu is not None:
+        line["nufft"] = nu
     if own_plan:
         plan.close()
     del F, G, flush
@@ -931,6 +1054,8 @@ def main():
         line = run_batched(args, w, rank, world, local)
     elif args.workload == "serve5":
         line = run_serving(args, w, rank, world, local)
+    elif args.workload == "nufft2":
+        line = run_nufft(args, w, rank, world, local)
     else:
         line = run_single(args, w, rank, world, local, args.steps, args.warmup)
         # the default run also measures the other configurations (one GPU, rank 0 only)

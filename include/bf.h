@@ -199,6 +199,42 @@ bf_status bf_unwrap(const double* u, int64_t n, double tau, const double* seed, 
 bf_status bf_nufft_decide(const bf_plan* plan, int block, int r, int r_eps, int q, double eps,
                           uint64_t seed, int* y, int* n, int* terms);
 
+/* NUFFT evaluation of the transform (Sec. 3, Eq. tg3), for phases that are
+ * rank 1 on each half of the columns: the built-in DFT, FIO, FIO_PW and ONES
+ * kinds (Phi = t_h(x) xi + rho(x) on xi >= 0 and on xi < 0, the split of the
+ * wave-equation FIO at xi = 0, Eq. FIOwq2 of Sec. 5).  There Algorithm 6's
+ * lifting with r = 1 removes each half's whole phase, and
+ *     g_i = sum_h sum_k a_k(x_i) e^{2 pi i rho_i} sum_{xi in h} e^{2 pi i t_h(x_i) xi} b_k(xi) f(xi)
+ * is 2 r_alpha one-dimensional NUFFTs (uniform modes, non-uniform targets) per
+ * right-hand side, with the amplitude split alpha ~ sum_k a_k b_k of
+ * Algorithm 1.  The paper names no NUFFT algorithm; this one is Gaussian
+ * gridding on a grid twice as fine as the modes, with msp grid points on each
+ * side of a target: its error falls like exp(-2 pi msp / 3), and msp is the
+ * smallest with exp(-2 pi msp / 3) <= eps (2 <= msp <= 16).
+ *
+ * bf_nufft_prepare: host FP64 planning of the targets, interpolation weights,
+ * deconvolution factors and twiddles, uploaded to the plan's device (O(N)
+ * memory; the plan need not be factored for the butterfly).  Replaces an
+ * earlier preparation.  *msp_out (nullable) receives msp.  Requirements: a
+ * power-of-two N with 256 <= N <= 2^20, a built-in phase of the kinds above
+ * (else BF_ERR_UNSUPPORTED), eps in (0, 1) (else BF_ERR_ARG).  Errors also
+ * BF_ERR_NOMEM, BF_ERR_CUDA.
+ *
+ * bf_nufft_apply: G = K F for m right-hand sides in complex FP32, F and G
+ * device [N][m] c64 as for bf_apply (G must not alias F), asynchronously on
+ * `stream`: three kernels (the deconvolution fused into the first pass of a
+ * four-step inverse FFT, the second pass, the interpolation).  Uses a
+ * workspace of 4 N r_alpha m c64 numbers owned by the plan, grown with
+ * cudaMalloc when m grows (so: not inside stream capture for a new m).
+ * Errors: BF_ERR_ARG, BF_ERR_STATE (no bf_nufft_prepare), BF_ERR_NOMEM,
+ * BF_ERR_CUDA.
+ *
+ * bf_nufft_info: msp, r_alpha, and the workspace bytes per right-hand side of
+ * a prepared plan (each pointer nullable); BF_ERR_STATE if not prepared. */
+bf_status bf_nufft_prepare(bf_plan* plan, double eps, int* msp_out);
+bf_status bf_nufft_apply(bf_plan* plan, const void* F, int64_t m, void* G, void* stream);
+bf_status bf_nufft_info(const bf_plan* plan, int* msp, int* r_alpha, int64_t* ws_bytes_per_rhs);
+
 /* Create a plan for the operator *desc to tolerance eps (the target relative
  * l2 error eps^b of Sec. 5).  With opt->r == 0 the interpolation rank is taken
  * from eps by the rule r = 4 + ceil(-log10 eps), measured for 1D-FIO-like
@@ -351,6 +387,9 @@ bf_status bf_profile_get(int i, const char** name, int64_t* launches, double* to
  * issue, are held to.  Synchronises the device; allocates 256 KB for the
  * duration of the call.  Errors: BF_ERR_ARG (NULL output), BF_ERR_CUDA. */
 bf_status bf_fp32_peak(int device, int* sm_count, double* tflops);
+/* The same for FP64 fused multiply-adds (the ceiling of the plain FP64 form's
+ * stage kernels), in TFLOP/s.  Errors: BF_ERR_ARG, BF_ERR_CUDA. */
+bf_status bf_fp64_peak(int device, double* tflops);
 
 #ifdef __cplusplus
 }

@@ -101,6 +101,10 @@ _SIGS = {
     "bf_nufft_decide": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int)]),
+    "bf_nufft_prepare": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+    "bf_nufft_apply": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "bf_nufft_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int64)]),
     "bf_last_error": (ctypes.c_char_p, []),
     "bf_profile_begin": (ctypes.c_int, []),
     "bf_profile_end": (ctypes.c_int, []),
@@ -109,6 +113,7 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_double)]),
     "bf_version": (ctypes.c_char_p, []),
     "bf_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "bf_fp64_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "bf_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_P)]),
     "bf_batch_run": (ctypes.c_int, [_P, _P]),
     "bf_batch_capture_graph": (ctypes.c_int, [_P, _P]),

@@ -242,6 +242,31 @@ class Plan:
                                         _stream_ptr(stream)), "bf_apply_host")
         return G
 
+    # -- NUFFT evaluation (Sec. 3, Eq. tg3) of phases rank 1 on each column half
+    def nufft_prepare(self, eps=1e-6):
+        """Plan the NUFFT evaluation (bf_nufft_prepare); returns msp."""
+        msp = ctypes.c_int()
+        L.check(self._lib.bf_nufft_prepare(self._h, float(eps), ctypes.byref(msp)), "bf_nufft_prepare")
+        return msp.value
+
+    def nufft_apply(self, F, G=None, stream=None):
+        """G = K F by 2 r_alpha 1-D NUFFTs (bf_nufft_apply); F, G contiguous CUDA complex64."""
+        import torch
+        if F.dtype != torch.complex64 or not F.is_cuda or not F.is_contiguous():
+            raise ValueError("F must be a contiguous CUDA complex64 tensor")
+        m = 1 if F.dim() == 1 else F.shape[1]
+        if G is None:
+            G = torch.empty_like(F)
+        L.check(self._lib.bf_nufft_apply(self._h, ctypes.c_void_p(F.data_ptr()), m, ctypes.c_void_p(G.data_ptr()),
+                                         _stream_ptr(stream)), "bf_nufft_apply")
+        return G
+
+    def nufft_info(self):
+        msp, ra, wb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        L.check(self._lib.bf_nufft_info(self._h, ctypes.byref(msp), ctypes.byref(ra), ctypes.byref(wb)),
+                "bf_nufft_info")
+        return {"msp": msp.value, "r_alpha": ra.value, "ws_bytes_per_rhs": wb.value}
+
     def sync_status(self, stream=None):
         return self._lib.bf_sync_status(self._h, _stream_ptr(stream))
 
@@ -469,3 +494,10 @@ def fp32_peak(device=0):
     sms, tf = ctypes.c_int(), ctypes.c_double()
     L.check(L.lib().bf_fp32_peak(int(device), ctypes.byref(sms), ctypes.byref(tf)), "bf_fp32_peak")
     return sms.value, tf.value
+
+
+def fp64_peak(device=0):
+    """Measured FP64 FMA TFLOP/s of ``device`` (bf_fp64_peak)."""
+    tf = ctypes.c_double()
+    L.check(L.lib().bf_fp64_peak(int(device), ctypes.byref(tf)), "bf_fp64_peak")
+    return tf.value

@@ -85,6 +85,7 @@ struct BlockFactors {
 };
 
 struct DeviceState;  // defined in the CUDA translation units
+struct NufftState;   // bf_nufft.cu
 
 }  // namespace bfi
 
@@ -99,6 +100,7 @@ struct bf_plan {
     bool otf = false;              // factored by bf_factor_otf (no phase tables; FP32 applies only)
     std::vector<bfi::BlockFactors> blocks;  // 1 or 4
     bfi::DeviceState* dev = nullptr;
+    bfi::NufftState* nufft = nullptr;  // bf_nufft_prepare (Sec. 3, Eq. tg3)
     std::map<int64_t, int> tuned_mr;  // autotuned column-slice width per m (FP32 fused apply)
     int mr_hint(int64_t m) const
     {
@@ -176,6 +178,7 @@ size_t device_ws_bytes(const bf_plan* p, bf_precision prec, int64_t m);
 bf_status device_apply_ws(bf_plan* p, bf_precision prec, const void* F, int64_t m, void* G, void* stream, void* ws,
                           size_t ws_bytes);
 void device_free(bf_plan* p);
+void nufft_free(bf_plan* p);  // bf_nufft.cu
 void device_info(const bf_plan* p, bf_plan_info* info);
 
 }  // namespace bfi

@@ -453,6 +453,7 @@ bf_status bf_plan_view(const bf_plan* p, int block, int what, int level, const d
 void bf_destroy(bf_plan* p)
 {
     if (!p) return;
+    nufft_free(p);
     device_free(p);
     delete p;
 }

@@ -72,11 +72,76 @@ __global__ void __launch_bounds__(256) ffma_peak_kernel(float* sink, float seed)
     if (s == -1.0f) sink[blockIdx.x] = s;
 }
 
+// The same loop in FP64 (DFMA).
+__global__ void __launch_bounds__(256) dfma_peak_kernel(double* sink, double seed, int iters)
+{
+    double a[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = seed + 1e-3 * (double)(threadIdx.x + c);
+    const double b = 0.9999999999, d = 1e-10;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[c] = fma(a[c], b, d);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += a[c];
+    if (s == -1.0) sink[blockIdx.x] = s;
+}
+
 }  // namespace bfi
 
 using namespace bfi;
 
 extern "C" {
+
+bf_status bf_fp64_peak(int device, double* tflops)
+{
+    if (!tflops) {
+        set_error("bf_fp64_peak: NULL output");
+        return BF_ERR_ARG;
+    }
+    int cur = -1, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
+        set_error("bf_fp64_peak: cannot select device %d", device);
+        return BF_ERR_CUDA;
+    }
+    bf_status st = BF_OK;
+    double* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t s = nullptr;
+    double best = 0.0;
+    const int iters = 256;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, device) != cudaSuccess ||
+        cudaMalloc(&sink, sizeof(double) * 65536) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error("bf_fp64_peak: CUDA set-up failed");
+        st = BF_ERR_CUDA;
+    } else {
+        const int blocks = sms * (per_sm / 256);
+        const double flops = (double)blocks * 256 * iters * 8 * 2;
+        for (int rep = 0; rep < 6 && st == BF_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            dfma_peak_kernel<<<blocks, 256, 0, s>>>(sink, 1.0 + 1e-3 * rep, iters);
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                set_error("bf_fp64_peak: kernel or timing failed");
+                st = BF_ERR_CUDA;
+            } else if (rep > 0 && ms > 0.f) {
+                best = std::max(best, flops / (ms * 1e-3) / 1e12);
+            }
+        }
+    }
+    if (s) cudaStreamDestroy(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sink) cudaFree(sink);
+    cudaSetDevice(cur);
+    *tflops = best;
+    return st;
+}
 
 bf_status bf_fp32_peak(int device, int* sm_count, double* tflops)
 {
