@@ -374,15 +374,21 @@ def run_serving(args, w, rank, world, local, side=False):
     errs = {}
     # the offered rate of the workload (above the GPU's capacity: throughput under
     # overload), a light rate the server sustains (latency), and the plain form
-    runs = (("batched_f32", api.F32, 4, False, torch.complex64, w["rate"], secs),
-            ("batched_f32_light", api.F32, 4, False, torch.complex64, w["rate_light"], secs_light))
-    for name, prec, slots, per_req, cdt, rate, secs_run in runs:
+    # method 0: the butterfly apply for every operator; method 1: Sec. 3's choice per operator
+    # (the NUFFT of Eq. tg3 where the phase is rank 1 on the column halves -- all four here)
+    # the light (latency) runs first, so that no run follows an overloaded one
+    runs = (("batched_f32_light", api.F32, 4, False, torch.complex64, w["rate_light"], secs_light, 0),
+            ("auto_method_f32_light", api.F32, 4, False, torch.complex64, w["rate_light"], secs_light, 1),
+            ("batched_f32", api.F32, 4, False, torch.complex64, w["rate"], secs, 0),
+            ("auto_method_f32", api.F32, 4, False, torch.complex64, w["rate"], secs, 1))
+    pools = pools_for(torch.complex64)     # one fixed F per (operator, m), shared by the runs
+    for name, prec, slots, per_req, cdt, rate, secs_run, method in runs:
         window = warm + secs_run
         times, opi, ms = inputs.poisson_requests(rate, window, len(Ns), mset, seed=rank)
-        srv = api.Server(n_slots=slots, max_batch_rhs=256, precision=prec, per_request=per_req, device=local)
+        srv = api.Server(n_slots=slots, max_batch_rhs=256, precision=prec, per_request=per_req, device=local,
+                         method=method)
         ops = [srv.add(p) for p in plans]
         srv.start()
-        pools = pools_for(cdt)
         with ClockSampler(local) as clk:
             st = serve_trace(srv, ops, pools, times, opi, ms, warm)
         st["clocks"] = clk.summary()
@@ -390,7 +396,7 @@ def run_serving(args, w, rank, world, local, side=False):
         st["window_s"] = window - warm
         st["served_req_per_s"] = st["completed"] / st["wall_s"] if st["wall_s"] > 0 else 0.0
         results[name] = st
-        if name == "batched_f32_light":
+        if name in ("batched_f32_light", "auto_method_f32_light"):
             # the light run's queue empties: once drained, every pool buffer that served a
             # request holds that request's result (one fixed F per (operator, m)); sampled
             # rows of the N = 2^16 operator's m = 16 result against the oracle
@@ -398,9 +404,9 @@ def run_serving(args, w, rank, world, local, side=False):
             o, mm = 1, 16
             if any(int(a) == o and int(b) == mm for a, b in zip(opi, ms)):
                 Fh = inputs.complex_gaussian(Ns[o], mm, seed=o * 100 + mm)
-                errs["batched_f32"] = oracle_rows_err(dict(w, N=Ns[o]), Fh, pools[(o, mm)][1].numpy(), 48)[0]
+                errs[name.replace("_light", "")] = oracle_rows_err(dict(w, N=Ns[o]), Fh, pools[(o, mm)][1].numpy(),
+                                                                     48)[0]
         srv.close()                        # drops requests still queued (the overloaded runs)
-        del pools
     # the plain per-request form: one request at a time, FP64 stage launches, host buffers
     # (bf_apply_host: copies in, apply, copies out).  Its capacity for the trace's mix (operator
     # and m independent and uniform) is sum_N N E[m] / sum_N t_N(E[m]); with the time linear in m
@@ -440,6 +446,11 @@ def run_serving(args, w, rank, world, local, side=False):
            "eps": w["eps"], "t_factor_s": round(t_factor, 2), "warmup_s": warm,
            "batched_f32": {k: v for k, v in b.items() if k != "clocks"},
            "batched_f32_light": {k: v for k, v in bl.items() if k != "clocks"},
+           "auto_method_f32": {k: v for k, v in results["auto_method_f32"].items() if k != "clocks"},
+           "auto_method_f32_light": {k: v for k, v in results["auto_method_f32_light"].items() if k != "clocks"},
+           "auto_method_note": "the same trace served with Sec. 3's choice per operator: every operator here has a "
+                               "phase that is rank 1 on the column halves, so all four are evaluated by the NUFFT "
+                               "of Eq. tg3 (bf_nufft_apply) instead of the butterfly",
            "plain_f64_per_request": p,
            "throughput_ratio_vs_plain": (b["units_per_s"] / p["units_per_s"]) if p["units_per_s"] else None,
            "rel_err_vs_fp64_oracle": errs,
@@ -461,6 +472,10 @@ def run_serving(args, w, rank, world, local, side=False):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded complex Gaussian F; analytic kernel; Poisson arrivals)", "config": cfg,
             "p50_ms": bl["p50_ms"], "p99_ms": bl["p99_ms"], "p99_ms_at_offered_rate": b["p99_ms"],
+            "auto_method": {"units_per_s": results["auto_method_f32"]["units_per_s"],
+                            "p50_ms": results["auto_method_f32_light"]["p50_ms"],
+                            "p99_ms": results["auto_method_f32_light"]["p99_ms"],
+                            "throughput_ratio_vs_plain": results["auto_method_f32"]["units_per_s"] / p["units_per_s"]},
             "roofline": roof, "cpu_baseline": None,
             "e2e": {"value": units_all / 1e9, "unit": UNIT, "h2d_bytes_per_step": None,
                     "d2h_bytes_per_step": None, "note": "requests are served from host buffers"},

@@ -40,6 +40,11 @@ typedef struct {
                                queue behind large applies                                       */
     int64_t small_units;    /* a batch is small if N * (its right-hand sides) <= this
                                (default 2^21)                                                   */
+    int method;             /* 0 (default): the butterfly apply for every operator; 1 (auto,
+                               BF_PREC_F32 without per_request): Sec. 3's choice per operator --
+                               the NUFFT of Eq. tg3 (bf_nufft_prepare / bf_nufft_apply) where the
+                               phase is rank 1 on the column halves, the butterfly otherwise     */
+    double nufft_eps;       /* tolerance of the NUFFT plans that method 1 prepares (default 1e-6) */
 } bf_server_options;
 
 typedef struct {
@@ -49,6 +54,11 @@ typedef struct {
     double p50_ms, p99_ms, mean_ms, max_ms;  /* submit-to-completion latency            */
     double units_per_s;        /* sum N*m of completed requests / wall time since reset */
     double wall_s;             /* seconds since start / last reset                    */
+    double device_busy_ms;     /* device time (CUDA events, copies included) covered by at
+                                  least one completed batch since reset (the first 2^20
+                                  batches after a reset are counted)                   */
+    double overlap_ms;         /* ... covered by two or more slots' batches at once     */
+    int64_t nufft_operators;   /* operators evaluated by the NUFFT (method 1)          */
 } bf_server_stats;
 
 bf_status bf_server_default_options(bf_server_options* opt);

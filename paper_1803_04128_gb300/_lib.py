@@ -54,14 +54,17 @@ class ApplyItem(ctypes.Structure):
 class ServerOptions(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int), ("hbm_budget", ctypes.c_int64), ("max_batch_rhs", ctypes.c_int64),
                 ("precision", ctypes.c_int), ("per_request", ctypes.c_int), ("device", ctypes.c_int),
-                ("n_priority_slots", ctypes.c_int), ("small_units", ctypes.c_int64)]
+                ("n_priority_slots", ctypes.c_int), ("small_units", ctypes.c_int64), ("method", ctypes.c_int),
+                ("nufft_eps", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("pending", ctypes.c_int64),
                 ("in_flight", ctypes.c_int64), ("launches", ctypes.c_int64), ("mean_batch_rhs", ctypes.c_double),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
-                ("max_ms", ctypes.c_double), ("units_per_s", ctypes.c_double), ("wall_s", ctypes.c_double)]
+                ("max_ms", ctypes.c_double), ("units_per_s", ctypes.c_double), ("wall_s", ctypes.c_double),
+                ("device_busy_ms", ctypes.c_double), ("overlap_ms", ctypes.c_double),
+                ("nufft_operators", ctypes.c_int64)]
 
 
 class PlanInfo(ctypes.Structure):

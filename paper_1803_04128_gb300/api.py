@@ -403,13 +403,16 @@ class Server:
     """Continuous-batching request loop over resident operators (bf_server_*)."""
 
     def __init__(self, n_slots=4, hbm_budget=0, max_batch_rhs=256, precision=F32, per_request=False, device=0,
-                 n_priority_slots=-1, small_units=0):
+                 n_priority_slots=-1, small_units=0, method=0, nufft_eps=1e-6):
+        """``method``: 0 = the butterfly apply for every operator; 1 = Sec. 3's choice per operator
+        (the NUFFT where the phase is rank 1 on the column halves, the butterfly otherwise)."""
         self._lib = L.lib()
         o = L.ServerOptions()
         L.check(self._lib.bf_server_default_options(ctypes.byref(o)), "bf_server_default_options")
         o.n_slots, o.hbm_budget, o.max_batch_rhs = n_slots, hbm_budget, max_batch_rhs
         o.precision, o.per_request, o.device = precision, int(per_request), device
         o.n_priority_slots, o.small_units = n_priority_slots, small_units
+        o.method, o.nufft_eps = method, nufft_eps
         self._h = ctypes.c_void_p()
         L.check(self._lib.bf_server_create(ctypes.byref(o), ctypes.byref(self._h)), "bf_server_create")
         self._plans = []

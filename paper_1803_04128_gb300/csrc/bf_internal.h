@@ -179,6 +179,9 @@ bf_status device_apply_ws(bf_plan* p, bf_precision prec, const void* F, int64_t 
                           size_t ws_bytes);
 void device_free(bf_plan* p);
 void nufft_free(bf_plan* p);  // bf_nufft.cu
+// NUFFT apply (Sec. 3, Eq. tg3) with a caller-owned workspace of >= nufft_ws_bytes(p, m)
+size_t nufft_ws_bytes(const bf_plan* p, int64_t m);
+bf_status nufft_apply_ws(bf_plan* p, const void* F, int64_t m, void* G, void* stream, void* ws, size_t ws_bytes);
 void device_info(const bf_plan* p, bf_plan_info* info);
 
 }  // namespace bfi

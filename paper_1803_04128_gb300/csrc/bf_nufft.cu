@@ -599,6 +599,77 @@ extern "C" bf_status bf_nufft_prepare(bf_plan* p, double eps, int* msp_out)
     return BF_OK;
 }
 
+namespace bfi {
+
+size_t nufft_ws_bytes(const bf_plan* p, int64_t m)
+{
+    const NufftState* s = p->nufft;
+    return s ? (size_t)4 * s->n * s->ra * m * sizeof(float2) : 0;
+}
+
+// The three launches of one NUFFT apply with a caller-owned workspace (T | H).
+bf_status nufft_apply_ws(bf_plan* p, const void* F, int64_t m, void* G, void* stream, void* ws, size_t ws_bytes)
+{
+    NufftState* s = p->nufft;
+    if (!s) {
+        set_error("NUFFT apply: call bf_nufft_prepare first");
+        return BF_ERR_STATE;
+    }
+    if (ws_bytes < nufft_ws_bytes(p, m)) {
+        set_error("NUFFT apply: workspace of %zu bytes too small (%zu needed)", ws_bytes, nufft_ws_bytes(p, m));
+        return BF_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t Mc = (int64_t)s->ra * m;
+    float2* T = (float2*)ws;
+    float2* H = T + 2 * s->n * Mc;
+    PassArgs pa{};
+    pa.F = (const float2*)F;
+    pa.bD = s->bD;
+    pa.tw = s->tw;
+    pa.N = s->N;
+    pa.M = s->M;
+    pa.n = s->n;
+    pa.m = m;
+    pa.Mc = Mc;
+    pa.n1 = s->n1;
+    pa.n2 = s->n2;
+    pa.lg1 = s->lg1;
+    pa.lg2 = s->lg2;
+    cudaError_t e = cudaSuccess;
+    {   // pass 1: n2-point DFTs over j2 for every (half, j1, column block)
+        PassArgs a1 = pa;
+        a1.out = T;
+        a1.cbk = cbk_for(s->n2, Mc);
+        a1.nblk = (int)((Mc + a1.cbk - 1) / a1.cbk);
+        ProfScope ps("nufft_pass1", st);
+        e = launch_pass<1>(s->n2, a1, (int64_t)2 * s->n1 * a1.nblk, (size_t)s->n2 * (a1.cbk + 2) * sizeof(float2), st);
+    }
+    if (e == cudaSuccess) {   // pass 2: n1-point DFTs over j1 for every (half, p2, column block)
+        PassArgs a2 = pa;
+        a2.in = T;
+        a2.out = H;
+        a2.cbk = cbk_for(s->n1, Mc);
+        a2.nblk = (int)((Mc + a2.cbk - 1) / a2.cbk);
+        ProfScope ps("nufft_pass2", st);
+        e = launch_pass<2>(s->n1, a2, (int64_t)2 * s->n2 * a2.nblk, (size_t)s->n1 * (a2.cbk + 2) * sizeof(float2), st);
+    }
+    if (e == cudaSuccess) {
+        InterpArgs ia{H, s->pa, s->W, s->p0, (float2*)G, s->N, s->n, m, Mc, s->ra, s->msp};
+        const int64_t ctas = (s->N / kTile) * ((m + 31) / 32);
+        ProfScope ps("nufft_interp", st);
+        nufft_interp<<<(unsigned)ctas, kNuThreads, 0, st>>>(ia);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        set_error("NUFFT apply: launch failed: %s", cudaGetErrorString(e));
+        return BF_ERR_CUDA;
+    }
+    return BF_OK;
+}
+
+}  // namespace bfi
+
 extern "C" bf_status bf_nufft_apply(bf_plan* p, const void* F, int64_t m, void* G, void* stream)
 {
     if (!p || !F || !G || m < 1) {
@@ -617,69 +688,20 @@ extern "C" bf_status bf_nufft_apply(bf_plan* p, const void* F, int64_t m, void* 
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != s->device) cudaSetDevice(s->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    const int64_t Mc = (int64_t)s->ra * m;
-    const size_t one = (size_t)2 * s->n * Mc * sizeof(float2);
+    const size_t need = nufft_ws_bytes(p, m);
     bf_status rs = BF_OK;
-    if (s->ws_bytes < 2 * one) {
+    if (s->ws_bytes < need) {
         cudaFree(s->ws);
         s->ws = nullptr;
         s->ws_bytes = 0;
-        if (cudaMalloc(&s->ws, 2 * one) != cudaSuccess) {
-            set_error("bf_nufft_apply: workspace of %zu bytes", 2 * one);
+        if (cudaMalloc(&s->ws, need) != cudaSuccess) {
+            set_error("bf_nufft_apply: workspace of %zu bytes", need);
             rs = BF_ERR_NOMEM;
         } else {
-            s->ws_bytes = 2 * one;
+            s->ws_bytes = need;
         }
     }
-    if (rs == BF_OK) {
-        float2* T = (float2*)s->ws;
-        float2* H = T + 2 * s->n * Mc;
-        PassArgs pa{};
-        pa.F = (const float2*)F;
-        pa.bD = s->bD;
-        pa.tw = s->tw;
-        pa.N = s->N;
-        pa.M = s->M;
-        pa.n = s->n;
-        pa.m = m;
-        pa.Mc = Mc;
-        pa.n1 = s->n1;
-        pa.n2 = s->n2;
-        pa.lg1 = s->lg1;
-        pa.lg2 = s->lg2;
-        cudaError_t e = cudaSuccess;
-        {   // pass 1: n2-point DFTs over j2 for every (half, j1, column block)
-            PassArgs a1 = pa;
-            a1.out = T;
-            a1.cbk = cbk_for(s->n2, Mc);
-            a1.nblk = (int)((Mc + a1.cbk - 1) / a1.cbk);
-            ProfScope ps("nufft_pass1", st);
-            e = launch_pass<1>(s->n2, a1, (int64_t)2 * s->n1 * a1.nblk,
-                               (size_t)s->n2 * (a1.cbk + 2) * sizeof(float2), st);
-        }
-        if (e == cudaSuccess) {   // pass 2: n1-point DFTs over j1 for every (half, p2, column block)
-            PassArgs a2 = pa;
-            a2.in = T;
-            a2.out = H;
-            a2.cbk = cbk_for(s->n1, Mc);
-            a2.nblk = (int)((Mc + a2.cbk - 1) / a2.cbk);
-            ProfScope ps("nufft_pass2", st);
-            e = launch_pass<2>(s->n1, a2, (int64_t)2 * s->n2 * a2.nblk,
-                               (size_t)s->n1 * (a2.cbk + 2) * sizeof(float2), st);
-        }
-        if (e == cudaSuccess) {
-            InterpArgs ia{H, s->pa, s->W, s->p0, (float2*)G, s->N, s->n, m, Mc, s->ra, s->msp};
-            const int64_t ctas = (s->N / kTile) * ((m + 31) / 32);
-            ProfScope ps("nufft_interp", st);
-            nufft_interp<<<(unsigned)ctas, kNuThreads, 0, st>>>(ia);
-            e = cudaGetLastError();
-        }
-        if (e != cudaSuccess) {
-            set_error("bf_nufft_apply: launch failed: %s", cudaGetErrorString(e));
-            rs = BF_ERR_CUDA;
-        }
-    }
+    if (rs == BF_OK) rs = nufft_apply_ws(p, F, m, G, stream, s->ws, s->ws_bytes);
     if (cur >= 0 && cur != s->device) cudaSetDevice(cur);
     return rs;
 }

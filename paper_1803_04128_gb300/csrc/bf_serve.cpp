@@ -20,6 +20,8 @@ using namespace bfi;
 namespace {
 
 using Clock = std::chrono::steady_clock;
+// device intervals kept for the busy / overlap statistics (per reset; later batches are not counted)
+constexpr size_t kMaxSpans = (size_t)1 << 20;
 
 double ms_since(Clock::time_point a, Clock::time_point b)
 {
@@ -40,6 +42,7 @@ struct Op {
     bf_plan* plan = nullptr;
     int64_t N = 0;
     int64_t cap = 0;  // right-hand sides per batch
+    bool nufft = false;  // evaluated by the NUFFT of Eq. tg3 (method = auto and the phase allows it)
     std::deque<uint64_t> pending;
 };
 
@@ -47,6 +50,7 @@ struct Slot {
     cudaStream_t st = nullptr;
     bool hi = false;  // highest-priority stream, small batches only
     cudaEvent_t ev = nullptr;
+    cudaEvent_t ev0 = nullptr;  // recorded before the batch's first copy (device-time accounting)
     void* F = nullptr;
     void* G = nullptr;
     void* ws = nullptr;
@@ -76,6 +80,9 @@ struct bf_server {
     int64_t submitted = 0, completed = 0, launches = 0, batch_cols = 0;
     double units_done = 0;
     Clock::time_point t0 = Clock::now();
+    // device intervals [start, end) of completed batches, ms after the base event
+    cudaEvent_t base = nullptr;
+    std::vector<std::pair<double, double>> spans;
 };
 
 namespace {
@@ -87,6 +94,12 @@ void reap(bf_server* s)
         cudaError_t e = cudaEventQuery(sl.ev);
         if (e == cudaErrorNotReady) continue;
         const auto now = Clock::now();
+        if (e == cudaSuccess) {
+            float a = 0.f, b = 0.f;
+            if (s->spans.size() < kMaxSpans && cudaEventElapsedTime(&a, s->base, sl.ev0) == cudaSuccess &&
+                cudaEventElapsedTime(&b, s->base, sl.ev) == cudaSuccess)
+                s->spans.emplace_back((double)a, (double)b);
+        }
         for (uint64_t id : sl.reqs) {
             auto it = s->reqs.find(id);
             if (it == s->reqs.end()) continue;
@@ -111,7 +124,8 @@ bf_status enqueue_batch(bf_server* s, Slot& sl, Op& op, std::vector<Req*>& rs)
 {
     const int64_t N = op.N, M = sl.cols;
     const size_t elt = s->elt;
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaEventRecord(sl.ev0, sl.st);
+    if (e != cudaSuccess) return BF_ERR_CUDA;
     int64_t c = 0;
     for (Req* r : rs) {
         e = cudaMemcpy2DAsync((unsigned char*)sl.F + c * elt, (size_t)M * elt, r->F, (size_t)r->m * elt,
@@ -119,7 +133,9 @@ bf_status enqueue_batch(bf_server* s, Slot& sl, Op& op, std::vector<Req*>& rs)
         if (e != cudaSuccess) return BF_ERR_CUDA;
         c += r->m;
     }
-    bf_status st = device_apply_ws(op.plan, (bf_precision)s->opt.precision, sl.F, M, sl.G, sl.st, sl.ws, sl.ws_bytes);
+    bf_status st = op.nufft ? nufft_apply_ws(op.plan, sl.F, M, sl.G, sl.st, sl.ws, sl.ws_bytes)
+                            : device_apply_ws(op.plan, (bf_precision)s->opt.precision, sl.F, M, sl.G, sl.st, sl.ws,
+                                              sl.ws_bytes);
     if (st != BF_OK) return st;
     c = 0;
     for (Req* r : rs) {
@@ -203,10 +219,14 @@ void scheduler(bf_server* s)
     }
 }
 
+size_t op_ws_bytes(const bf_server* s, const Op& op, int64_t m)
+{
+    return op.nufft ? nufft_ws_bytes(op.plan, m) : device_ws_bytes(op.plan, (bf_precision)s->opt.precision, m);
+}
+
 int64_t per_col_bytes(const bf_server* s, const Op& op, int64_t m)
 {
-    return (int64_t)(2 * (size_t)op.N * (size_t)m * s->elt +
-                     device_ws_bytes(op.plan, (bf_precision)s->opt.precision, m));
+    return (int64_t)(2 * (size_t)op.N * (size_t)m * s->elt + op_ws_bytes(s, op, m));
 }
 
 }  // namespace
@@ -228,6 +248,8 @@ bf_status bf_server_default_options(bf_server_options* o)
     o->device = 0;
     o->n_priority_slots = -1;  // n_slots / 2
     o->small_units = 0;        // 2^21
+    o->method = 0;             // the butterfly apply for every operator
+    o->nufft_eps = 1e-6;
     return BF_OK;
 }
 
@@ -317,6 +339,12 @@ bf_status bf_server_add_operator(bf_server* s, bf_plan* plan, int* op_id)
     Op op;
     op.plan = plan;
     op.N = plan->N;
+    if (s->opt.method == 1 && s->opt.precision == BF_PREC_F32 && !s->opt.per_request) {
+        // Sec. 3's choice: the NUFFT of Eq. tg3 where the phase is rank 1 on the column halves
+        // (bf_nufft_prepare accepts it), the butterfly otherwise
+        if (plan->nufft || bf_nufft_prepare(plan, s->opt.nufft_eps > 0 ? s->opt.nufft_eps : 1e-6, nullptr) == BF_OK)
+            op.nufft = true;
+    }
     s->ops.push_back(op);
     if (op_id) *op_id = (int)s->ops.size() - 1;
     return BF_OK;
@@ -350,7 +378,7 @@ bf_status bf_server_start(bf_server* s)
         }
         op.cap = m;
         slab = std::max(slab, (size_t)op.N * (size_t)m * s->elt);
-        ws = std::max(ws, device_ws_bytes(op.plan, (bf_precision)s->opt.precision, m));
+        ws = std::max(ws, op_ws_bytes(s, op, m));
     }
     s->slots.resize((size_t)s->opt.n_slots);
     int pri_lo = 0, pri_hi = 0;
@@ -361,13 +389,18 @@ bf_status bf_server_start(bf_server* s)
         sl.hi = (int)i < nhi;
         cudaError_t e;
         if ((e = cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.hi ? pri_hi : pri_lo)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreate(&sl.ev)) != cudaSuccess || (e = cudaEventCreate(&sl.ev0)) != cudaSuccess ||
             (e = cudaMalloc(&sl.F, slab)) != cudaSuccess || (e = cudaMalloc(&sl.G, slab)) != cudaSuccess ||
             (e = cudaMalloc(&sl.ws, ws)) != cudaSuccess) {
             set_error("bf_server_start: slot allocation: %s", cudaGetErrorString(e));
             return e == cudaErrorMemoryAllocation ? BF_ERR_NOMEM : BF_ERR_CUDA;
         }
         sl.ws_bytes = ws;
+    }
+    if (cudaEventCreate(&s->base) != cudaSuccess || cudaEventRecord(s->base, s->slots[0].st) != cudaSuccess ||
+        cudaEventSynchronize(s->base) != cudaSuccess) {
+        set_error("bf_server_start: base event");
+        return BF_ERR_CUDA;
     }
     s->t0 = Clock::now();
     s->started = true;
@@ -490,6 +523,24 @@ bf_status bf_server_get_stats(bf_server* s, bf_server_stats* out)
     }
     out->wall_s = ms_since(s->t0, Clock::now()) / 1e3;
     out->units_per_s = out->wall_s > 0 ? s->units_done / out->wall_s : 0.0;
+    // device time of the completed batches: covered by at least one slot, and by two or more
+    std::vector<std::pair<double, int>> ev;
+    for (auto& sp : s->spans) {
+        ev.emplace_back(sp.first, +1);
+        ev.emplace_back(sp.second, -1);
+    }
+    std::sort(ev.begin(), ev.end());
+    int depth = 0;
+    double prev = 0;
+    for (auto& e : ev) {
+        if (depth >= 1) out->device_busy_ms += e.first - prev;
+        if (depth >= 2) out->overlap_ms += e.first - prev;
+        depth += e.second;
+        prev = e.first;
+    }
+    int64_t nn = 0;
+    for (auto& op : s->ops) nn += op.nufft ? 1 : 0;
+    out->nufft_operators = nn;
     return BF_OK;
 }
 
@@ -506,6 +557,7 @@ bf_status bf_server_reset_stats(bf_server* s)
     s->launches = 0;
     s->batch_cols = 0;
     s->units_done = 0;
+    s->spans.clear();
     s->t0 = Clock::now();
     return BF_OK;
 }
@@ -528,8 +580,10 @@ void bf_server_destroy(bf_server* s)
         cudaFree(sl.G);
         cudaFree(sl.ws);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.ev0) cudaEventDestroy(sl.ev0);
         if (sl.st) cudaStreamDestroy(sl.st);
     }
+    if (s->base) cudaEventDestroy(s->base);
     delete s;
 }
 

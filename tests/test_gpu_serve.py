@@ -44,6 +44,7 @@ def test_results_same_alone_and_in_the_mix():
     st = srv.stats()
     assert st["completed"] == 48 and st["pending"] == 0
     assert st["mean_batch_rhs"] >= 1.0 and st["launches"] <= 48
+    assert st["device_busy_ms"] > 0
     assert st["p99_ms"] >= st["p50_ms"] > 0 and min(lat) > 0
     for o, F, G, _ in reqs:
         alone = plans[o].apply(torch.from_numpy(F).cuda(), prec=api.F32).cpu().numpy()
@@ -90,3 +91,73 @@ def test_admission_by_hbm_budget():
         srv2.submit(op, F, np.empty_like(F))
     srv.close()
     srv2.close()
+
+
+def _burst(srv, ops, Ns, n, ms, seed, pinned=True):
+    """n requests (operator, m drawn from ms) with page-locked buffers, all built first and
+    then submitted back to back, so that they queue while the slots are busy."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(n):
+        o = int(rng.integers(0, len(Ns)))
+        m = int(rng.choice(ms))
+        F = torch.from_numpy(inputs.complex_gaussian(Ns[o], m, seed=seed + k).astype(np.complex64))
+        G = torch.full_like(F, float("nan"))
+        if pinned:
+            F, G = F.pin_memory(), G.pin_memory()
+        reqs.append([o, F, G, None])
+    for r in reqs:
+        r[3] = srv.submit(ops[r[0]], r[1], r[2])
+    for r in reqs:
+        srv.wait(r[3], 120000.0)
+    return reqs
+
+
+def test_batches_form_and_slots_overlap_on_the_device():
+    # continuous batching: requests that arrive while slots are busy are packed into fewer
+    # applies, and the slots' batches (copies and kernels, CUDA-event intervals) overlap in time
+    Ns = [16384, 65536]
+    plans = [api.Plan(N, eps=1e-6, amp_kind=L.AMP_SMOOTH) for N in Ns]
+    srv = api.Server(n_slots=4, max_batch_rhs=64)
+    ops = [srv.add(p) for p in plans]
+    srv.start()
+    reqs = _burst(srv, ops, Ns, 40, (1, 4, 16), seed=300)
+    st = srv.stats()
+    assert st["completed"] == 40
+    assert st["launches"] < 40, st             # requests were batched
+    assert st["overlap_ms"] > 0.0, st          # two slots' device work overlapped
+    assert st["overlap_ms"] <= st["device_busy_ms"]
+    for o, F, G, _ in reqs:
+        alone = plans[o].apply(F.cuda(), prec=api.F32).cpu()
+        assert torch.equal(G, alone)
+    srv.close()
+
+
+def test_auto_method_serves_nufft_where_the_phase_allows():
+    # Sec. 3's choice per operator: the FIO operator (rank 1 on the column halves) by the NUFFT,
+    # the separable phase with a xi^2 term by the butterfly; each result equals its method's
+    # apply of that request alone, and meets the direct sum
+    plans = [api.Plan(16384, eps=1e-6, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH),
+             api.Plan(4096, eps=1e-6, phase_kind=L.PHASE_SEP, amp_kind=L.AMP_SMOOTH)]
+    Ns = [16384, 4096]
+    srv = api.Server(n_slots=3, max_batch_rhs=64, method=1)
+    ops = [srv.add(p) for p in plans]
+    srv.start()
+    assert srv.stats()["nufft_operators"] == 1
+    reqs = _burst(srv, ops, Ns, 24, (1, 4, 16), seed=500)
+    assert srv.stats()["completed"] == 24
+    for o, F, G, _ in reqs:
+        if o == 0:
+            alone = plans[0].nufft_apply(F.cuda()).cpu()
+        else:
+            alone = plans[1].apply(F.cuda(), prec=api.F32).cpu()
+        assert torch.equal(G, alone)
+    o, F, G, _ = next(r for r in reqs if r[0] == 0)
+    rows = inputs.sample_rows(16384, 24, seed=4)
+    gd = od.direct(od.FIO, 16384, F.numpy().astype(np.complex128), rows, amp=1)
+    assert relerr(G.numpy()[rows], gd) < 1e-5
+    o, F, G, _ = next(r for r in reqs if r[0] == 1)
+    rows = inputs.sample_rows(4096, 24, seed=5)
+    gd = od.direct(od.SEP, 4096, F.numpy().astype(np.complex128), rows, amp=1)
+    assert relerr(G.numpy()[rows], gd) < 1e-5
+    srv.close()
