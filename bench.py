@@ -605,6 +605,7 @@ def run_batched(args, w, rank, world, local, steps=None, warmup=None):
     cfg = {"workload": w["desc"], "n_ops": len(shapes), "shapes": shapes, "units_per_step": units,
            "r": plans[shapes[0][0]].info()["r"], "eps": w["eps"], "l2": "flushed (512 MB write) between timed steps",
            "t_factor_s": round(t_factor, 2), "t_autotune_s": round(t_tune, 2),
+           "tile_shapes": [dict(api.tile_shapes(plans[N], m), N=N, m=m) for N, m in shapes],
            "sequential_single_op_ms_per_step": seq_ms, "batched_ms_per_step": ms_max / steps,
            "speedup_batched_vs_sequential": seq_ms / (ms_max / steps),
            "hbm_frac_of_measured": bytes_apply / (ms_max / steps * 1e-3) / (peaks["hbm_gbs"] * 1e9),
@@ -960,6 +961,7 @@ def run_single(args, w, rank, world, local, steps, warmup, plan=None, sides=True
            "plan": "on-the-fly (bf_factor_otf)" if otf else "phase tables",
            "dev_bytes_f32": info["dev_bytes_f32"], "dev_bytes_f64": info["dev_bytes_f64"],
            "mr_autotuned": mr_tuned,
+           "tile_shapes": api.tile_shapes(plan, m) if prec == api.F32 else None,
            "parallelism": "replicas" if world > 1 else "single GPU",
            "hbm_frac_of_measured": hbm_frac, "algorithmic_bytes_per_step": bytes_apply,
            "algorithmic_flops_per_step": (front + back) * w["split"] ** 2}

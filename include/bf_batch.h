@@ -66,13 +66,26 @@ bf_status bf_batch_debug_hold(bf_batch* batch, int on);
 
 void bf_batch_destroy(bf_batch* batch); /* NULL-safe */
 
-/* Choose the column-slice width (right-hand sides per CTA, a power of two) of
- * the FP32 fused apply for this plan and m by timing the candidates on the
- * GPU, and remember it in the plan (bf_apply and bf_batch_create use it).
+/* Choose the level-tile shapes of the FP32 fused apply (the tiling of Algorithm
+ * 4.1's levels, Sec. 4) for this plan and m by timing candidates on the GPU:
+ * the column-slice width mr (right-hand sides per tile, a power of two), the
+ * most levels a pass closes over one tile when long H or G level ranges are
+ * split into passes through HBM, the front tiles per CTA, and the T_Omega
+ * chunks a back CTA processes together.  The fields are searched one after the
+ * other (each against the built-in rule too), 4 timed applies per candidate.
+ * Every candidate computes the same result bitwise.  The choice is kept in the
+ * plan (bf_apply, bf_apply_host, bf_batch_create and the sharded apply use it).
  * cache_path (nullable): a text cache; an entry for this (N, r, r_alpha,
  * split, m) is used without timing, and new results are appended.
- * *mr_out (nullable) receives the choice.  Allocates temporaries. */
+ * *mr_out (nullable) receives the chosen mr.  Allocates temporaries. */
 bf_status bf_autotune(bf_plan* plan, int64_t m, const char* cache_path, int* mr_out);
+
+/* The level-tile shapes bf_apply uses for this plan and m (the autotuner's
+ * choice, else the built-in rules): mr, the most levels per pass, front tiles
+ * per CTA and back chunks per CTA (each pointer nullable).  Errors: BF_ERR_ARG,
+ * BF_ERR_STATE (plan not uploaded). */
+bf_status bf_autotune_get(const bf_plan* plan, int64_t m, int* mr, int* levels_per_pass, int* tpc_front,
+                          int* tpc_back);
 
 /* One right-hand-side block of bf_apply_batched: G = K F, device [N][m] c64,
  * caller-owned, G not aliasing F. */

@@ -133,6 +133,8 @@ _SIGS = {
     "bf_apply_shard_front": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int64, _P, _P]),
     "bf_apply_shard_back": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int64, _P, _P]),
     "bf_autotune": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
+    "bf_autotune_get": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "bf_server_default_options": (ctypes.c_int, [ctypes.POINTER(ServerOptions)]),
     "bf_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOptions), ctypes.POINTER(_P)]),
     "bf_server_add_operator": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int)]),

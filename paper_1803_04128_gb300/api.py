@@ -271,8 +271,17 @@ class Plan:
         return self._lib.bf_sync_status(self._h, _stream_ptr(stream))
 
 
+def tile_shapes(plan, m):
+    """The FP32 apply's level-tile shapes for (plan, m) (bf_autotune_get): dict of mr,
+    levels_per_pass, tpc_front, tpc_back."""
+    v = [ctypes.c_int() for _ in range(4)]
+    L.check(L.lib().bf_autotune_get(plan._h, int(m), *[ctypes.byref(x) for x in v]), "bf_autotune_get")
+    return dict(zip(("mr", "levels_per_pass", "tpc_front", "tpc_back"), (x.value for x in v)))
+
+
 def autotune(plan, m, cache_path=None):
-    """Time the column-slice candidates of the FP32 apply for (plan, m); returns mr."""
+    """Time the level-tile shape candidates of the FP32 apply for (plan, m); returns mr
+    (the other chosen shapes: tile_shapes)."""
     mr = ctypes.c_int()
     L.check(L.lib().bf_autotune(plan._h, int(m), None if cache_path is None else str(cache_path).encode(),
                                 ctypes.byref(mr)), "bf_autotune")

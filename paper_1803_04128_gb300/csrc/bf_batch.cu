@@ -413,10 +413,12 @@ bf_status bf_autotune(bf_plan* p, int64_t m, const char* cache_path, int* mr_out
             while (fgets(line, sizeof(line), f)) {
                 const size_t kl = strlen(key);
                 if (strncmp(line, key, kl) == 0 && line[kl] == ' ') {
-                    int mr = atoi(line + kl + 4);  // " mr=<v>"
-                    if (mr > 0) {
-                        p->tuned_mr[m] = mr;
-                        if (mr_out) *mr_out = mr;
+                    int word = atoi(line + kl + 4);  // " mr=<v>"
+                    const char* c = strstr(line + kl, " cfg=");
+                    if (c) word = atoi(c + 5);       // the full tuning word, where recorded
+                    if (tune_mr(word) > 0) {
+                        p->tuned_mr[m] = word;
+                        if (mr_out) *mr_out = tune_mr(word);
                         fclose(f);
                         return BF_OK;
                     }
@@ -427,15 +429,30 @@ bf_status bf_autotune(bf_plan* p, int64_t m, const char* cache_path, int* mr_out
     }
     cudaError_t e = cudaSetDevice(ds->device);
     if (e != cudaSuccess) return cuda_fail("bf_autotune: cudaSetDevice", e);
-    const int mr0 = fused_f32_config(g0, m, 0).mr;
-    std::vector<int> cand;
+    // candidate tuning words, searched one field at a time: the column-slice width mr, then
+    // the most levels per pass of split level ranges, then the front tiles per CTA, then the
+    // back chunks per CTA; each field keeps the best of its candidates (and 0, the built-in
+    // rule) before the next is searched.  Every candidate computes the same result bitwise.
+    auto cfg_of = [&](int w) { return fused_f32_config(g0, m, w); };
+    auto same = [&](int a, int b) {
+        const FusedCfg x = cfg_of(a), y = cfg_of(b);
+        return x.mr == y.mr && x.tpc_f == y.tpc_f && x.tpc_b == y.tpc_b && x.kpass == y.kpass;
+    };
+    const int mr0 = cfg_of(0).mr;
+    std::vector<int> mrs;
     for (int mr = 1; mr <= 128; mr *= 2)
-        if (mr >= mr0 / 4 && mr <= mr0 * 4 && (int64_t)mr <= 2 * m && fused_f32_config(g0, m, mr).mr == mr)
-            cand.push_back(mr);
-    if (cand.empty()) cand.push_back(mr0);
+        if (mr >= mr0 / 4 && mr <= mr0 * 4 && (int64_t)mr <= 2 * m && cfg_of(mr).mr == mr) mrs.push_back(mr);
+    if (mrs.empty()) mrs.push_back(mr0);
+    std::vector<int> kps = {0};
+    if (std::max(g0.kH, g0.kG) > 2)
+        for (int kp = 2; kp <= 6; ++kp) kps.push_back(kp);
+    const int tlogs[] = {0, 1, 2, 3, 4, 5};  // 0: the rule; v: 2^(v - 1) tiles per CTA
+    // workspace for every candidate: the largest over mr and pass splits (tiles per CTA do
+    // not change it)
     size_t wsmax = 0;
-    for (int mr : cand)
-        for (auto& B : ds->blocks) wsmax = std::max(wsmax, fused_f32_ws_bytes(B.g, m, mr));
+    for (int mr : mrs)
+        for (int kp : kps)
+            for (auto& B : ds->blocks) wsmax = std::max(wsmax, fused_f32_ws_bytes(B.g, m, tune_word(mr, kp, 0, 0)));
     void *F = nullptr, *G = nullptr, *ws = nullptr;
     const size_t nb = (size_t)p->N * m * sizeof(float2);
     cudaStream_t s = nullptr;
@@ -455,44 +472,85 @@ bf_status bf_autotune(bf_plan* p, int64_t m, const char* cache_path, int* mr_out
         cleanup();
         return cuda_fail("bf_autotune: set-up", e);
     }
-    int best = cand[0];
-    float best_ms = 1e30f;
-    for (int mr : cand) {
+    // time one candidate: 4 applies after one warm-up
+    auto trial = [&](int w, float* out_ms) -> cudaError_t {
         float tot = 0;
         for (int rep = 0; rep < 5; ++rep) {
             cudaEventRecord(e0, s);
             for (size_t i = 0; i < ds->blocks.size(); ++i) {
                 const DevBlock& B = ds->blocks[i];
                 const int beta = (p->opt.split == 2 && (i % 2) == 1) ? 1 : 0;
-                e = launch_fused_f32(B, (const float2*)F + B.col0 * m, m, (float2*)G + B.row0 * m, beta,
-                                     (float2*)ws, s, mr);
-                if (e != cudaSuccess) break;
+                const cudaError_t le = launch_fused_f32(B, (const float2*)F + B.col0 * m, m,
+                                                        (float2*)G + B.row0 * m, beta, (float2*)ws, s, w);
+                if (le != cudaSuccess) return le;
             }
             cudaEventRecord(e1, s);
-            if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
-                cleanup();
-                return cuda_fail("bf_autotune: trial", e);
-            }
+            const cudaError_t se = cudaEventSynchronize(e1);
+            if (se != cudaSuccess) return se;
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rep >= 1) tot += ms;  // first run warms up
+            if (rep >= 1) tot += ms;  // the first run warms up
         }
-        if (tot < best_ms) {
-            best_ms = tot;
-            best = mr;
+        *out_ms = tot;
+        return cudaSuccess;
+    };
+    int best = tune_word(mrs[0], 0, 0, 0);
+    float best_ms = 1e30f;
+    std::vector<int> tried;
+    auto consider = [&](int w) -> cudaError_t {
+        for (int t : tried)
+            if (same(t, w)) return cudaSuccess;  // the same effective configuration
+        tried.push_back(w);
+        float ms = 0;
+        const cudaError_t te = trial(w, &ms);
+        if (te != cudaSuccess) return te;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = w;
         }
-    }
+        return cudaSuccess;
+    };
+    for (int mr : mrs)
+        if ((e = consider(tune_word(mr, 0, 0, 0))) != cudaSuccess) break;
+    const int mrb = tune_mr(best);
+    for (size_t i = 0; i < kps.size() && e == cudaSuccess; ++i) e = consider(tune_word(mrb, kps[i], 0, 0));
+    const int kpb = tune_kpass(best);
+    for (int v : tlogs)
+        if (e == cudaSuccess) e = consider(tune_word(mrb, kpb, v, 0));
+    const int tfb = (best >> 12) & 0xF;
+    for (int v : tlogs)
+        if (e == cudaSuccess) e = consider(tune_word(mrb, kpb, tfb, v));
     cleanup();
+    if (e != cudaSuccess) return cuda_fail("bf_autotune: trial", e);
     p->tuned_mr[m] = best;
-    if (mr_out) *mr_out = best;
+    if (mr_out) *mr_out = tune_mr(best);
     if (cache_path) {
         FILE* f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s mr=%d ms=%.4f\n", key, best, best_ms / 4);
+            fprintf(f, "%s mr=%d cfg=%d ms=%.4f\n", key, tune_mr(best), best, best_ms / 4);
             fclose(f);
         }
     }
     return BF_OK;
 }
+
+bf_status bf_autotune_get(const bf_plan* p, int64_t m, int* mr, int* levels_per_pass, int* tpc_front, int* tpc_back)
+{
+    if (!p || m < 1) {
+        set_error("bf_autotune_get: NULL plan or m < 1");
+        return BF_ERR_ARG;
+    }
+    if (!p->dev || p->dev->blocks.empty()) {
+        set_error("bf_autotune_get: plan not uploaded");
+        return BF_ERR_STATE;
+    }
+    const FusedCfg c = fused_f32_config(p->dev->blocks[0].g, m, p->mr_hint(m));
+    if (mr) *mr = c.mr;
+    if (levels_per_pass) *levels_per_pass = c.kpass;
+    if (tpc_front) *tpc_front = c.tpc_f;
+    if (tpc_back) *tpc_back = c.tpc_b;
+    return BF_OK;
+}
+
 
 }  // extern "C"

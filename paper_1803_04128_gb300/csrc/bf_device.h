@@ -115,8 +115,23 @@ struct FusedCfg {
     int nslice;   // ceil(m / mr)
     int tpc_f;    // front tiles per CTA
     int tpc_b;    // T_Omega chunks a back CTA processes together
+    int kpass;    // most levels per pass (the largest pass of the H and G ranges)
 };
-// mr_hint: column-slice width chosen by the autotuner (0 = built-in rule)
+inline int tune_word(int mr, int kpass, int tpc_f_log1, int tpc_b_log1)
+{
+    return (mr & 0xFF) | ((kpass & 0xF) << 8) | ((tpc_f_log1 & 0xF) << 12) | ((tpc_b_log1 & 0xF) << 16);
+}
+inline int tune_mr(int w) { return w & 0xFF; }
+inline int tune_kpass(int w) { return (w >> 8) & 0xF; }
+inline int tune_tpc_f(int w) { return ((w >> 12) & 0xF) ? 1 << (((w >> 12) & 0xF) - 1) : 0; }
+inline int tune_tpc_b(int w) { return ((w >> 16) & 0xF) ? 1 << (((w >> 16) & 0xF) - 1) : 0; }
+// mr_hint: the autotuner's tuning word (0 = built-in rules everywhere):
+//   bits 0..7   mr, right-hand sides per column slice (a power of two)
+//   bits 8..11  most levels per pass of the plain apply's split level ranges
+//   bits 12..15 front tiles per CTA, as log2 + 1
+//   bits 16..19 T_Omega chunks a back CTA processes together, as log2 + 1
+// A field outside what fits (shared memory, tile counts) falls back to the built-in rule.
+// Every choice gives the same tiles' arithmetic per column: results are bitwise equal.
 // split: the plain apply's level passes (long H or G ranges in several passes); false: one pass per
 // side, as the batched and sharded applies run them
 FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint = 0, bool split = true);

@@ -149,10 +149,11 @@ namespace {
 // workspaces.  The batched and sharded applies keep one pass per side.
 constexpr int kSplitAbove = 5, kSplitAboveOtf = 4, kPassMax = 4;
 
-std::vector<int> split_levels(int k, bool split, bool otf)
+std::vector<int> split_levels(int k, bool split, bool otf, int kpass = 0)
 {
-    if (!split || k <= (otf ? kSplitAboveOtf : kSplitAbove)) return {k};
-    const int n = (k + kPassMax - 1) / kPassMax, base = k / n, extra = k % n;
+    if (!split || (kpass > 0 ? k <= kpass : k <= (otf ? kSplitAboveOtf : kSplitAbove))) return {k};
+    const int pm = kpass > 0 ? kpass : kPassMax;
+    const int n = (k + pm - 1) / pm, base = k / n, extra = k % n;
     std::vector<int> v;
     for (int i = 0; i < n; ++i) v.push_back(base + (i < extra ? 1 : 0));
     return v;
@@ -171,9 +172,10 @@ struct Passes {
     }
 };
 
-Passes passes_of(const Geo& g, bool split)
+Passes passes_of(const Geo& g, bool split, int hint = 0)
 {
-    return Passes{split_levels(g.kH, split, g.otf), split_levels(g.kG, split, g.otf)};
+    const int kp = tune_kpass(hint);
+    return Passes{split_levels(g.kH, split, g.otf, kp), split_levels(g.kG, split, g.otf, kp)};
 }
 
 // largest shared memory of any pass for (mr, CTp) with one tile per CTA
@@ -198,8 +200,9 @@ int tiles_per_cta(int k, int CTp, int64_t tiles, SmemFn smem)
     return tpc;
 }
 
-FusedCfg config_of(const Geo& g, int64_t m, int mr_hint, const Passes& ps)
+FusedCfg config_of(const Geo& g, int64_t m, int hint, const Passes& ps)
 {
+    const int mr_hint = tune_mr(hint);
     const int Tmax = 1 << ps.kmax();
     const int ra = g.ra > 0 ? g.ra : 1;
     const int NV = g.nv;
@@ -229,6 +232,14 @@ FusedCfg config_of(const Geo& g, int64_t m, int mr_hint, const Passes& ps)
     c.tpc_f = tiles_per_cta(kf, CTp, (int64_t)1 << (g.L - kf),
                             [&](int t) { return front_smem(g, kf, lastf, g.r, NV, CTp, mr, t); });
     c.tpc_b = tiles_per_cta(kb, CTp, (int64_t)1 << g.l1, [&](int t) { return back_smem(g, kb, g.r, NV, CTp, mr, t); });
+    // the autotuner's tiles per CTA, where they fit (at most 16, within the tile counts and
+    // the two-CTAs-per-SM shared-memory limit)
+    const int tf = tune_tpc_f(hint), tb = tune_tpc_b(hint);
+    if (tf > 0 && tf <= 16 && (int64_t)tf <= ((int64_t)1 << (g.L - kf)) &&
+        front_smem(g, kf, lastf, g.r, NV, CTp, mr, tf) <= 113 * 1024)
+        c.tpc_f = tf;
+    if (tb > 0 && tb <= 16 && tb <= (1 << g.l1) && back_smem(g, kb, g.r, NV, CTp, mr, tb) <= 113 * 1024) c.tpc_b = tb;
+    c.kpass = ps.kmax();
     return c;
 }
 
@@ -315,12 +326,12 @@ bool make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int bet
 
 FusedCfg fused_f32_config(const Geo& g, int64_t m, int mr_hint, bool split)
 {
-    return config_of(g, m, mr_hint, passes_of(g, split));
+    return config_of(g, m, mr_hint, passes_of(g, split, mr_hint));
 }
 
 size_t fused_f32_ws_bytes(const Geo& g, int64_t m, int mr_hint, bool split)
 {
-    const Passes ps = passes_of(g, split);
+    const Passes ps = passes_of(g, split, mr_hint);
     const FusedCfg c = config_of(g, m, mr_hint, ps);
     const int CTp = 1 << ilog2((g.ra > 0 ? g.ra : 1) * c.mr);
     const size_t w = (size_t)c.nslice * g.P * g.r * CTp * sizeof(float2);
@@ -330,7 +341,7 @@ size_t fused_f32_ws_bytes(const Geo& g, int64_t m, int mr_hint, bool split)
 bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int mr_hint,
                      FrontArgs* fa, BackArgs* ba, size_t* sf, size_t* sb, int64_t* nfront, int64_t* nback)
 {
-    return make_args(B, F, m, G, beta, ws, mr_hint, passes_of(B.g, false), fa, ba, sf, sb, nfront, nback);
+    return make_args(B, F, m, G, beta, ws, mr_hint, passes_of(B.g, false, mr_hint), fa, ba, sf, sb, nfront, nback);
 }
 
 template <int R>
@@ -386,7 +397,7 @@ cudaError_t launch_fused_f32(const DevBlock& B, const float2* F, int64_t m, floa
         return cudaSuccess;
     }
     const Geo& g = B.g;
-    const Passes ps = passes_of(g, true);
+    const Passes ps = passes_of(g, true, mr_hint);
     FrontArgs fa;
     BackArgs ba;
     size_t sf, sb;
@@ -490,7 +501,7 @@ static bool chunk_args(const DevBlock& B, const float2* F, int64_t m, float2* G,
 {
     const Geo& g = B.g;
     if (g.ra == 0 || nch < 1 || (nch & (nch - 1))) return false;
-    const Passes ps = passes_of(g, true);
+    const Passes ps = passes_of(g, true, mr_hint);
     if (ps.split()) return false;
     if (!make_args(B, F, m, G, 0, ws, mr_hint, ps, fa, ba, sf, sb, nf, nb, true)) return false;
     const int64_t nc0 = (g.N / g.n0) >> (fa->K + g.l1);  // T_Omega chunks c0 (tiles per x-node)

@@ -85,6 +85,29 @@ def test_autotune_choice_does_not_change_results(tmp_path):
     assert torch.equal(before, after)
     plan2 = api.Plan(N, r=10, amp_kind=L.AMP_SMOOTH)
     assert api.autotune(plan2, m, cache) == mr           # served from the cache
+    assert api.tile_shapes(plan2, m) == api.tile_shapes(plan, m)
+
+
+@pytest.mark.parametrize("N,m", [(65536, 1), (65536, 64), (1 << 20, 3)])
+def test_level_tile_autotuner_keeps_results_bitwise(N, m, tmp_path):
+    # the autotuner searches mr, the levels per pass (N = 2^20 splits its level ranges) and
+    # the tiles per CTA; whatever it picks, every column sees the same arithmetic
+    plan = api.Plan(N, eps=1e-6, amp_kind=L.AMP_SMOOTH, factor_on_device=True)
+    F = torch.from_numpy(inputs.complex_gaussian(N, m, seed=N + m)).to(torch.complex64).cuda()
+    before = plan.apply(F, prec=api.F32).clone()
+    rule = api.tile_shapes(plan, m)
+    api.autotune(plan, m, tmp_path / "tune.txt")
+    tuned = api.tile_shapes(plan, m)
+    assert tuned["mr"] >= 1 and tuned["tpc_front"] >= 1 and tuned["tpc_back"] >= 1
+    assert tuned["levels_per_pass"] >= 1 and rule["levels_per_pass"] >= 1
+    after = plan.apply(F, prec=api.F32)
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    assert torch.equal(before, after), (rule, tuned)
+    rows = inputs.sample_rows(N, 16, seed=3)
+    gd = od.direct(od.FIO, N, F.cpu().numpy().astype(np.complex128), rows, amp=1)
+    assert relerr(after.cpu().numpy()[rows], gd) < 1e-5
+    plan.close()
 
 
 def test_wait_timeout_is_reported_not_hung():
