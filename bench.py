@@ -188,13 +188,14 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {"f32": ("bf_f32_tile.h", "bf_kernels_f32.cu"), "otf": ("bf_f32_tile.h", "bf_kernels_otf.cu"),
-                  "tc": ("bf_kernels_tc.cu", "bf_tc.h"), "f64": ("bf_kernels_f64.cu",)}
+                  "tc": ("bf_kernels_tc.cu", "bf_tc.h"), "f64": ("bf_kernels_f64.cu",), "nufft": ("bf_nufft.cu",)}
 
 
 def kernel_hash(kernel):
     """Hash of the source file(s) of a kernel family ('front_f32' -> f32, 'back_tc' -> tc,
     'front_f32_otf' -> otf, ...)."""
-    fam = next((f for f in ("tc", "f64", "otf") if kernel.endswith("_" + f)), "f32")
+    fam = "nufft" if kernel.startswith("nufft") else next((f for f in ("tc", "f64", "otf") if kernel.endswith("_" + f)),
+                                                          "f32")
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[fam]:
         with open(os.path.join(ROOT, "paper_1803_04128_gb300", "csrc", f), "rb") as fh:
