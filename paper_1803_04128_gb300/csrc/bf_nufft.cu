@@ -94,7 +94,12 @@ struct DftStage {
             for (int j = 0; j < LEN / 2; ++j) {
                 const float2 u = v[s0 + j];
                 float2 t = v[s0 + j + LEN / 2];
-                if (j != 0) t = nu_cmul(c_w32[j * (32 / LEN)], t);
+                constexpr int kq = 8;  // e^{2 pi i k / 32} is i^(k / 8) for k a multiple of 8: exact
+                const int tw = j * (32 / LEN);
+                if (tw == kq) t = make_float2(-t.y, t.x);
+                else if (tw == 2 * kq) t = make_float2(-t.x, -t.y);
+                else if (tw == 3 * kq) t = make_float2(t.y, -t.x);
+                else if (tw != 0) t = nu_cmul(c_w32[tw], t);
                 v[s0 + j] = make_float2(u.x + t.x, u.y + t.y);
                 v[s0 + j + LEN / 2] = make_float2(u.x - t.x, u.y - t.y);
             }
