@@ -53,9 +53,10 @@ WORKLOADS = {
     "nufft2": dict(N=65536, m=64, phase=1, amp=1, eps=1e-6, prec="f32", split=1,
                    desc="fio2's operator (1D FIO, smooth rank-2 amplitude, N=65536, m=64, complex FP32) evaluated "
                         "by 1-D NUFFTs on the column halves xi >= 0 and xi < 0 (Sec. 3, Eq. tg3), eps=1e-6"),
-    "fio3": dict(N=262144, m=256, phase=2, amp=1, eps=1e-4, prec="bf16x3", split=2,
+    "fio3": dict(N=262144, m=256, phase=2, amp=1, eps=1e-6, prec="bf16x3", split=2, l1=5,
                  desc="piecewise FIO (jump at x=1/2), N=262144 as four N/2 sub-BFs, m=256, alpha as fio2, "
-                      "split-BF16 tensor-core apply (hi/lo operands, FP32 accumulation), BF eps=1e-4 (r=8)"),
+                      "split-BF16 tensor-core apply (hi/lo operands, FP32 accumulation), BF eps=1e-6 (r=10) with V "
+                      "and U at level 5 (32-index leaf groups: tiles of 2^3 and 2^4 pairs fit tensor memory)"),
 }
 
 FP32_LANES_PER_SM = 128
@@ -820,14 +821,14 @@ def run_single(args, w, rank, world, local, steps, warmup, plan=None, sides=True
     if own_plan:
         t0 = time.perf_counter()
         plan = api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
-                        on_the_fly=otf, factor_on_device=bool(w.get("factor_on_device")))
+                        on_the_fly=otf, factor_on_device=bool(w.get("factor_on_device")), l1=w.get("l1", 0))
         t_factor = time.perf_counter() - t0
         # the same operator with its phase tables built on the GPU (bf_factor_device), for the record
         if sides and not otf and not w.get("factor_on_device"):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             api.Plan(N, eps=w["eps"], phase_kind=w["phase"], amp_kind=w["amp"], split=w["split"], device=local,
-                     factor_on_device=True).close()
+                     factor_on_device=True, l1=w.get("l1", 0)).close()
             torch.cuda.synchronize()
             t_factor_dev = time.perf_counter() - t0
     info = plan.info()
@@ -1002,15 +1003,14 @@ def side_lines(args, rank, world, local):
     w["desc"] = ("plain FP64 per-stage form (one launch per stage, CUDA-graph replay) at the fio2 shape: "
                  "N=65536, m=64, eps=1e-6")
     out["fp64_plain_fio2"] = run_single(args, w, rank, world, local, st, wu, sides=False)
-    # config 3: split-BF16 tensor cores and FP32 on the same four sub-BFs
+    # config 3: split-BF16 tensor cores (V and U at level 5) and FP32 (the built-in level) on
+    # the same operator at the same eps
     w3 = dict(WORKLOADS["fio3"], name="fio3", factor_on_device=True, err_rows=24)
-    plan3 = api.Plan(w3["N"], eps=w3["eps"], phase_kind=w3["phase"], amp_kind=w3["amp"], split=w3["split"],
-                     device=local, factor_on_device=True)
-    out["fio3_bf16x3"] = run_single(args, w3, rank, world, local, st, wu, plan=plan3, sides=False)
-    w3f = dict(w3, prec="f32", desc=w3["desc"].replace("split-BF16 tensor-core apply (hi/lo operands, FP32 "
-                                                       "accumulation)", "complex FP32 apply"))
-    out["fio3_f32"] = run_single(args, w3f, rank, world, local, st, wu, plan=plan3, sides=False)
-    plan3.close()
+    out["fio3_bf16x3"] = run_single(args, w3, rank, world, local, st, wu, sides=False)
+    w3f = dict(w3, prec="f32", l1=0,
+               desc="piecewise FIO (jump at x=1/2), N=262144 as four N/2 sub-BFs, m=256, alpha as fio2, complex "
+                    "FP32 apply, BF eps=1e-6 (r=10), V and U at the built-in level 4")
+    out["fio3_f32"] = run_single(args, w3f, rank, world, local, st, wu, sides=False)
     torch.cuda.empty_cache()
     out["fio4"] = run_batched(args, dict(WORKLOADS["fio4"], name="fio4"), rank, world, local, steps=st, warmup=wu)
     torch.cuda.empty_cache()
@@ -1044,6 +1044,9 @@ def main():
     if args.prec and args.prec != w["prec"]:
         w["prec"] = args.prec
         w["desc"] += " [apply precision overridden to %s]" % args.prec
+        if args.prec != "bf16x3" and w.get("l1"):
+            w["l1"] = 0                     # the FP32 / FP64 kernels take the built-in V level
+            w["desc"] += " [V and U at the built-in level]"
     if args.eps:
         w["eps"] = args.eps
         w["desc"] += " [BF eps overridden to %g]" % args.eps

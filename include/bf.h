@@ -138,6 +138,12 @@ typedef struct {
     double phase_tol;     /* relative singular-value cut of the recovered phase (default 1e-13) */
     double tau;           /* discontinuity threshold of Algorithm 3 on second differences of  *
                            * Phi in turns (default 0.25: pi/2 of the phase 2 pi Phi)           */
+    int l1;               /* level of the V and U stages (Eq. 1 and Eq. bf3 evaluated on leaf    *
+                           * groups of n0 2^l1 indices); 0 (default): the first level whose       *
+                           * nodes hold more than r indices, where skipping the levels below is   *
+                           * exact.  A larger l1 starts the recursion higher: fewer H and G levels *
+                           * (smaller tiles, e.g. for the split-BF16 kernels' tensor memory), more *
+                           * V and U work; it must not exceed floor(L/2)                          */
 } bf_options;
 
 typedef struct {

@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
                 ("amp_rank", ctypes.c_int), ("amp_oversample", ctypes.c_int), ("amp_tol", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("keep_host", ctypes.c_int), ("device", ctypes.c_int),
                 ("indirect", ctypes.c_int), ("phase_rank", ctypes.c_int), ("phase_oversample", ctypes.c_int),
-                ("phase_tol", ctypes.c_double), ("tau", ctypes.c_double)]
+                ("phase_tol", ctypes.c_double), ("tau", ctypes.c_double), ("l1", ctypes.c_int)]
 
 
 class BatchItem(ctypes.Structure):

@@ -54,7 +54,7 @@ class Plan:
     def __init__(self, N, eps=1e-6, phase_kind=L.PHASE_FIO, phase_param=1.0, amp_kind=L.AMP_ONE,
                  r=0, n0=1, split=1, seed=0, keep_host=True, device=0, factor=True, phi=None, alpha=None,
                  factor_on_device=False, on_the_fly=False, indirect=False, entry=None, entries=None,
-                 matvec=None, amp_rank=0, amp_oversample=0, phase_rank=0, phase_oversample=0, _handle=None):
+                 matvec=None, amp_rank=0, amp_oversample=0, phase_rank=0, phase_oversample=0, l1=0, _handle=None):
         """``indirect``: factor from the kernel's entries alone (amplitude and phase
         recovered, Algorithms 1 and 3-5).  A kernel without a built-in kind is given by
         ``entry(x, xi) -> complex`` or, in bulk, ``entries(i, j) -> complex array`` over
@@ -63,7 +63,8 @@ class Plan:
         Y = K X or K^T X for a complex array X of shape (N, m); it implies indirect too.
         ``amp_rank``, ``amp_oversample`` (``phase_rank``, ``phase_oversample``): Algorithm 1's
         rank parameter and oversampling for the amplitude (the recovered phase); 0: the
-        library's defaults."""
+        library's defaults.  ``l1``: level of the V and U stages (0: the first level whose
+        nodes hold more than r indices; see bf_options.l1)."""
         self._lib = L.lib()
         self._h = ctypes.c_void_p()
         self._keep = []
@@ -124,6 +125,7 @@ class Plan:
                 o.phase_rank = phase_rank
             if phase_oversample:
                 o.phase_oversample = phase_oversample
+            o.l1 = l1
             L.check(self._lib.bf_plan_create(ctypes.byref(d), eps, ctypes.byref(o), ctypes.byref(self._h)),
                     "bf_plan_create")
             if on_the_fly:

@@ -432,7 +432,7 @@ bf_status factor_block(const KernelFn& k, const bf_options& opt, BlockFactors& B
     B.L = 0;
     while (((int64_t)n0 << B.L) < N) ++B.L;
     B.h = B.L / 2;
-    B.l1 = choose_l1(r, n0);
+    B.l1 = std::max(choose_l1(r, n0), opt.l1);
     B.nv = n0 << B.l1;
     const int L = B.L, h = B.h, l1 = B.l1;
     if (h < l1) {

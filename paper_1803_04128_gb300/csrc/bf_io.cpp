@@ -162,9 +162,12 @@ bf_status bf_plan_load(const char* path, const bf_options* opt, bf_plan** out)
             B.L = 0;
             while (((int64_t)B.n0 << B.L) < B.N) ++B.L;
             B.h = B.L / 2;
-            B.l1 = choose_l1(B.r, B.n0);
-            B.nv = B.n0 << B.l1;
             rd.vec(B.a); rd.vec(B.b); rd.vec(B.Mv); rd.vec(B.EV);
+            // the leaf group of V (n0 2^l1 indices) from Mv's size [r][nv]: the level of V and U
+            B.nv = B.r > 0 ? (int)(B.Mv.size() / (size_t)B.r) : 0;
+            B.l1 = 0;
+            while (B.l1 < 31 && (B.n0 << B.l1) < B.nv) ++B.l1;
+            if (B.nv != (B.n0 << B.l1) || B.l1 < choose_l1(B.r, B.n0) || B.l1 > B.h) rd.ok = false;
             uint32_t nh = rd.val<uint32_t>();
             if (!rd.ok || nh > 64) throw std::bad_alloc();
             B.MH.resize(nh); B.EH.resize(nh);

@@ -754,11 +754,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) back_tc(TcArgs A)
     if (!ok) atomicExch(A.err, 3);
 }
 
-template <int R>
-cudaError_t launch_tc_r(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int* err,
-                        cudaStream_t st)
+template <int R, int NV>
+cudaError_t launch_tc_rn(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int* err,
+                         cudaStream_t st)
 {
-    constexpr int NV = (R < 8) ? 8 : (R < 16 ? 16 : 32);
     const Geo& g = B.g;
     TcArgs a;
     a.g = g;
@@ -801,6 +800,17 @@ cudaError_t launch_tc_r(const DevBlock& B, const float2* F, int64_t m, float2* G
     return cudaGetLastError();
 }
 
+// leaf groups of V and U: 16 indices (the first level with more than r indices, r <= 12) or
+// 32 (V and U one level higher, plans built with a larger l1)
+template <int R>
+cudaError_t launch_tc_r(const DevBlock& B, const float2* F, int64_t m, float2* G, int beta, float2* ws, int* err,
+                        cudaStream_t st)
+{
+    if (B.g.nv == 16) return launch_tc_rn<R, 16>(B, F, m, G, beta, ws, err, st);
+    if (B.g.nv == 32) return launch_tc_rn<R, 32>(B, F, m, G, beta, ws, err, st);
+    return cudaErrorNotSupported;
+}
+
 }  // namespace
 
 bool tc_supported(const Geo& g, const char** why)
@@ -810,9 +820,8 @@ bool tc_supported(const Geo& g, const char** why)
         if (why) *why = "split-BF16 kernels are built for r = 8, 10, 12";
         return false;
     }
-    const int NV = r < 16 ? 16 : 32;
-    if (g.nv != NV) {
-        if (why) *why = "split-BF16 kernels need n0 <= r";
+    if (g.nv != 16 && g.nv != 32) {
+        if (why) *why = "split-BF16 kernels need V and U leaf groups of 16 or 32 indices";
         return false;
     }
     if (g.ra != 1 && g.ra != 2 && g.ra != 4) {
@@ -827,7 +836,7 @@ bool tc_supported(const Geo& g, const char** why)
     const int T = 1 << (g.kH > g.kG ? g.kH : g.kG);
     if (T * slot > 512) {
         if (why) *why = "tile does not fit tensor memory (2^kH or 2^kG pairs x TMEM columns per pair > 512); use a "
-                        "larger tolerance (r = 8) or split the operator";
+                        "larger tolerance (r = 8) or V and U one level higher (bf_options.l1)";
         return false;
     }
     return true;

@@ -123,6 +123,12 @@ bf_status bf_plan_create(const bf_kernel_desc* desc, double eps, const bf_option
     }
     const int64_t Nb = N / o.split;
     int l1 = choose_l1(r, o.n0);
+    if (o.l1 < 0 || (o.l1 > 0 && o.l1 < l1)) {
+        set_error("bf_plan_create: l1=%d below the first level whose nodes hold more than r=%d indices (%d)", o.l1, r,
+                  l1);
+        return BF_ERR_ARG;
+    }
+    if (o.l1 > l1) l1 = o.l1;
     int L = 0;
     while (((int64_t)o.n0 << L) < Nb) ++L;
     if (((int64_t)o.n0 << L) != Nb || L / 2 < l1) {

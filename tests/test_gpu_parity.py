@@ -234,6 +234,33 @@ def test_bf16x3_config3_shape_r8_split():
     assert relerr(g[rows], gd) < 1e-3
 
 
+@pytest.mark.parametrize("N,m,kind,okind,split", [(262144, 4, L.PHASE_FIO_PW, od.FIOPW, 2),
+                                                  (65536, 130, L.PHASE_FIO, od.FIO, 1)])
+def test_bf16x3_at_eps_1e6_with_v_and_u_one_level_higher(N, m, kind, okind, split):
+    # config 3 at the contract's eps = 1e-6 (r = 10): with V and U at level 5 (32-index leaf
+    # groups) the N/2 sub-BFs have kH = 3 and kG = 4, tiles that fit tensor memory.  Against
+    # the same plan's FP64 apply (precision only, 3e-4) and the direct sum (1e-3); the FP64
+    # apply of this plan meets the direct sum to eps; the FP32 kernels have no 32-index
+    # leaf groups at r = 10 and refuse
+    plan = api.Plan(N, eps=1e-6, phase_kind=kind, amp_kind=L.AMP_SMOOTH, split=split, l1=5)
+    assert plan.info()["r"] == 10 and plan.info()["l1"] == 5
+    F = inputs.complex_gaussian(N, m, seed=N + m)
+    g = run(plan, F, api.BF16X3)
+    g64 = run(plan, F, api.F64)
+    assert relerr(g, g64) < 3e-4
+    if split == 2:
+        rows = np.concatenate([inputs.sample_rows(N // 2, 24, seed=1), N // 2 + inputs.sample_rows(N // 2, 24, seed=2)])
+    else:
+        rows = inputs.sample_rows(N, 48, seed=3)
+    gd = od.direct(okind, N, F, rows, amp=1)
+    assert relerr(g[rows], gd) < 1e-3
+    assert relerr(g64[rows], gd) < 1e-6
+    Ft = torch.from_numpy(F).to(torch.complex64).cuda()
+    with pytest.raises(L.BFError) as e:
+        plan.apply(Ft, prec=api.F32)
+    assert e.value.status == L.BF_ERR_UNSUPPORTED
+
+
 def test_bf16x3_refuses_tiles_that_do_not_fit():
     plan = api.Plan(262144, r=10, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH, split=2)
     F = torch.zeros((262144, 1), dtype=torch.complex64, device="cuda")

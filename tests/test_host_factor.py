@@ -211,3 +211,33 @@ def test_smallest_block_per_r(r, N_min):
     with pytest.raises(L.BFError) as exc:
         api.Plan(N_min // 2, r=r)
     assert exc.value.status == L.BF_ERR_ARG
+
+
+@pytest.mark.parametrize("N,split,kind,okind,l1", [(4096, 1, L.PHASE_FIO, od.FIO, 5), (16384, 1, L.PHASE_FIO, od.FIO, 6),
+                                                  (8192, 2, L.PHASE_FIO_PW, od.FIOPW, 5)])
+def test_v_and_u_at_a_higher_level(N, split, kind, okind, l1, tmp_path):
+    # bf_options.l1: Eq. 1 (V) and Eq. bf3 (U) evaluated directly on leaf groups of 2^l1 indices
+    # and the recursion started there.  The same operator to the same tolerance (the direct sum
+    # bounds it), with fewer H and G levels; a saved plan keeps its level.
+    p = api.Plan(N, eps=1e-6, phase_kind=kind, amp_kind=L.AMP_SMOOTH, split=split, l1=l1)
+    base = api.Plan(N, eps=1e-6, phase_kind=kind, amp_kind=L.AMP_SMOOTH, split=split)
+    info, ib = p.info(), base.info()
+    assert info["l1"] == l1 and ib["l1"] < l1 and info["L"] == ib["L"]
+    F = inputs.complex_gaussian(N, 3, seed=N + l1)
+    rows = inputs.sample_rows(N, 96, seed=4)
+    gd = od.direct(okind, N, F, rows, amp=1)
+    g = factored_ref.apply(p, F)
+    assert relerr(g[rows], gd) < 1e-6
+    assert relerr(g[rows], gd) < 2 * relerr(factored_ref.apply(base, F)[rows], gd) + 1e-9
+    path = tmp_path / "p.bfplan"
+    p.save(path)
+    q = api.Plan.load(path)
+    assert q.info()["l1"] == l1 and np.array_equal(factored_ref.apply(q, F), g)
+
+
+def test_v_level_below_the_rule_is_refused():
+    with pytest.raises(L.BFError) as e:
+        api.Plan(4096, eps=1e-6, l1=3)           # level 3 nodes hold 8 <= r = 10 indices
+    assert e.value.status == L.BF_ERR_ARG
+    with pytest.raises(L.BFError):
+        api.Plan(4096, eps=1e-6, l1=7)           # above floor(L / 2) = 6
