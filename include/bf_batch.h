@@ -64,6 +64,22 @@ bf_status bf_batch_set_spin_limit(bf_batch* batch, long long polls);
  * not written.  Nothing faults or hangs: each wait is bounded. */
 bf_status bf_batch_debug_hold(bf_batch* batch, int on);
 
+/* How the batch runs (the results are bitwise the same either way):
+ *   0 (default): one persistent launch over all work items of all operators, a back tile
+ *      waiting (bounded) for its operator's fronts -- the form described above;
+ *   1: two launches, one over every operator's front tiles and one over every back tile,
+ *      one CTA per work item, operators by decreasing work, each launch with its own
+ *      shared-memory size and the tile bodies inlined (no waits: bf_batch_debug_hold has
+ *      no effect).
+ * Changing the mode drops a captured graph (capture again).  Errors: BF_ERR_ARG. */
+bf_status bf_batch_set_mode(bf_batch* batch, int mode);
+bf_status bf_batch_get_mode(const bf_batch* batch, int* mode);
+/* Time both modes on `stream` (one warm-up and three timed runs each; the operators' G
+ * are written) and keep the faster.  *mode_out (nullable) receives it, ms_out (nullable,
+ * 2 doubles) the mean milliseconds of modes 0 and 1.  Synchronises the stream; call it
+ * before bf_batch_capture_graph. */
+bf_status bf_batch_tune(bf_batch* batch, void* stream, int* mode_out, double* ms_out);
+
 void bf_batch_destroy(bf_batch* batch); /* NULL-safe */
 
 /* Choose the level-tile shapes of the FP32 fused apply (the tiling of Algorithm

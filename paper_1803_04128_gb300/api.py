@@ -395,6 +395,22 @@ class Batch:
     def set_spin_limit(self, polls):
         L.check(self._lib.bf_batch_set_spin_limit(self._h, int(polls)), "bf_batch_set_spin_limit")
 
+    def set_mode(self, mode):
+        """0: one persistent launch (default); 1: a front and a back launch over all operators."""
+        L.check(self._lib.bf_batch_set_mode(self._h, int(mode)), "bf_batch_set_mode")
+
+    def mode(self):
+        v = ctypes.c_int()
+        L.check(self._lib.bf_batch_get_mode(self._h, ctypes.byref(v)), "bf_batch_get_mode")
+        return v.value
+
+    def tune(self, stream=None):
+        """Time both modes and keep the faster; returns (mode, [ms of mode 0, ms of mode 1])."""
+        mo = ctypes.c_int()
+        ms = (ctypes.c_double * 2)()
+        L.check(self._lib.bf_batch_tune(self._h, _stream_ptr(stream), ctypes.byref(mo), ms), "bf_batch_tune")
+        return mo.value, [ms[0], ms[1]]
+
     def debug_hold(self, on=True):
         L.check(self._lib.bf_batch_debug_hold(self._h, int(on)), "bf_batch_debug_hold")
 

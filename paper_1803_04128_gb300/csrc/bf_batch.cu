@@ -53,7 +53,13 @@ bf_status enqueue(bf_batch* b, cudaStream_t st)
         set_error("bf_batch: no persistent grid configured");
         return BF_ERR_STATE;
     }
-    cudaError_t e = cudaMemsetAsync(b->reset_ptr, 0, b->reset_bytes, st);
+    cudaError_t e;
+    if (b->bl.mode == 1) {
+        e = batch_phases_f32(b->r, b->bl, st, false);
+        if (e != cudaSuccess) return cuda_fail("bf_batch: phase launches", e);
+        return BF_OK;
+    }
+    e = cudaMemsetAsync(b->reset_ptr, 0, b->reset_bytes, st);
     if (e != cudaSuccess) return cuda_fail("bf_batch: reset", e);
     e = batch_launch_f32(b->r, b->bl, st, false, nullptr);
     if (e != cudaSuccess) return cuda_fail("bf_batch: launch", e);
@@ -136,7 +142,7 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
     b->items.resize((size_t)n);
     std::vector<int64_t> off((size_t)(2 * n));
     int64_t tot = 0;
-    size_t smem = 0;
+    size_t smem = 0, smem_f = 0, smem_b = 0;
     for (int i = 0; i < n; ++i) {
         const DevBlock& B = in[i].plan->dev->blocks[0];
         BatchItem& bi = b->items[(size_t)i];
@@ -157,6 +163,21 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
             return BF_ERR_UNSUPPORTED;
         }
         smem = std::max(smem, std::max(sf, sb));
+        smem_f = std::max(smem_f, sf);
+        smem_b = std::max(smem_b, sb);
+    }
+    // mode 1's order: operators by decreasing work (front + back CTAs), so that the small ones
+    // fill the last wave of each phase
+    std::vector<int> ord((size_t)n);
+    for (int i = 0; i < n; ++i) ord[(size_t)i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+        const BatchItem &a = b->items[(size_t)x], &c = b->items[(size_t)y];
+        return a.nfront + a.nback > c.nfront + c.nback;
+    });
+    std::vector<int64_t> off_f((size_t)n + 1, 0), off_b((size_t)n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+        off_f[(size_t)k + 1] = off_f[(size_t)k] + b->items[(size_t)ord[(size_t)k]].nfront;
+        off_b[(size_t)k + 1] = off_b[(size_t)k] + b->items[(size_t)ord[(size_t)k]].nback;
     }
     // Work order: each operator's front segment, and its back segment once at
     // least kBackLag work items have been queued after that front segment (or
@@ -185,12 +206,15 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
         set_error("bf_batch_create: a tile needs %zu bytes of shared memory", smem);
         return BF_ERR_UNSUPPORTED;
     }
-    // device copies: items | off[2n] | seg[2n] | counter | done[n] | err
+    // device copies: items | off[2n] | seg[2n] | counter | done[n] | err | ord[n] | off_f[n+1] | off_b[n+1]
     const size_t s_items = ((size_t)n * sizeof(BatchItem) + 255) & ~(size_t)255;
     const size_t s_off = ((size_t)(2 * n) * sizeof(int64_t) + 255) & ~(size_t)255;
     const size_t s_seg = ((size_t)(2 * n) * sizeof(int) + 255) & ~(size_t)255;
     const size_t s_reset = ((sizeof(unsigned long long) + (size_t)n * sizeof(int)) + 255) & ~(size_t)255;
-    b->dmem_bytes = s_items + s_off + s_seg + s_reset + 256;
+    const size_t s_ord = ((size_t)n * sizeof(int) + 255) & ~(size_t)255;
+    const size_t s_offp = ((size_t)(n + 1) * sizeof(int64_t) + 255) & ~(size_t)255;
+    const size_t o_phase = s_items + s_off + s_seg + s_reset + 256;
+    b->dmem_bytes = o_phase + s_ord + 2 * s_offp;
     if ((e = cudaMalloc(&b->dmem, b->dmem_bytes)) != cudaSuccess) {
         free_batch(b);
         return cuda_fail("bf_batch_create: descriptors", e);
@@ -200,6 +224,9 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
     std::memcpy(host.data(), b->items.data(), (size_t)n * sizeof(BatchItem));
     std::memcpy(host.data() + s_items, off.data(), (size_t)(2 * n) * sizeof(int64_t));
     std::memcpy(host.data() + s_items + s_off, seg.data(), (size_t)(2 * n) * sizeof(int));
+    std::memcpy(host.data() + o_phase, ord.data(), (size_t)n * sizeof(int));
+    std::memcpy(host.data() + o_phase + s_ord, off_f.data(), (size_t)(n + 1) * sizeof(int64_t));
+    std::memcpy(host.data() + o_phase + s_ord + s_offp, off_b.data(), (size_t)(n + 1) * sizeof(int64_t));
     if ((e = cudaMemcpy(base, host.data(), b->dmem_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
         free_batch(b);
         return cuda_fail("bf_batch_create: upload", e);
@@ -215,7 +242,16 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
     b->bl.err = (int*)(b->reset_ptr + s_reset);
     b->bl.total = tot;
     b->bl.smem = smem;
+    b->bl.ord = (const int*)(base + o_phase);
+    b->bl.off_f = (const int64_t*)(base + o_phase + s_ord);
+    b->bl.off_b = (const int64_t*)(base + o_phase + s_ord + s_offp);
+    b->bl.smem_f = smem_f;
+    b->bl.smem_b = smem_b;
+    b->bl.total_f = off_f[(size_t)n];
+    b->bl.total_b = off_b[(size_t)n];
+    b->bl.mode = 0;
     e = batch_launch_f32(b->r, b->bl, nullptr, true, nullptr);
+    if (e == cudaSuccess) e = batch_phases_f32(b->r, b->bl, nullptr, true);
     if (e == cudaSuccess) e = batch_launch_f32(b->r, b->bl, nullptr, false, &b->bl.grid);
     if (e != cudaSuccess || b->bl.grid < 1) {
         free_batch(b);
@@ -309,6 +345,81 @@ bf_status bf_batch_get_info(const bf_batch* b, int64_t* work_items, int* grid, i
     if (ws_bytes) *ws_bytes = (int64_t)b->ws_bytes;
     if (smem) *smem = (int64_t)b->bl.smem;
     return BF_OK;
+}
+
+bf_status bf_batch_set_mode(bf_batch* b, int mode)
+{
+    if (!b || (mode != 0 && mode != 1)) {
+        set_error("bf_batch_set_mode: NULL batch or mode not 0 / 1");
+        return BF_ERR_ARG;
+    }
+    if (b->bl.mode != mode && b->exec) {
+        cudaGraphExecDestroy(b->exec);  // a captured graph holds the other mode's launches
+        b->exec = nullptr;
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->bl.mode = mode;
+    return BF_OK;
+}
+
+bf_status bf_batch_get_mode(const bf_batch* b, int* mode)
+{
+    if (!b || !mode) {
+        set_error("bf_batch_get_mode: NULL argument");
+        return BF_ERR_ARG;
+    }
+    *mode = b->bl.mode;
+    return BF_OK;
+}
+
+bf_status bf_batch_tune(bf_batch* b, void* stream, int* mode_out, double* ms_out)
+{
+    if (!b) {
+        set_error("bf_batch_tune: NULL batch");
+        return BF_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return cuda_fail("bf_batch_tune: cudaSetDevice", e);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail("bf_batch_tune: events", e);
+    }
+    const int keep = b->bl.mode;
+    double best = 1e30, ms[2] = {0, 0};
+    int bm = keep;
+    bf_status rs = BF_OK;
+    for (int mode = 0; mode < 2 && rs == BF_OK; ++mode) {
+        b->bl.mode = mode;
+        double tot = 0;
+        for (int rep = 0; rep < 4 && rs == BF_OK; ++rep) {  // one warm-up, three timed
+            cudaEventRecord(e0, st);
+            rs = enqueue(b, st);
+            cudaEventRecord(e1, st);
+            if (rs == BF_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) rs = cuda_fail("bf_batch_tune: run", e);
+            float t = 0;
+            if (rs == BF_OK) cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) tot += t;
+        }
+        ms[mode] = tot / 3;
+        if (rs == BF_OK && ms[mode] < best) {
+            best = ms[mode];
+            bm = mode;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->bl.mode = keep;
+    if (rs != BF_OK) return rs;
+    rs = bf_batch_set_mode(b, bm);
+    if (mode_out) *mode_out = bm;
+    if (ms_out) {
+        ms_out[0] = ms[0];
+        ms_out[1] = ms[1];
+    }
+    return rs;
 }
 
 bf_status bf_batch_set_spin_limit(bf_batch* b, long long polls)

@@ -108,6 +108,15 @@ struct BatchLaunch {
     int wait_extra = 0;  // test hook: extra front completions a back tile waits for (never arrive)
     size_t smem = 0;
     int grid = 0;
+    // mode 1 (two phase launches): one launch over every operator's front tiles, then one over
+    // every back tile, each CTA one work item; operators in the order ord (largest work first),
+    // work item w of a phase belongs to ord[k] with off_x[k] <= w < off_x[k + 1]
+    int mode = 0;
+    const int* ord = nullptr;      // [nitems]
+    const int64_t* off_f = nullptr;  // [nitems + 1]
+    const int64_t* off_b = nullptr;  // [nitems + 1]
+    size_t smem_f = 0, smem_b = 0;
+    int64_t total_f = 0, total_b = 0;  // work items (CTAs) of each phase
 };
 
 // one front and one back pass over all kH and kG levels (the batched and sharded applies)
@@ -126,5 +135,7 @@ cudaError_t launch_mid_otf(int r, const MidArgs& ma, size_t smem, int64_t nblock
 // grid_out != NULL: only compute the persistent grid (occupancy x SMs) for bl.smem;
 // otherwise launch (bl.grid CTAs).
 cudaError_t batch_launch_f32(int r, const BatchLaunch& bl, cudaStream_t st, bool set_attr, int* grid_out);
+// mode 1: the two phase launches (set_attr: configure the kernels' shared memory only)
+cudaError_t batch_phases_f32(int r, const BatchLaunch& bl, cudaStream_t st, bool set_attr);
 
 }  // namespace bfi

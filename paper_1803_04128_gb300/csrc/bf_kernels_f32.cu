@@ -114,6 +114,55 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
+// The batch in two phase launches: every operator's front tiles in one launch, then every
+// back tile in a second one (no hand-off waits: the launch boundary orders them).  One CTA per
+// work item, the tile bodies inlined, each launch with its own shared-memory size.
+template <int R, int NV, int BACK>
+__global__ void __launch_bounds__(kThreads, 2)
+    batch_phase_f32(const BatchItem* items, const int* ord, const int64_t* off, int nitems)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t w = blockIdx.x;
+    int lo = 0, hi = nitems - 1;  // the last k with off[k] <= w
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchItem& it = items[__ldg(ord + lo)];
+    const int64_t local = w - __ldg(off + lo);
+    if (BACK) back_tile<R, NV>(it.ba, local, smem_raw);
+    else front_tile<R, NV>(it.fa, local, smem_raw);
+}
+
+template <int R>
+cudaError_t batch_phases_r(const BatchLaunch& bl, cudaStream_t st, bool set_attr)
+{
+    constexpr int NV = nv_of<R>();
+    if (set_attr) {
+        cudaError_t e = cudaFuncSetAttribute(batch_phase_f32<R, NV, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bl.smem_f);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(batch_phase_f32<R, NV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bl.smem_b);
+    }
+    if (bl.total_f < 1 || bl.total_b < 1 || bl.total_f >= (1ll << 31) || bl.total_b >= (1ll << 31))
+        return cudaErrorInvalidConfiguration;
+    {
+        ProfScope ps("batch_front_f32", st);
+        batch_phase_f32<R, NV, 0><<<(unsigned)bl.total_f, kThreads, bl.smem_f, st>>>(bl.items, bl.ord, bl.off_f,
+                                                                                    bl.nitems);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps("batch_back_f32", st);
+        batch_phase_f32<R, NV, 1><<<(unsigned)bl.total_b, kThreads, bl.smem_b, st>>>(bl.items, bl.ord, bl.off_b,
+                                                                                   bl.nitems);
+    }
+    return cudaGetLastError();
+}
+
 template <int R>
 cudaError_t batch_launch_r(const BatchLaunch& bl, cudaStream_t st, bool set_attr, int* grid_out)
 {
@@ -556,6 +605,19 @@ cudaError_t launch_fused_f32_chunked(const DevBlock& B, const float2* F, int64_t
     if (e == cudaSuccess) e = cudaEventRecord(join[3], st2);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join[3], 0);
     return e;
+}
+
+cudaError_t batch_phases_f32(int r, const BatchLaunch& bl, cudaStream_t st, bool set_attr)
+{
+    switch (r) {
+    case 6: return batch_phases_r<6>(bl, st, set_attr);
+    case 8: return batch_phases_r<8>(bl, st, set_attr);
+    case 10: return batch_phases_r<10>(bl, st, set_attr);
+    case 12: return batch_phases_r<12>(bl, st, set_attr);
+    case 14: return batch_phases_r<14>(bl, st, set_attr);
+    case 16: return batch_phases_r<16>(bl, st, set_attr);
+    default: return cudaErrorNotSupported;
+    }
 }
 
 cudaError_t batch_launch_f32(int r, const BatchLaunch& bl, cudaStream_t st, bool set_attr, int* grid_out)

@@ -173,3 +173,31 @@ def test_apply_batched_rejects_bad_items():
     assert lib.bf_apply_batched(ctypes.cast(plans, ctypes.c_void_p), ctypes.cast(arr, ctypes.c_void_p), 1,
                                 None) == L.BF_ERR_ARG
     assert lib.bf_apply_batched(None, ctypes.cast(arr, ctypes.c_void_p), 1, None) == L.BF_ERR_ARG
+
+
+def test_two_phase_mode_is_bitwise_the_same_and_tunable():
+    # mode 1 (a front launch and a back launch over every operator) against mode 0 and the
+    # single applies, eager and replayed from a graph; the tuner keeps one of the two
+    ops = make_ops([(4096, 3), (16384, 40), (2048, 1), (65536, 17), (8192, 128)], seed=40)
+    b = api.Batch(ops)
+    assert b.mode() == 0
+    b.set_mode(1)
+    b.run()
+    assert b.status() == 0
+    ref = [plan.apply(F, prec=api.F32) for plan, F, G in ops]
+    for (plan, F, G), r in zip(ops, ref):
+        assert torch.equal(G, r)
+    for _, _, G in ops:
+        G.fill_(float("nan"))
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    b.capture(s)
+    b.replay(s)
+    assert b.status(s) == 0
+    for (plan, F, G), r in zip(ops, ref):
+        assert torch.equal(G, r)
+    mode, ms = b.tune()
+    assert mode in (0, 1) and ms[0] > 0 and ms[1] > 0 and b.mode() == mode
+    for (plan, F, G), r in zip(ops, ref):
+        assert torch.equal(G, r)
+    b.close()
