@@ -284,85 +284,6 @@ __device__ __forceinline__ void g_item(float2* x0, float2* x1, int CTp, const fl
     }
 }
 
-// With few (group, column) items per CTA, two threads share an item and each computes one
-// of its two outputs: the inputs are read into registers first (a barrier separates the reads
-// from the in-place writes), then each output is formed with exactly the FMAs, in the same
-// order, that h_item / g_item use for it, so the results are bitwise the same.
-template <int R>
-__device__ __forceinline__ void h_half(const float2 (&lam)[2 * R], float2* xo, int CTp, const float2* E,
-                                       const float* Mh)
-{
-    constexpr int R4 = Pad4<R>::v;
-    float2 o[R];
-#pragma unroll
-    for (int t = 0; t < R; ++t) o[t] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int cs2 = 0; cs2 < R; ++cs2) {
-        const float4 e = reinterpret_cast<const float4*>(E)[cs2];
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-            const int cs = 2 * cs2 + h2;
-            const float2 u = cmulf(h2 ? make_float2(e.z, e.w) : make_float2(e.x, e.y), lam[cs]);
-            const float4* mh = reinterpret_cast<const float4*>(Mh + cs * R4);
-#pragma unroll
-            for (int t4 = 0; t4 < R4 / 4; ++t4) {
-                const float4 w = mh[t4];
-                const float ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int t = 4 * t4 + q;
-                    if (t < R) {
-                        o[t].x = fmaf(ww[q], u.x, o[t].x);
-                        o[t].y = fmaf(ww[q], u.y, o[t].y);
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < R; ++t) xo[t * CTp] = o[t];
-}
-
-template <int R>
-__device__ __forceinline__ void g_half(const float2 (&nu0)[R], const float2 (&nu1)[R], float2* xo, int CTp,
-                                       const float2* Fp, const float* Mg, int pos)
-{
-    constexpr int R4 = Pad4<R>::v;
-    float2 w0[R], w1[R];
-#pragma unroll
-    for (int t = 0; t < R; ++t) w0[t] = w1[t] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int s = 0; s < R; ++s) {
-        const float4* mg = reinterpret_cast<const float4*>(Mg + (pos * R + s) * R4);
-#pragma unroll
-        for (int t4 = 0; t4 < R4 / 4; ++t4) {
-            const float4 w = mg[t4];
-            const float ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int t = 4 * t4 + q;
-                if (t < R) {
-                    w0[t].x = fmaf(ww[q], nu0[s].x, w0[t].x);
-                    w0[t].y = fmaf(ww[q], nu0[s].y, w0[t].y);
-                    w1[t].x = fmaf(ww[q], nu1[s].x, w1[t].x);
-                    w1[t].y = fmaf(ww[q], nu1[s].y, w1[t].y);
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int t2 = 0; t2 < R / 2; ++t2) {
-        const float4 fa = reinterpret_cast<const float4*>(Fp)[t2];
-        const float4 fb = reinterpret_cast<const float4*>(Fp + R)[t2];
-        float2 o = cmulf(make_float2(fa.x, fa.y), w0[2 * t2]);
-        cfmaf(o, make_float2(fb.x, fb.y), w1[2 * t2]);
-        xo[(2 * t2) * CTp] = o;
-        float2 o2 = cmulf(make_float2(fa.z, fa.w), w0[2 * t2 + 1]);
-        cfmaf(o2, make_float2(fb.z, fb.w), w1[2 * t2 + 1]);
-        xo[(2 * t2 + 1) * CTp] = o2;
-    }
-}
-
 // Switch blocks (step 4 of Algorithm 4.1) of the T = 2^K pairs (x-node (p << K) + lp at
 // level h, T_Omega node c0 at level L-h), lp < T, evaluated into Ss [T][R][R]:
 // entry (lp, t, s) = e(Phi(x_t, xi_s) - Phi(c_A, xi_s) - Phi(x_t, c_B)); one (lp, t) row per
@@ -425,7 +346,7 @@ __device__ __forceinline__ void switch_item(const float2* xs, int CTp, const flo
 // beside the tiles; the batched kernel keeps its slices wider).  With OTF the
 // phase tables are not read: EV, each level's EH and the switch blocks are
 // evaluated (otf_turns, otf_exp) into the same shared buffers.
-template <int R, int NV, bool OTF = false, bool HALF = false>
+template <int R, int NV, bool OTF = false>
 __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, unsigned char* smem_raw)
 {
     constexpr int R4 = Pad4<R>::v;
@@ -601,40 +522,15 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
         }
         const int kj = K - j, half = 1 << kj;
         const float* Mh = MHTs + (size_t)(j - 1) * 2 * R * R4;
-        const int items = tpc * (T / 2) * CTp;
-        if constexpr (HALF) {  // two threads per item (2 items <= kThreads), one output each
-            const int it = tid >> 1, side = tid & 1;
-            float2 lam[2 * R];
-            float2* xo = nullptr;
-            const float2* Eo = nullptr;
-            if (it < items) {
-                const int col = it & (CTp - 1), grp = (it >> lct) & (T / 2 - 1), u = it >> (lct + K - 1);
-                const int a = grp >> kj, bp = grp & (half - 1);
-                const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
-                float2* x0 = Xof(u) + (size_t)base * R * CTp + col;
-                float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
-#pragma unroll
-                for (int s = 0; s < R; ++s) {
-                    lam[s] = x0[s * CTp];
-                    lam[R + s] = x1[s * CTp];
-                }
-                const float2* Eh = EHof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
-                xo = side ? x1 : x0;
-                Eo = Eh + (size_t)((2 * a + side) * half + bp) * 2 * R;
-            }
-            __syncthreads();
-            if (it < items) h_half<R>(lam, xo, CTp, Eo, Mh);
-        } else {
-            for (int it = tid; it < items; it += kThreads) {
-                const int col = it & (CTp - 1), grp = (it >> lct) & (T / 2 - 1), u = it >> (lct + K - 1);
-                const int a = grp >> kj, bp = grp & (half - 1);
-                const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
-                float2* x0 = Xof(u) + (size_t)base * R * CTp + col;
-                float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
-                const float2* Eh = EHof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
-                h_item<R>(x0, x1, CTp, Eh + (size_t)((2 * a) * half + bp) * 2 * R,
-                          Eh + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mh);
-            }
+        for (int it = tid; it < tpc * (T / 2) * CTp; it += kThreads) {
+            const int col = it & (CTp - 1), grp = (it >> lct) & (T / 2 - 1), u = it >> (lct + K - 1);
+            const int a = grp >> kj, bp = grp & (half - 1);
+            const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
+            float2* x0 = Xof(u) + (size_t)base * R * CTp + col;
+            float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
+            const float2* Eh = EHof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
+            h_item<R>(x0, x1, CTp, Eh + (size_t)((2 * a) * half + bp) * 2 * R,
+                      Eh + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mh);
         }
         __syncthreads();
         if (j + 2 <= K) {
@@ -672,7 +568,7 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
 // G levels run together, their U contributions are accumulated one chunk after
 // the other in increasing c0' (the same order for any tpc).  With OTF, FG and
 // EU are evaluated into their shared buffers instead of copied.
-template <int R, int NU, bool OTF = false, bool HALF = false>
+template <int R, int NU, bool OTF = false>
 __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsigned char* smem_raw)
 {
     constexpr int R4 = Pad4<R>::v;
@@ -764,40 +660,15 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
             }
             const int kj = K - j, half = 1 << kj;
             const float* Mg = MGTs + (size_t)(j - 1) * 2 * R * R4;
-            const int items = tpc * (T / 2) * CTp;
-            if constexpr (HALF) {  // two threads per item (2 items <= kThreads), one position each
-                const int it = tid >> 1, side = tid & 1;
-                float2 nu0[R], nu1[R];
-                float2* xo = nullptr;
-                const float2* Fo = nullptr;
-                if (it < items) {
-                    const int col = it & (CTp - 1), grp = (it >> lct) & (T / 2 - 1), u = it >> (lct + K - 1);
-                    const int a = grp >> kj, bp = grp & (half - 1);
-                    const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
-                    float2* x0 = Xof(u) + (size_t)base * R * CTp + col;
-                    float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
-#pragma unroll
-                    for (int s2 = 0; s2 < R; ++s2) {
-                        nu0[s2] = x0[s2 * CTp];
-                        nu1[s2] = x1[s2 * CTp];
-                    }
-                    const float2* Fg = FGof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
-                    xo = side ? x1 : x0;
-                    Fo = Fg + (size_t)((2 * a + side) * half + bp) * 2 * R;
-                }
-                __syncthreads();
-                if (it < items) g_half<R>(nu0, nu1, xo, CTp, Fo, Mg, side);
-            } else {
-                for (int it = tid; it < items; it += kThreads) {
-                    const int col = it & (CTp - 1), grp = (it >> lct) & (T / 2 - 1), u = it >> (lct + K - 1);
-                    const int a = grp >> kj, bp = grp & (half - 1);
-                    const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
-                    float2* x0 = Xof(u) + (size_t)base * R * CTp + col;
-                    float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
-                    const float2* Fg = FGof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
-                    g_item<R>(x0, x1, CTp, Fg + (size_t)((2 * a) * half + bp) * 2 * R,
-                              Fg + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mg);
-                }
+            for (int it = tid; it < tpc * (T / 2) * CTp; it += kThreads) {
+                const int col = it & (CTp - 1), grp = (it >> lct) & (T / 2 - 1), u = it >> (lct + K - 1);
+                const int a = grp >> kj, bp = grp & (half - 1);
+                const int base = (bp << j) + (int)brev((unsigned)a, j - 1);
+                float2* x0 = Xof(u) + (size_t)base * R * CTp + col;
+                float2* x1 = x0 + (size_t)(1 << (j - 1)) * R * CTp;
+                const float2* Fg = FGof(u) + (size_t)((j - 1) & 1) * T * 2 * R;
+                g_item<R>(x0, x1, CTp, Fg + (size_t)((2 * a) * half + bp) * 2 * R,
+                          Fg + (size_t)((2 * a + 1) * half + bp) * 2 * R, Mg);
             }
             __syncthreads();
             if (j + 2 <= K) {

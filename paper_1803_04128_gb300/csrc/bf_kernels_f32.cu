@@ -10,68 +10,40 @@
 namespace bfi {
 namespace {
 
-// HALF: the tiles have at most kThreads / 2 (group, column) items per level, and two threads
-// share each item (one output each); a separate instantiation, so that the wide tiles keep
-// their register allocation.
-template <int R, int NV, bool HALF>
+template <int R, int NV>
 __global__ void __launch_bounds__(kThreads, 2) front_f32(FrontArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    front_tile<R, NV, false, HALF>(A, blockIdx.x, smem_raw);
+    front_tile<R, NV>(A, blockIdx.x, smem_raw);
 }
 
-template <int R, int NU, bool HALF>
+template <int R, int NU>
 __global__ void __launch_bounds__(kThreads, 2) back_f32(BackArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    back_tile<R, NU, false, HALF>(A, blockIdx.x, smem_raw);
-}
-
-inline bool half_items(int K, int tpc, int CTp) { return 2 * tpc * ((1 << K) / 2) * CTp <= kThreads; }
-
-template <int R, bool HALF>
-cudaError_t launch_front_k(const FrontArgs& fa, size_t sf, int64_t nfront, cudaStream_t st)
-{
-    constexpr int NV = nv_of<R>();
-    cudaError_t e = cudaFuncSetAttribute(front_f32<R, NV, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
-    if (e != cudaSuccess) return e;
-    ProfScope ps("front_f32", st);
-    front_f32<R, NV, HALF><<<(unsigned)nfront, kThreads, sf, st>>>(fa);
-    return cudaGetLastError();
-}
-
-template <int R, bool HALF>
-cudaError_t launch_back_k(const BackArgs& ba, size_t sb, int64_t nback, cudaStream_t st)
-{
-    constexpr int NV = nv_of<R>();
-    cudaError_t e = cudaFuncSetAttribute(back_f32<R, NV, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-    if (e != cudaSuccess) return e;
-    ProfScope ps("back_f32", st);
-    back_f32<R, NV, HALF><<<(unsigned)nback, kThreads, sb, st>>>(ba);
-    return cudaGetLastError();
-}
-
-template <int R>
-cudaError_t launch_front_r(const FrontArgs& fa, size_t sf, int64_t nfront, cudaStream_t st)
-{
-    return half_items(fa.K, fa.tpc, fa.CTp) ? launch_front_k<R, true>(fa, sf, nfront, st)
-                                            : launch_front_k<R, false>(fa, sf, nfront, st);
-}
-
-template <int R>
-cudaError_t launch_back_r(const BackArgs& ba, size_t sb, int64_t nback, cudaStream_t st)
-{
-    return half_items(ba.K, ba.tpc, ba.CTp) ? launch_back_k<R, true>(ba, sb, nback, st)
-                                            : launch_back_k<R, false>(ba, sb, nback, st);
+    back_tile<R, NU>(A, blockIdx.x, smem_raw);
 }
 
 template <int R>
 cudaError_t launch_r(const FrontArgs& fa, const BackArgs& ba, size_t sf, size_t sb, int64_t nfront, int64_t nback,
                      cudaStream_t st)
 {
-    const cudaError_t e = launch_front_r<R>(fa, sf, nfront, st);
+    constexpr int NV = nv_of<R>();
+    cudaError_t e = cudaFuncSetAttribute(front_f32<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
     if (e != cudaSuccess) return e;
-    return launch_back_r<R>(ba, sb, nback, st);
+    e = cudaFuncSetAttribute(back_f32<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps("front_f32", st);
+        front_f32<R, NV><<<(unsigned)nfront, kThreads, sf, st>>>(fa);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps("back_f32", st);
+        back_f32<R, NV><<<(unsigned)nback, kThreads, sb, st>>>(ba);
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- batched --
@@ -424,7 +396,22 @@ bool fused_make_args(const DevBlock& B, const float2* F, int64_t m, float2* G, i
 template <int R>
 cudaError_t launch_part_r(const FrontArgs* fa, const BackArgs* ba, size_t smem, int64_t nblocks, cudaStream_t st)
 {
-    return fa ? launch_front_r<R>(*fa, smem, nblocks, st) : launch_back_r<R>(*ba, smem, nblocks, st);
+    constexpr int NV = nv_of<R>();
+    cudaError_t e;
+    if (fa) {
+        if ((e = cudaFuncSetAttribute(front_f32<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        ProfScope ps("front_f32", st);
+        front_f32<R, NV><<<(unsigned)nblocks, kThreads, smem, st>>>(*fa);
+    } else {
+        if ((e = cudaFuncSetAttribute(back_f32<R, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        ProfScope ps("back_f32", st);
+        back_f32<R, NV><<<(unsigned)nblocks, kThreads, smem, st>>>(*ba);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_part(int r, const FrontArgs* fa, const BackArgs* ba, size_t smem, int64_t nblocks, cudaStream_t st)
