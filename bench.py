@@ -745,7 +745,7 @@ def nufft_side(w, F, G, flush, stream, local, steps, warmup):
             "apply_frac": sum(byt.values()) / (ms / steps * 1e-3) / 1e9 / peaks["hbm_gbs"],
             "peak_source": "measured copy bandwidth (%s)" % src}
     Gh = Gn.cpu().numpy()
-    err, nrows = oracle_rows_err(w, None, Gh, 256, G_rows=None, F_dev=F)
+    err, nrows = oracle_rows_err(w, None, Gh, w.get("err_rows", 256), G_rows=None, F_dev=F)
     out = {"value": N * m * steps / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms / steps, "msp": msp,
            "t_prepare_s": round(t_prep, 3), "rel_err_vs_fp64_oracle": err, "rel_err_rows": nrows,
            "rel_diff_vs_butterfly_apply": None if G is None else float((Gn - G).norm() / G.norm()),
@@ -1027,6 +1027,13 @@ def side_lines(args, rank, world, local):
                desc="piecewise FIO (jump at x=1/2), N=262144 as four N/2 sub-BFs, m=256, alpha as fio2, complex "
                     "FP32 apply, BF eps=1e-6 (r=10), V and U at the built-in level 4")
     out["fio3_f32"] = run_single(args, w3f, rank, world, local, st, wu, sides=False)
+    # the same operator by the NUFFT of Eq. tg3 (its phase is rank 1 on each column half)
+    from paper_1803_04128_gb300 import inputs
+    F3 = torch.from_numpy(inputs.complex_gaussian(w3["N"], w3["m"], seed=rank)).to(torch.complex64).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out["fio3_nufft"] = nufft_side(dict(w3f, err_rows=24), F3, None, flush, torch.cuda.current_stream(), local, st, wu)
+    del F3, flush
+    torch.cuda.empty_cache()
     torch.cuda.empty_cache()
     out["fio4"] = run_batched(args, dict(WORKLOADS["fio4"], name="fio4"), rank, world, local, steps=st, warmup=wu)
     torch.cuda.empty_cache()
