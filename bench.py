@@ -362,7 +362,7 @@ def run_serving(args, w, rank, world, local, side=False):
                       factor_on_device=True) for N in Ns]
     t_factor = time.perf_counter() - t0
     warm = 1.0
-    secs, secs_light = (4.0, 4.0) if side else (w["seconds"], w["seconds_light"])
+    secs, secs_light = (4.0, 6.0) if side else (w["seconds"], w["seconds_light"])
 
     def pools_for(cdt):
         out = {}
@@ -387,8 +387,10 @@ def run_serving(args, w, rank, world, local, side=False):
     for name, prec, slots, per_req, cdt, rate, secs_run, method in runs:
         window = warm + secs_run
         times, opi, ms = inputs.poisson_requests(rate, window, len(Ns), mset, seed=rank)
-        srv = api.Server(n_slots=slots, max_batch_rhs=256, precision=prec, per_request=per_req, device=local,
-                         method=method)
+        # batch width: 256 right-hand sides under overload (throughput); 64 at the light rate,
+        # so that a large request never waits for a batch four times its own size (latency)
+        srv = api.Server(n_slots=slots, max_batch_rhs=64 if "light" in name else 256, precision=prec,
+                         per_request=per_req, device=local, method=method)
         ops = [srv.add(p) for p in plans]
         srv.start()
         # start-up: every (operator, m) served once before the trace, so that first-use costs
