@@ -10,7 +10,11 @@
  * pending requests as fit (column-concatenated right-hand sides) into one
  * apply (a priority slot takes the oldest small request and packs up to the
  * small-batch size); requests that arrive while slots are busy wait for the next free
- * slot; the S slots' batches run concurrently on the device.  Each request's
+ * slot; the S slots' batches run concurrently on the device.  A batch of 2..64
+ * requests and at most 1024 right-hand sides moves each request's rows in one
+ * contiguous host<->device copy and interleaves the column blocks on the
+ * device; larger batches copy each request's column block with a strided 2-D
+ * copy (slow for narrow blocks).  Each request's
  * result is bit-identical to applying its operator to that request alone
  * (columns never mix).  The paper has no serving component: this rests on its
  * observation (Sec. 1 footnote) that the factorisation is built once and then

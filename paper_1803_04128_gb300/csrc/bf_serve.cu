@@ -22,6 +22,57 @@ namespace {
 using Clock = std::chrono::steady_clock;
 // device intervals kept for the busy / overlap statistics (per reset; later batches are not counted)
 constexpr size_t kMaxSpans = (size_t)1 << 20;
+// batches of 2..kMaxSegs requests and at most kMaxCols columns move each request's rows as one
+// contiguous copy and interleave them on the device (a host copy with rows of m elements is
+// slow for small m); others copy each request's column block with a 2-D copy
+constexpr int kMaxSegs = 64, kMaxCols = 1024;
+
+// Column blocks of a batch: request k owns columns [c0[k], c0[k + 1]) of the [N][M] batch
+// and, in the contiguous staging buffer, the N x m_k rows from element c0[k] * N on.
+struct Segs {
+    int n;
+    int c0[kMaxSegs + 1];
+};
+
+// GATHER: dst[x][col] = staging of col's request (x, col - c0);  else the reverse.  A block
+// takes chunks of about 4096 consecutive batch elements (whole rows of [N][M]), one thread
+// per element, so the batch side is coalesced and each request's side walks its rows
+// contiguously.
+template <typename T, bool GATHER>
+__global__ void interleave(const T* __restrict__ src, T* __restrict__ dst, int64_t N, int M, Segs sg)
+{
+    __shared__ short seg_of[kMaxCols];
+    for (int k = 0; k < sg.n; ++k)
+        for (int c = sg.c0[k] + (int)threadIdx.x; c < sg.c0[k + 1]; c += blockDim.x) seg_of[c] = (short)k;
+    __syncthreads();
+    const int rows = M >= 4096 ? 1 : 4096 / M;
+    const int64_t nchunks = (N + rows - 1) / rows;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t x0 = ch * rows;
+        const int nr = (int)(N - x0 < rows ? N - x0 : rows);
+        for (int i = threadIdx.x; i < nr * M; i += blockDim.x) {
+            const int xl = i / M, col = i - xl * M, k = seg_of[col], c0 = sg.c0[k], mk = sg.c0[k + 1] - c0;
+            const int64_t e = x0 * M + i, st = (int64_t)c0 * N + (x0 + xl) * mk + (col - c0);
+            if (GATHER) dst[e] = src[st];
+            else dst[st] = src[e];
+        }
+    }
+}
+
+cudaError_t launch_interleave(bool gather, size_t elt, const void* src, void* dst, int64_t N, int M, const Segs& sg,
+                              int nsm, cudaStream_t st)
+{
+    const int64_t chunks = (N + (4096 / M) - 1) / (4096 / M);  // M <= kMaxCols < 4096
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)nsm * 8));
+    if (elt == sizeof(float2)) {
+        if (gather) interleave<float2, true><<<grid, 256, 0, st>>>((const float2*)src, (float2*)dst, N, M, sg);
+        else interleave<float2, false><<<grid, 256, 0, st>>>((const float2*)src, (float2*)dst, N, M, sg);
+    } else {
+        if (gather) interleave<double2, true><<<grid, 256, 0, st>>>((const double2*)src, (double2*)dst, N, M, sg);
+        else interleave<double2, false><<<grid, 256, 0, st>>>((const double2*)src, (double2*)dst, N, M, sg);
+    }
+    return cudaGetLastError();
+}
 
 double ms_since(Clock::time_point a, Clock::time_point b)
 {
@@ -83,6 +134,7 @@ struct bf_server {
     // device intervals [start, end) of completed batches, ms after the base event
     cudaEvent_t base = nullptr;
     std::vector<std::pair<double, double>> spans;
+    int nsm = 1;  // SMs of the device (grid of the interleave kernels)
 };
 
 namespace {
@@ -126,21 +178,41 @@ bf_status enqueue_batch(bf_server* s, Slot& sl, Op& op, std::vector<Req*>& rs)
     const size_t elt = s->elt;
     cudaError_t e = cudaEventRecord(sl.ev0, sl.st);
     if (e != cudaSuccess) return BF_ERR_CUDA;
+    // staged: each request's rows in one contiguous copy into sl.G (free until the apply
+    // writes it), interleaved into sl.F; after the apply, G de-interleaved into sl.F (free
+    // again) and copied out per request
+    const bool staged = rs.size() > 1 && rs.size() <= (size_t)kMaxSegs && M <= kMaxCols;
+    Segs sg{};
     int64_t c = 0;
     for (Req* r : rs) {
-        e = cudaMemcpy2DAsync((unsigned char*)sl.F + c * elt, (size_t)M * elt, r->F, (size_t)r->m * elt,
-                              (size_t)r->m * elt, (size_t)N, cudaMemcpyHostToDevice, sl.st);
+        if (staged) {
+            sg.c0[sg.n++] = (int)c;
+            e = cudaMemcpyAsync((unsigned char*)sl.G + (size_t)c * N * elt, r->F, (size_t)N * r->m * elt,
+                                cudaMemcpyHostToDevice, sl.st);
+        } else {
+            e = cudaMemcpy2DAsync((unsigned char*)sl.F + c * elt, (size_t)M * elt, r->F, (size_t)r->m * elt,
+                                  (size_t)r->m * elt, (size_t)N, cudaMemcpyHostToDevice, sl.st);
+        }
         if (e != cudaSuccess) return BF_ERR_CUDA;
         c += r->m;
     }
+    sg.c0[sg.n] = (int)c;
+    if (staged && launch_interleave(true, elt, sl.G, sl.F, N, (int)M, sg, s->nsm, sl.st) != cudaSuccess)
+        return BF_ERR_CUDA;
     bf_status st = op.nufft ? nufft_apply_ws(op.plan, sl.F, M, sl.G, sl.st, sl.ws, sl.ws_bytes)
                             : device_apply_ws(op.plan, (bf_precision)s->opt.precision, sl.F, M, sl.G, sl.st, sl.ws,
                                               sl.ws_bytes);
     if (st != BF_OK) return st;
+    if (staged && launch_interleave(false, elt, sl.G, sl.F, N, (int)M, sg, s->nsm, sl.st) != cudaSuccess)
+        return BF_ERR_CUDA;
     c = 0;
     for (Req* r : rs) {
-        e = cudaMemcpy2DAsync(r->G, (size_t)r->m * elt, (unsigned char*)sl.G + c * elt, (size_t)M * elt,
-                              (size_t)r->m * elt, (size_t)N, cudaMemcpyDeviceToHost, sl.st);
+        if (staged)
+            e = cudaMemcpyAsync(r->G, (unsigned char*)sl.F + (size_t)c * N * elt, (size_t)N * r->m * elt,
+                                cudaMemcpyDeviceToHost, sl.st);
+        else
+            e = cudaMemcpy2DAsync(r->G, (size_t)r->m * elt, (unsigned char*)sl.G + c * elt, (size_t)M * elt,
+                                  (size_t)r->m * elt, (size_t)N, cudaMemcpyDeviceToHost, sl.st);
         if (e != cudaSuccess) return BF_ERR_CUDA;
         c += r->m;
     }
@@ -274,7 +346,8 @@ bf_status bf_server_create(const bf_server_options* opt, bf_server** out)
         return BF_ERR_ARG;
     }
     s->elt = s->opt.precision == BF_PREC_F64 ? sizeof(double2) : sizeof(float2);
-    if (cudaSetDevice(s->opt.device) != cudaSuccess) {
+    if (cudaSetDevice(s->opt.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->opt.device) != cudaSuccess) {
         delete s;
         set_error("bf_server_create: cannot use device %d", s->opt.device);
         return BF_ERR_CUDA;

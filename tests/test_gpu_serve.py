@@ -161,3 +161,37 @@ def test_auto_method_serves_nufft_where_the_phase_allows():
     gd = od.direct(od.SEP, 4096, F.numpy().astype(np.complex128), rows, amp=1)
     assert relerr(G.numpy()[rows], gd) < 1e-5
     srv.close()
+
+
+@pytest.mark.parametrize("prec,max_rhs,ms,n", [
+    (api.F64, 64, (1, 4, 16), 24),      # batches of several requests, 16-byte elements
+    (api.F32, 256, (1,), 120),          # more requests in a batch than the staged copy takes
+    (api.F32, 2048, (200, 300), 12),    # batches wider than the staged copy takes
+])
+def test_batch_copies_keep_results_bitwise(prec, max_rhs, ms, n):
+    # a batch moves its requests' rows either as one contiguous copy per request plus a device
+    # interleave, or (many or wide requests) as one strided copy per request; both give each
+    # request exactly its apply alone
+    Ns = [1024, 2048]
+    plans = [api.Plan(N, eps=1e-6, amp_kind=L.AMP_SMOOTH) for N in Ns]
+    srv = api.Server(n_slots=2, max_batch_rhs=max_rhs, precision=prec, n_priority_slots=0)
+    ops = [srv.add(p) for p in plans]
+    srv.start()
+    rng = np.random.default_rng(7)
+    dt = np.complex128 if prec == api.F64 else np.complex64
+    reqs = []
+    for k in range(n):
+        o = int(rng.integers(0, 2))
+        m = int(rng.choice(ms))
+        F = torch.from_numpy(inputs.complex_gaussian(Ns[o], m, seed=900 + k).astype(dt)).pin_memory()
+        G = torch.full_like(F, float("nan")).pin_memory()
+        reqs.append((o, F, G))
+    rids = [srv.submit(ops[o], F, G) for o, F, G in reqs]
+    for rid in rids:
+        srv.wait(rid, 120000.0)
+    st = srv.stats()
+    assert st["completed"] == n and st["launches"] < n, st
+    for o, F, G in reqs:
+        alone = plans[o].apply(F.cuda(), prec=prec).cpu()
+        assert torch.equal(G, alone)
+    srv.close()
