@@ -242,18 +242,23 @@ struct InterpArgs {
 
 // G[i][c] = sum_h sum_k pa[h][k][i] sum_q W[h][i][q] H[h][(p0 + q) mod n][k m + c].
 // A CTA takes a tile of kTile consecutive targets and 32 consecutive right-hand sides c; warp
-// w takes the run of kRun targets i0 + w kRun .. and the 32 c (lanes).  For each half h and
-// amplitude term k in turn, the grid rows the tile's windows cover (span_T rows from p_lo)
-// are copied into shared memory with cp.async (8 bytes per (row, c), zero-filled past m),
-// then each warp walks the union of its own run's windows once: every row feeds all kRun
-// targets through the warp's dense weight block Wd[p - p_run][t] (zero outside target t's
-// window).  Tiles whose rows exceed the buffer (targets far apart, e.g. at a jump of the
-// phase) read each target's window from global memory instead.  Every output is the sum
-// over the same weights and rows in increasing p either way.
+// w takes the run of kRun targets i0 + w kRun .. and the 32 c (lanes).  The rounds r = (h, k),
+// h outer, each need the grid rows that the tile's windows cover for half h (span_T rows from
+// p_lo), columns k m + c0 .. + 31.  kBuf rounds are in flight at once: their rows are copied
+// with cp.async (zero-filled past m) into a ring of kBuf shared buffers, one commit group per
+// round, so that the next rounds' copies overlap the current round's arithmetic.  In a round
+// each warp walks the union of its own run's windows once: every row feeds all kRun targets
+// through the warp's dense weight block Wd[p - p_run][t] (zero outside target t's window),
+// built at the first round of each half.  Tiles whose rows exceed a buffer (targets far apart,
+// e.g. at a jump of the phase) read each target's window from global memory instead.  Every
+// output is the sum over the same weights and rows in increasing p, then k, then h, either way.
 constexpr int kRun = 8;
 constexpr int kTile = 64;                   // targets per CTA = kRun * 8 warps
 constexpr int kSpanMax = 48;                // rows of one warp's union of windows
-constexpr int kRowsMax = 128;               // rows of the CTA's buffer
+constexpr int kRowsMax = 112;               // rows of one buffer
+constexpr int kBuf = 2;                     // rounds whose rows are in flight together
+constexpr size_t kInterpSmem = (size_t)kBuf * kRowsMax * 32 * sizeof(float2) +
+                               (size_t)(kNuThreads / 32) * kSpanMax * kRun * sizeof(float);
 __device__ __forceinline__ void nu_cp8(void* dst, const void* src, bool valid)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
@@ -276,13 +281,14 @@ __device__ __forceinline__ void nu_fma2(float2& acc, float w, float2 v)
 }
 __global__ void __launch_bounds__(kNuThreads, 3) nufft_interp(const InterpArgs A)
 {
-    __shared__ __align__(16) float2 Hs[kRowsMax][32];
-    __shared__ __align__(16) float Wd_all[kNuThreads / 32][kSpanMax][kRun];
-    __shared__ int Rel_all[kNuThreads / 32][kRun];
-    __shared__ int s_lo[kNuThreads / 32], s_hi[kNuThreads / 32];
+    extern __shared__ __align__(16) unsigned char nu_sm[];
+    float2(*Hb)[32] = reinterpret_cast<float2(*)[32]>(nu_sm);  // kBuf buffers of kRowsMax rows
+    float(*Wd)[kRun] = reinterpret_cast<float(*)[kRun]>(nu_sm + (size_t)kBuf * kRowsMax * 32 * sizeof(float2)) +
+                       (size_t)(threadIdx.x >> 5) * kSpanMax;
+    __shared__ int Rel_all[2][kNuThreads / 32][kRun];
+    __shared__ int s_lo[2][kNuThreads / 32], s_hi[2][kNuThreads / 32];
+    __shared__ int s_pT[2], s_tlo[2], s_spanT[2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float (*Wd)[kRun] = Wd_all[wid];
-    int* Rel = Rel_all[wid];
     const int64_t ncb = (A.m + 31) / 32;
     const int64_t tile = blockIdx.x / ncb;
     const int64_t c0 = (blockIdx.x % ncb) * 32;
@@ -291,12 +297,8 @@ __global__ void __launch_bounds__(kNuThreads, 3) nufft_interp(const InterpArgs A
     const bool live = c < A.m;
     const int w2 = 2 * A.msp;
     const int nmask = (int)(A.n - 1);
-    float2 g[kRun];
-#pragma unroll
-    for (int t = 0; t < kRun; ++t) g[t] = make_float2(0.f, 0.f);
+    // window starts of both halves relative to the tile's first target, as signed offsets mod n
     for (int h = 0; h < 2; ++h) {
-        const float2* Hh = A.H + (int64_t)h * A.n * A.Mc;
-        // window starts relative to the tile's first target, as signed offsets mod n
         const int pT = __ldg(A.p0 + h * A.N + iT);
         int rel = 0;
         if (lane < kRun) {
@@ -310,102 +312,126 @@ __global__ void __launch_bounds__(kNuThreads, 3) nufft_interp(const InterpArgs A
             lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
             hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         }
+        if (lane < kRun) Rel_all[h][wid][lane] = rel - lo;
         if (lane == 0) {
-            s_lo[wid] = lo;
-            s_hi[wid] = hi;
+            s_lo[h][wid] = lo;
+            s_hi[h][wid] = hi;
         }
-        __syncthreads();
+        if (threadIdx.x == 0) s_pT[h] = pT;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        const int h = threadIdx.x;
         int tlo = INT_MAX, thi = INT_MIN;
-#pragma unroll
         for (int w = 0; w < kNuThreads / 32; ++w) {
-            tlo = min(tlo, s_lo[w]);
-            thi = max(thi, s_hi[w]);
+            tlo = min(tlo, s_lo[h][w]);
+            thi = max(thi, s_hi[h][w]);
         }
-        const int spanT = thi - tlo + w2;      // CTA-uniform
-        const int span = hi - lo + w2;         // warp-uniform
-        const bool tiled = spanT <= kRowsMax;  // CTA-uniform
-        // the warp's weights: Wd = 0, then each target's 2 msp weights (contiguous in W for
-        // the run: one coalesced read) at rows Rel[t] .. Rel[t] + 2 msp - 1 of its span
-        if (tiled) {
-            if (lane < kRun) Rel[lane] = rel - lo;
-            __syncwarp();
-            if (span <= kSpanMax) {
-                for (int e = lane; e < kSpanMax * kRun; e += 32) (&Wd[0][0])[e] = 0.f;
-                __syncwarp();
-                const float* Wr = A.W + (h * A.N + i0) * w2;
-                for (int e = lane; e < kRun * w2; e += 32) {
-                    const int t = e / w2, q = e - t * w2;
-                    Wd[Rel[t] + q][t] = __ldg(Wr + e);
-                }
-            }
-        }
-        for (int k = 0; k < A.ra; ++k) {
-            float2 acc[kRun];
-#pragma unroll
-            for (int t = 0; t < kRun; ++t) acc[t] = make_float2(0.f, 0.f);
-            if (tiled) {
-                // rows pT + tlo .. pT + tlo + spanT - 1 (mod n) of columns k m + c0 .. + 31
-                const float2* src = Hh + k * A.m + c0;
+        s_tlo[h] = tlo;
+        s_spanT[h] = thi - tlo + w2;
+    }
+    __syncthreads();
+    const int nr = 2 * A.ra;  // rounds
+    // the copies of round r into buffer r % kBuf (none for an untiled half), one commit group
+    auto issue = [&](int r) {
+        if (r < nr) {
+            const int h = r / A.ra, k = r - h * A.ra, spanT = s_spanT[h];
+            if (spanT <= kRowsMax) {
+                float2(*Hs)[32] = Hb + (r % kBuf) * kRowsMax;
+                const float2* src = A.H + (int64_t)h * A.n * A.Mc + k * A.m + c0;
+                const int pl = s_pT[h] + s_tlo[h];
                 if ((A.m & 1) == 0) {  // even m: every (row, column pair) is 16-byte aligned
                     for (int e = threadIdx.x; e < spanT * 16; e += kNuThreads) {
                         const int pp = e >> 4, cc = 2 * (e & 15);
                         const bool ok = c0 + cc < A.m;
-                        nu_cp16(&Hs[pp][cc], src + (int64_t)((pT + tlo + pp) & nmask) * A.Mc + (ok ? cc : 0), ok);
+                        nu_cp16(&Hs[pp][cc], src + (int64_t)((pl + pp) & nmask) * A.Mc + (ok ? cc : 0), ok);
                     }
                 } else {
                     for (int e = threadIdx.x; e < spanT * 32; e += kNuThreads) {
                         const int pp = e >> 5, cc = e & 31;
                         const bool ok = c0 + cc < A.m;
-                        nu_cp8(&Hs[pp][cc], src + (int64_t)((pT + tlo + pp) & nmask) * A.Mc + (ok ? cc : 0), ok);
+                        nu_cp8(&Hs[pp][cc], src + (int64_t)((pl + pp) & nmask) * A.Mc + (ok ? cc : 0), ok);
                     }
                 }
-                asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-                __syncthreads();
-                if (live && span <= kSpanMax) {
-                    const int base = lo - tlo;
-                    for (int pp = 0; pp < span; ++pp) {
-                        const float2 hv = Hs[base + pp][lane];
-                        const float4 wa = *reinterpret_cast<const float4*>(&Wd[pp][0]);
-                        const float4 wb = *reinterpret_cast<const float4*>(&Wd[pp][4]);
-                        const float ww[kRun] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-                        for (int t = 0; t < kRun; ++t) nu_fma2(acc[t], ww[t], hv);
-                    }
-                } else if (live) {  // the run's windows are far apart: each target on its own
-#pragma unroll
-                    for (int t = 0; t < kRun; ++t) {
-                        const int b0 = lo - tlo + Rel[t];
-                        for (int q = 0; q < w2; ++q) {
-                            const float2 hv = Hs[b0 + q][lane];
-                            const float w = __ldg(A.W + (h * A.N + i0 + t) * w2 + q);
-                            acc[t].x = fmaf(w, hv.x, acc[t].x);
-                            acc[t].y = fmaf(w, hv.y, acc[t].y);
-                        }
-                    }
-                }
-                __syncthreads();  // the buffer is refilled for the next (h, k)
-            } else if (live) {
-#pragma unroll
-                for (int t = 0; t < kRun; ++t) {
-                    const int64_t i = i0 + t;
-                    const int p0 = __ldg(A.p0 + h * A.N + i);
-                    const float* w = A.W + (h * A.N + i) * w2;
-                    for (int q = 0; q < w2; ++q) {
-                        const float wq = __ldg(w + q);
-                        const float2 hv = __ldg(Hh + (int64_t)((p0 + q) & nmask) * A.Mc + k * A.m + c);
-                        acc[t].x = fmaf(wq, hv.x, acc[t].x);
-                        acc[t].y = fmaf(wq, hv.y, acc[t].y);
-                    }
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < kRun; ++t) {
-                const float2 pk = __ldg(A.pa + ((int64_t)h * A.ra + k) * A.N + i0 + t);
-                g[t].x = fmaf(pk.x, acc[t].x, fmaf(-pk.y, acc[t].y, g[t].x));
-                g[t].y = fmaf(pk.x, acc[t].y, fmaf(pk.y, acc[t].x, g[t].y));
             }
         }
-        __syncthreads();  // s_lo / s_hi and the weights are rewritten for the next half
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+#pragma unroll
+    for (int r = 0; r < kBuf; ++r) issue(r);
+    float2 g[kRun];
+#pragma unroll
+    for (int t = 0; t < kRun; ++t) g[t] = make_float2(0.f, 0.f);
+    for (int r = 0; r < nr; ++r) {
+        const int h = r / A.ra, k = r - h * A.ra;
+        const bool tiled = s_spanT[h] <= kRowsMax;                     // CTA-uniform
+        const int lo = s_lo[h][wid], span = s_hi[h][wid] - lo + w2;  // warp-uniform
+        const int* Rel = Rel_all[h][wid];
+        // groups committed: kBuf + r; round r's is complete once at most kBuf - 1 are pending
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kBuf - 1) : "memory");
+        __syncthreads();
+        if (k == 0 && tiled && span <= kSpanMax) {
+            // the warp's weights for half h: Wd = 0, then each target's 2 msp weights
+            // (contiguous in W for the run: one coalesced read) at rows Rel[t] .. of its span
+            for (int e = lane; e < kSpanMax * kRun; e += 32) (&Wd[0][0])[e] = 0.f;
+            __syncwarp();
+            const float* Wr = A.W + (h * A.N + i0) * w2;
+            for (int e = lane; e < kRun * w2; e += 32) {
+                const int t = e / w2, q = e - t * w2;
+                Wd[Rel[t] + q][t] = __ldg(Wr + e);
+            }
+            __syncwarp();
+        }
+        float2 acc[kRun];
+#pragma unroll
+        for (int t = 0; t < kRun; ++t) acc[t] = make_float2(0.f, 0.f);
+        if (tiled) {
+            float2(*Hs)[32] = Hb + (r % kBuf) * kRowsMax;
+            const int base = lo - s_tlo[h];
+            if (live && span <= kSpanMax) {
+                for (int pp = 0; pp < span; ++pp) {
+                    const float2 hv = Hs[base + pp][lane];
+                    const float4 wa = *reinterpret_cast<const float4*>(&Wd[pp][0]);
+                    const float4 wb = *reinterpret_cast<const float4*>(&Wd[pp][4]);
+                    const float ww[kRun] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                    for (int t = 0; t < kRun; ++t) nu_fma2(acc[t], ww[t], hv);
+                }
+            } else if (live) {  // the run's windows are far apart: each target on its own
+#pragma unroll
+                for (int t = 0; t < kRun; ++t) {
+                    const int b0 = base + Rel[t];
+                    for (int q = 0; q < w2; ++q) {
+                        const float2 hv = Hs[b0 + q][lane];
+                        const float w = __ldg(A.W + (h * A.N + i0 + t) * w2 + q);
+                        acc[t].x = fmaf(w, hv.x, acc[t].x);
+                        acc[t].y = fmaf(w, hv.y, acc[t].y);
+                    }
+                }
+            }
+        } else if (live) {
+            const float2* Hh = A.H + (int64_t)h * A.n * A.Mc;
+#pragma unroll
+            for (int t = 0; t < kRun; ++t) {
+                const int64_t i = i0 + t;
+                const int p0 = __ldg(A.p0 + h * A.N + i);
+                const float* w = A.W + (h * A.N + i) * w2;
+                for (int q = 0; q < w2; ++q) {
+                    const float wq = __ldg(w + q);
+                    const float2 hv = __ldg(Hh + (int64_t)((p0 + q) & nmask) * A.Mc + k * A.m + c);
+                    acc[t].x = fmaf(wq, hv.x, acc[t].x);
+                    acc[t].y = fmaf(wq, hv.y, acc[t].y);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kRun; ++t) {
+            const float2 pk = __ldg(A.pa + ((int64_t)h * A.ra + k) * A.N + i0 + t);
+            g[t].x = fmaf(pk.x, acc[t].x, fmaf(-pk.y, acc[t].y, g[t].x));
+            g[t].y = fmaf(pk.x, acc[t].y, fmaf(pk.y, acc[t].x, g[t].y));
+        }
+        __syncthreads();  // buffer r % kBuf and the weights are free
+        issue(r + kBuf);
     }
     if (live) {
 #pragma unroll
@@ -592,6 +618,8 @@ extern "C" bf_status bf_nufft_prepare(bf_plan* p, double eps, int* msp_out)
     if (e == cudaSuccess) e = cudaMemcpy(s->p0, p0.data(), p0.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w32, w32, sizeof(w32));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(nufft_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInterpSmem);
     if (cur >= 0) cudaSetDevice(cur);
     if (e != cudaSuccess) {
         set_error("bf_nufft_prepare: upload failed: %s", cudaGetErrorString(e));
@@ -663,7 +691,7 @@ bf_status nufft_apply_ws(bf_plan* p, const void* F, int64_t m, void* G, void* st
         InterpArgs ia{H, s->pa, s->W, s->p0, (float2*)G, s->N, s->n, m, Mc, s->ra, s->msp};
         const int64_t ctas = (s->N / kTile) * ((m + 31) / 32);
         ProfScope ps("nufft_interp", st);
-        nufft_interp<<<(unsigned)ctas, kNuThreads, 0, st>>>(ia);
+        nufft_interp<<<(unsigned)ctas, kNuThreads, kInterpSmem, st>>>(ia);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {
