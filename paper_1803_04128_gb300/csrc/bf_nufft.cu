@@ -341,11 +341,11 @@ __global__ void __launch_bounds__(kNuThreads, 3) nufft_interp(const InterpArgs A
                 const float2* src = A.H + (int64_t)h * A.n * A.Mc + k * A.m + c0;
                 const int pl = s_pT[h] + s_tlo[h];
                 if ((A.m & 1) == 0) {  // even m: every (row, column pair) is 16-byte aligned
-                    for (int e = threadIdx.x; e < spanT * 16; e += kNuThreads) {
-                        const int pp = e >> 4, cc = 2 * (e & 15);
-                        const bool ok = c0 + cc < A.m;
-                        nu_cp16(&Hs[pp][cc], src + (int64_t)((pl + pp) & nmask) * A.Mc + (ok ? cc : 0), ok);
-                    }
+                    const int cc = 2 * (threadIdx.x & 15);
+                    const bool ok = c0 + cc < A.m;
+                    const float2* sc = src + (ok ? cc : 0);
+                    for (int pp = threadIdx.x >> 4; pp < spanT; pp += kNuThreads / 16)
+                        nu_cp16(&Hs[pp][cc], sc + (int64_t)((pl + pp) & nmask) * A.Mc, ok);
                 } else {
                     for (int e = threadIdx.x; e < spanT * 32; e += kNuThreads) {
                         const int pp = e >> 5, cc = e & 31;
@@ -373,12 +373,13 @@ __global__ void __launch_bounds__(kNuThreads, 3) nufft_interp(const InterpArgs A
         if (k == 0 && tiled && span <= kSpanMax) {
             // the warp's weights for half h: Wd = 0, then each target's 2 msp weights
             // (contiguous in W for the run: one coalesced read) at rows Rel[t] .. of its span
-            for (int e = lane; e < kSpanMax * kRun; e += 32) (&Wd[0][0])[e] = 0.f;
+            for (int e = lane; e < kSpanMax * kRun / 4; e += 32)
+                reinterpret_cast<float4*>(&Wd[0][0])[e] = make_float4(0.f, 0.f, 0.f, 0.f);
             __syncwarp();
-            const float* Wr = A.W + (h * A.N + i0) * w2;
-            for (int e = lane; e < kRun * w2; e += 32) {
-                const int t = e / w2, q = e - t * w2;
-                Wd[Rel[t] + q][t] = __ldg(Wr + e);
+            {   // lane: target t = lane / 4, weights q = lane % 4, + 4, ...
+                const int t = lane >> 2, rt = Rel[t];
+                const float* Wr = A.W + (h * A.N + i0 + t) * w2;
+                for (int q = lane & 3; q < w2; q += 4) Wd[rt + q][t] = __ldg(Wr + q);
             }
             __syncwarp();
         }
