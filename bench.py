@@ -625,7 +625,8 @@ def run_batched(args, w, rank, world, local, steps=None, warmup=None):
            "t_factor_s": round(t_factor, 2), "t_autotune_s": round(t_tune, 2),
            "tile_shapes": [dict(api.tile_shapes(plans[N], m), N=N, m=m) for N, m in shapes],
            "batch_mode": {"chosen": mode, "ms_mode0_one_persistent_launch": mode_ms[0],
-                          "ms_mode1_front_and_back_launches": mode_ms[1]},
+                          "ms_mode1_front_and_back_launches": mode_ms[1],
+                          "ms_mode2_own_applies_on_4_streams": mode_ms[2]},
            "sequential_single_op_ms_per_step": seq_ms, "batched_ms_per_step": ms_max / steps,
            "speedup_batched_vs_sequential": seq_ms / (ms_max / steps),
            "hbm_frac_of_measured": bytes_apply / (ms_max / steps * 1e-3) / (peaks["hbm_gbs"] * 1e9),

@@ -70,15 +70,22 @@ bf_status bf_batch_debug_hold(bf_batch* batch, int on);
  *   1: two launches, one over every operator's front tiles and one over every back tile,
  *      one CTA per work item, operators by decreasing work, each launch with its own
  *      shared-memory size and the tile bodies inlined (no waits: bf_batch_debug_hold has
- *      no effect).
+ *      no effect);
+ *   2: each operator's own fused apply (the kernels and tile shapes bf_apply uses for it)
+ *      on one of four streams forked from and joined to the caller's stream, operators by
+ *      decreasing work, each on the stream with the least work so far, so that one
+ *      operator's last wave runs beside the next ones' tiles (no waits either).
  * Changing the mode drops a captured graph (capture again).  Errors: BF_ERR_ARG. */
 bf_status bf_batch_set_mode(bf_batch* batch, int mode);
 bf_status bf_batch_get_mode(const bf_batch* batch, int* mode);
-/* Time both modes on `stream` (one warm-up and three timed runs each; the operators' G
- * are written) and keep the faster.  *mode_out (nullable) receives it, ms_out (nullable,
- * 2 doubles) the mean milliseconds of modes 0 and 1.  Synchronises the stream; call it
- * before bf_batch_capture_graph. */
+/* Time the three modes on `stream` (one warm-up and three timed runs each; the operators'
+ * G are written) and keep the fastest.  *mode_out (nullable) receives it, ms_out
+ * (nullable, 2 doubles) the mean milliseconds of modes 0 and 1 (all three:
+ * bf_batch_tune_times).  Synchronises the stream; call it before bf_batch_capture_graph. */
 bf_status bf_batch_tune(bf_batch* batch, void* stream, int* mode_out, double* ms_out);
+/* The mean milliseconds of modes 0, 1, 2 from the last bf_batch_tune (zeros before one):
+ * the first min(n, 3) into ms.  Errors: BF_ERR_ARG. */
+bf_status bf_batch_tune_times(const bf_batch* batch, double* ms, int n);
 
 void bf_batch_destroy(bf_batch* batch); /* NULL-safe */
 

@@ -130,6 +130,7 @@ _SIGS = {
     "bf_batch_set_mode": (ctypes.c_int, [_P, ctypes.c_int]),
     "bf_batch_get_mode": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "bf_batch_tune": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "bf_batch_tune_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "bf_apply_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _P]),
     "bf_apply_batched_release": (None, []),
     "bf_shard_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),

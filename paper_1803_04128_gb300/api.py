@@ -405,11 +405,13 @@ class Batch:
         return v.value
 
     def tune(self, stream=None):
-        """Time both modes and keep the faster; returns (mode, [ms of mode 0, ms of mode 1])."""
+        """Time the three modes and keep the fastest; returns (mode, [ms of modes 0, 1, 2])."""
         mo = ctypes.c_int()
         ms = (ctypes.c_double * 2)()
         L.check(self._lib.bf_batch_tune(self._h, _stream_ptr(stream), ctypes.byref(mo), ms), "bf_batch_tune")
-        return mo.value, [ms[0], ms[1]]
+        al = (ctypes.c_double * 3)()
+        L.check(self._lib.bf_batch_tune_times(self._h, al, 3), "bf_batch_tune_times")
+        return mo.value, [al[0], al[1], al[2]]
 
     def debug_hold(self, on=True):
         L.check(self._lib.bf_batch_debug_hold(self._h, int(on)), "bf_batch_debug_hold")

@@ -12,11 +12,31 @@
 
 using namespace bfi;
 
+namespace {
+constexpr int kStreams = 4;  // mode 2's streams
+// one operator of mode 2: its own fused apply, as bf_apply launches it
+struct SoloItem {
+    const DevBlock* B = nullptr;
+    const float2* F = nullptr;
+    float2* G = nullptr;
+    int64_t m = 0;
+    float2* ws = nullptr;
+    int hint = 0;
+    int stream = 0;
+};
+}  // namespace
+
 struct bf_batch {
     int device = 0;
     int r = 0;
     BatchLaunch bl;
     std::vector<BatchItem> items;
+    // mode 2: the operators' own applies on kStreams streams (decreasing work, each on the
+    // stream with the least work so far), forked from and joined to the caller's stream
+    std::vector<SoloItem> solo;
+    cudaStream_t ss[kStreams] = {};
+    cudaEvent_t fork = nullptr, join[kStreams] = {};
+    double tune_ms[3] = {0, 0, 0};
     void* dmem = nullptr;  // items, offsets, counter/done, err
     size_t dmem_bytes = 0;
     void* ws = nullptr;
@@ -42,6 +62,11 @@ void free_batch(bf_batch* b)
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    for (int k = 0; k < kStreams; ++k) {
+        if (b->ss[k]) cudaStreamDestroy(b->ss[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->dmem) cudaFree(b->dmem);
     if (b->ws) cudaFree(b->ws);
     delete b;
@@ -49,11 +74,24 @@ void free_batch(bf_batch* b)
 
 bf_status enqueue(bf_batch* b, cudaStream_t st)
 {
+    cudaError_t e;
+    if (b->bl.mode == 2) {
+        if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return cuda_fail("bf_batch: fork", e);
+        for (int k = 0; k < kStreams; ++k)
+            if ((e = cudaStreamWaitEvent(b->ss[k], b->fork, 0)) != cudaSuccess) return cuda_fail("bf_batch: fork", e);
+        for (const SoloItem& it : b->solo)
+            if ((e = launch_fused_f32(*it.B, it.F, it.m, it.G, 0, it.ws, b->ss[it.stream], it.hint)) != cudaSuccess)
+                return cuda_fail("bf_batch: launch", e);
+        for (int k = 0; k < kStreams; ++k)
+            if ((e = cudaEventRecord(b->join[k], b->ss[k])) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(st, b->join[k], 0)) != cudaSuccess)
+                return cuda_fail("bf_batch: join", e);
+        return BF_OK;
+    }
     if (b->bl.grid < 1) {
         set_error("bf_batch: no persistent grid configured");
         return BF_ERR_STATE;
     }
-    cudaError_t e;
     if (b->bl.mode == 1) {
         e = batch_phases_f32(b->r, b->bl, st, false);
         if (e != cudaSuccess) return cuda_fail("bf_batch: phase launches", e);
@@ -131,8 +169,11 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
     for (int i = 0; i < n; ++i) {
         const DevBlock& B = in[i].plan->dev->blocks[0];
         ws_off[(size_t)i] = ws_total;
-        ws_total += (std::max(fused_f32_ws_bytes(B.g, in[i].m, in[i].plan->mr_hint(in[i].m), false),
-                              fused_f32_ws_bytes(B.g, in[i].m, 0, false)) + 255) & ~(size_t)255;
+        // the persistent kernels' one pass per side, and (mode 2) the plan's own apply, whose
+        // long level ranges may run in passes
+        const int hint = in[i].plan->mr_hint(in[i].m);
+        ws_total += (std::max({fused_f32_ws_bytes(B.g, in[i].m, hint, false), fused_f32_ws_bytes(B.g, in[i].m, 0, false),
+                               fused_f32_ws_bytes(B.g, in[i].m, hint)}) + 255) & ~(size_t)255;
     }
     if ((e = cudaMalloc(&b->ws, std::max<size_t>(ws_total, 256))) != cudaSuccess) {
         free_batch(b);
@@ -174,6 +215,36 @@ bf_status bf_batch_create(const bf_batch_item* in, int n, bf_batch** out)
         const BatchItem &a = b->items[(size_t)x], &c = b->items[(size_t)y];
         return a.nfront + a.nback > c.nfront + c.nback;
     });
+    // mode 2: operators by decreasing work, each on the stream with the least work so far
+    {
+        int64_t load[kStreams] = {};
+        b->solo.resize((size_t)n);
+        for (int k = 0; k < n; ++k) {
+            const int i = ord[(size_t)k];
+            const BatchItem& bi = b->items[(size_t)i];
+            int best = 0;
+            for (int q = 1; q < kStreams; ++q)
+                if (load[q] < load[best]) best = q;
+            load[best] += bi.nfront + bi.nback;
+            SoloItem& so = b->solo[(size_t)k];
+            so.B = &in[i].plan->dev->blocks[0];
+            so.F = (const float2*)in[i].F;
+            so.G = (float2*)in[i].G;
+            so.m = in[i].m;
+            so.ws = (float2*)((unsigned char*)b->ws + ws_off[(size_t)i]);
+            so.hint = in[i].plan->mr_hint(in[i].m);
+            so.stream = best;
+        }
+        e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (int q = 0; q < kStreams && e == cudaSuccess; ++q) {
+            e = cudaStreamCreateWithFlags(&b->ss[q], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[q], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            free_batch(b);
+            return cuda_fail("bf_batch_create: streams", e);
+        }
+    }
     std::vector<int64_t> off_f((size_t)n + 1, 0), off_b((size_t)n + 1, 0);
     for (int k = 0; k < n; ++k) {
         off_f[(size_t)k + 1] = off_f[(size_t)k] + b->items[(size_t)ord[(size_t)k]].nfront;
@@ -349,8 +420,8 @@ bf_status bf_batch_get_info(const bf_batch* b, int64_t* work_items, int* grid, i
 
 bf_status bf_batch_set_mode(bf_batch* b, int mode)
 {
-    if (!b || (mode != 0 && mode != 1)) {
-        set_error("bf_batch_set_mode: NULL batch or mode not 0 / 1");
+    if (!b || mode < 0 || mode > 2) {
+        set_error("bf_batch_set_mode: NULL batch or mode not 0, 1 or 2");
         return BF_ERR_ARG;
     }
     if (b->bl.mode != mode && b->exec) {
@@ -388,10 +459,10 @@ bf_status bf_batch_tune(bf_batch* b, void* stream, int* mode_out, double* ms_out
         return cuda_fail("bf_batch_tune: events", e);
     }
     const int keep = b->bl.mode;
-    double best = 1e30, ms[2] = {0, 0};
+    double best = 1e30, ms[3] = {0, 0, 0};
     int bm = keep;
     bf_status rs = BF_OK;
-    for (int mode = 0; mode < 2 && rs == BF_OK; ++mode) {
+    for (int mode = 0; mode < 3 && rs == BF_OK; ++mode) {
         b->bl.mode = mode;
         double tot = 0;
         for (int rep = 0; rep < 4 && rs == BF_OK; ++rep) {  // one warm-up, three timed
@@ -414,12 +485,23 @@ bf_status bf_batch_tune(bf_batch* b, void* stream, int* mode_out, double* ms_out
     b->bl.mode = keep;
     if (rs != BF_OK) return rs;
     rs = bf_batch_set_mode(b, bm);
+    for (int k = 0; k < 3; ++k) b->tune_ms[k] = ms[k];
     if (mode_out) *mode_out = bm;
     if (ms_out) {
         ms_out[0] = ms[0];
         ms_out[1] = ms[1];
     }
     return rs;
+}
+
+bf_status bf_batch_tune_times(const bf_batch* b, double* ms, int n)
+{
+    if (!b || !ms || n < 1) {
+        set_error("bf_batch_tune_times: NULL argument or n < 1");
+        return BF_ERR_ARG;
+    }
+    for (int k = 0; k < n && k < 3; ++k) ms[k] = b->tune_ms[k];
+    return BF_OK;
 }
 
 bf_status bf_batch_set_spin_limit(bf_batch* b, long long polls)

@@ -177,7 +177,7 @@ def test_apply_batched_rejects_bad_items():
 
 def test_two_phase_mode_is_bitwise_the_same_and_tunable():
     # mode 1 (a front launch and a back launch over every operator) against mode 0 and the
-    # single applies, eager and replayed from a graph; the tuner keeps one of the two
+    # single applies, eager and replayed from a graph; the tuner keeps one of the three modes
     ops = make_ops([(4096, 3), (16384, 40), (2048, 1), (65536, 17), (8192, 128)], seed=40)
     b = api.Batch(ops)
     assert b.mode() == 0
@@ -197,7 +197,29 @@ def test_two_phase_mode_is_bitwise_the_same_and_tunable():
     for (plan, F, G), r in zip(ops, ref):
         assert torch.equal(G, r)
     mode, ms = b.tune()
-    assert mode in (0, 1) and ms[0] > 0 and ms[1] > 0 and b.mode() == mode
+    assert mode in (0, 1, 2) and min(ms) > 0 and b.mode() == mode
     for (plan, F, G), r in zip(ops, ref):
         assert torch.equal(G, r)
     b.close()
+
+
+def test_stream_mode_is_bitwise_the_same_and_replays():
+    # mode 2 (each operator's own apply on four forked streams) against the single applies,
+    # run directly and replayed from a CUDA graph (the fork and join are captured)
+    ops = make_ops(SHAPES + [(65536, 5)], seed=40)
+    b = api.Batch(ops)
+    b.set_mode(2)
+    assert b.mode() == 2
+    b.run()
+    assert b.status() == 0
+    for plan, F, G in ops:
+        assert torch.equal(G, plan.apply(F, prec=api.F32))
+    s = torch.cuda.Stream()
+    b.capture(s)
+    for _, _, G in ops:
+        G.fill_(float("nan"))
+    b.replay(s)
+    b.replay(s)
+    assert b.status(s) == 0
+    for plan, F, G in ops:
+        assert torch.equal(G, plan.apply(F, prec=api.F32))
