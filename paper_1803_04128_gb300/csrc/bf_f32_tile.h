@@ -48,6 +48,15 @@ __device__ __forceinline__ void cfmaf(float2& acc, float2 a, float2 b)
     acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
     acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
 }
+// acc += w v for a real weight and a complex value as one packed two-lane FMA: the same two
+// IEEE fused multiply-adds as two fmaf calls (bitwise the same), in one issue slot
+__device__ __forceinline__ void rcfma(float2& acc, float w, float2 v)
+{
+    asm("{\n.reg .b64 wa, vb, ac;\nmov.b64 wa, {%2, %2};\nmov.b64 vb, {%3, %4};\nmov.b64 ac, {%0, %1};\n"
+        "fma.rn.f32x2 ac, wa, vb, ac;\nmov.b64 {%0, %1}, ac;\n}"
+        : "+f"(acc.x), "+f"(acc.y)
+        : "f"(w), "f"(v.x), "f"(v.y));
+}
 __device__ __forceinline__ unsigned brev(unsigned v, int bits)
 {
     return bits == 0 ? 0u : (__brev(v) >> (32 - bits));
@@ -216,10 +225,8 @@ __device__ __forceinline__ void h_item(float2* x0, float2* x1, int CTp, const fl
                 for (int q = 0; q < 4; ++q) {
                     const int t = 4 * t4 + q;
                     if (t < R) {
-                        o0[t].x = fmaf(ww[q], u0.x, o0[t].x);
-                        o0[t].y = fmaf(ww[q], u0.y, o0[t].y);
-                        o1[t].x = fmaf(ww[q], u1.x, o1[t].x);
-                        o1[t].y = fmaf(ww[q], u1.y, o1[t].y);
+                        rcfma(o0[t], ww[q], u0);
+                        rcfma(o1[t], ww[q], u1);
                     }
                 }
             }
@@ -260,10 +267,8 @@ __device__ __forceinline__ void g_item(float2* x0, float2* x1, int CTp, const fl
                 for (int q = 0; q < 4; ++q) {
                     const int t = 4 * t4 + q;
                     if (t < R) {
-                        w0[t].x = fmaf(ww[q], nu0[s].x, w0[t].x);
-                        w0[t].y = fmaf(ww[q], nu0[s].y, w0[t].y);
-                        w1[t].x = fmaf(ww[q], nu1[s].x, w1[t].x);
-                        w1[t].y = fmaf(ww[q], nu1[s].y, w1[t].y);
+                        rcfma(w0[t], ww[q], nu0[s]);
+                        rcfma(w1[t], ww[q], nu1[s]);
                     }
                 }
             }
@@ -501,8 +506,7 @@ __device__ __forceinline__ void front_tile(const FrontArgs& A, int64_t work, uns
                     for (int q = 0; q < 4; ++q) {
                         const int t = 4 * t4 + q;
                         if (t < R) {
-                            acc[t].x = fmaf(ww[q], z.x, acc[t].x);
-                            acc[t].y = fmaf(ww[q], z.y, acc[t].y);
+                            rcfma(acc[t], ww[q], z);
                         }
                     }
                 }
@@ -708,8 +712,7 @@ __device__ __forceinline__ void back_tile(const BackArgs& A, int64_t work, unsig
                                 for (int q = 0; q < 4; ++q) {
                                     const int s = 4 * s4 + q;
                                     if (s < R) {
-                                        w.x = fmaf(mm[q], v[s].x, w.x);
-                                        w.y = fmaf(mm[q], v[s].y, w.y);
+                                        rcfma(w, mm[q], v[s]);
                                     }
                                 }
                             }
