@@ -82,6 +82,15 @@ __device__ __forceinline__ float2 nu_cmul(float2 a, float2 b)
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
+// (u + t, u - t) on packed two-lane adds: the same IEEE additions as the scalar forms
+__device__ __forceinline__ void nu_bfly(float2 u, float2 t, float2& p, float2& q)
+{
+    asm("{\n.reg .b64 a, b, c, d;\nmov.b64 a, {%4, %5};\nmov.b64 b, {%6, %7};\n"
+        "add.rn.f32x2 c, a, b;\nsub.rn.f32x2 d, a, b;\nmov.b64 {%0, %1}, c;\nmov.b64 {%2, %3}, d;\n}"
+        : "=f"(p.x), "=f"(p.y), "=f"(q.x), "=f"(q.y)
+        : "f"(u.x), "f"(u.y), "f"(t.x), "f"(t.y));
+}
+
 // One radix-2 stage of butterflies of span LEN (twiddles e^{2 pi i j / LEN}), then the next;
 // a template recursion, so that every register index is a compile-time constant.
 template <int R, int LEN>
@@ -100,8 +109,7 @@ struct DftStage {
                 else if (tw == 2 * kq) t = make_float2(-t.x, -t.y);
                 else if (tw == 3 * kq) t = make_float2(t.y, -t.x);
                 else if (tw != 0) t = nu_cmul(c_w32[tw], t);
-                v[s0 + j] = make_float2(u.x + t.x, u.y + t.y);
-                v[s0 + j + LEN / 2] = make_float2(u.x - t.x, u.y - t.y);
+                nu_bfly(u, t, v[s0 + j], v[s0 + j + LEN / 2]);
             }
         }
         DftStage<R, 2 * LEN>::run(v);
