@@ -3,7 +3,8 @@
  * autotuner of the butterfly-factorisation library (see bf.h for conventions).
  *
  * A batch applies many operators g_i = K_i f_i (each a plan of bf.h, of its own
- * N_i, with its own m_i right-hand sides) in ONE persistent launch: every CTA
+ * N_i, with its own m_i right-hand sides).  By default (mode 0, bf_batch_set_mode
+ * has the others) it does so in ONE persistent launch: every CTA
  * takes work items from an atomic counter in the order [front tiles of op 0]
  * [back tiles of op 0] [front tiles of op 1] ... (front = V, H levels and
  * switch; back = G levels and U); a back tile of operator i waits (bounded)
@@ -34,7 +35,9 @@ typedef struct {
 } bf_batch_item;
 
 /* Build a batch (uploads plans, allocates one workspace per item and the work
- * list).  All plans must share r and device and be unsplit (split == 1).
+ * list).  All plans must share r and device and be unsplit (split == 1).  The
+ * batch keeps device addresses of the plans' factors: the plans must stay alive
+ * and uploaded, and must not be refactored, while the batch exists.
  * Errors: BF_ERR_ARG, BF_ERR_UNSUPPORTED, BF_ERR_NOMEM, BF_ERR_CUDA. */
 bf_status bf_batch_create(const bf_batch_item* items, int n, bf_batch** out);
 
