@@ -1016,7 +1016,7 @@ def run_single(args, w, rank, world, local, steps, warmup, plan=None, sides=True
 
 def side_lines(args, rank, world, local):
     """The other configurations, measured in the default run beside the headline:
-    the plain FP64 per-stage form at the headline's shape, config 3 (split-BF16 and
+    the plain FP64 per-stage form at the headline's shape, config 1, config 3 (split-BF16 and
     FP32 on the same plan), config 4 (one batched launch against one by one) and
     config 5 (serving).  Each is a full JSON object with its own roofline and error
     against the FP64 oracle on sampled rows."""
@@ -1029,6 +1029,9 @@ def side_lines(args, rank, world, local):
     w["desc"] = ("plain FP64 per-stage form (one launch per stage, CUDA-graph replay) at the fio2 shape: "
                  "N=65536, m=64, eps=1e-6")
     out["fp64_plain_fio2"] = run_single(args, w, rank, world, local, st, wu, sides=False)
+    # config 1: the plain FP64 form at N = 1024, one right-hand side (every row against the oracle)
+    out["fio1"] = run_single(args, dict(WORKLOADS["fio1"], name="fio1", err_rows=1024), rank, world, local, 50, wu,
+                             sides=False)
     # config 3: split-BF16 tensor cores (V and U at level 5) and FP32 (the built-in level) on
     # the same operator at the same eps
     w3 = dict(WORKLOADS["fio3"], name="fio3", factor_on_device=True, err_rows=24)
