@@ -97,11 +97,18 @@ struct Op {
     std::deque<uint64_t> pending;
 };
 
+// A single large NUFFT request runs in kChunks column chunks, so that its host copies overlap
+// its kernels: chunk k's copy in, its apply and its copy out are on three streams.
+constexpr int kChunks = 2;
+constexpr int64_t kChunkMinCols = 32, kChunkMinUnits = (int64_t)1 << 20;
+
 struct Slot {
     cudaStream_t st = nullptr;
     bool hi = false;  // highest-priority stream, small batches only
     cudaEvent_t ev = nullptr;
     cudaEvent_t ev0 = nullptr;  // recorded before the batch's first copy (device-time accounting)
+    cudaStream_t up = nullptr, down = nullptr;           // chunked requests: copies in / out
+    cudaEvent_t in_ready[kChunks] = {}, done[kChunks] = {}, joined = nullptr;
     void* F = nullptr;
     void* G = nullptr;
     void* ws = nullptr;
@@ -178,6 +185,38 @@ bf_status enqueue_batch(bf_server* s, Slot& sl, Op& op, std::vector<Req*>& rs)
     const size_t elt = s->elt;
     cudaError_t e = cudaEventRecord(sl.ev0, sl.st);
     if (e != cudaSuccess) return BF_ERR_CUDA;
+    if (op.nufft && rs.size() == 1 && M >= kChunkMinCols && M % kChunks == 0 && N * M >= kChunkMinUnits) {
+        // one request in column chunks: every column is computed on its own, so the chunks
+        // give the request's result exactly; the copies of one chunk overlap the kernels of
+        // the other (strided host rows of M / kChunks elements)
+        const Req* r = rs[0];
+        const int64_t mc = M / kChunks;
+        const size_t w = (size_t)mc * elt, pitch = (size_t)M * elt, blk = (size_t)N * w;
+        if ((e = cudaStreamWaitEvent(sl.up, sl.ev0, 0)) != cudaSuccess) return BF_ERR_CUDA;
+        for (int k = 0; k < kChunks; ++k) {
+            if ((e = cudaMemcpy2DAsync((unsigned char*)sl.F + k * blk, w, (const unsigned char*)r->F + k * w, pitch, w,
+                                       (size_t)N, cudaMemcpyHostToDevice, sl.up)) != cudaSuccess ||
+                (e = cudaEventRecord(sl.in_ready[k], sl.up)) != cudaSuccess)
+                return BF_ERR_CUDA;
+        }
+        for (int k = 0; k < kChunks; ++k) {
+            if ((e = cudaStreamWaitEvent(sl.st, sl.in_ready[k], 0)) != cudaSuccess) return BF_ERR_CUDA;
+            const bf_status st = nufft_apply_ws(op.plan, (unsigned char*)sl.F + k * blk, mc,
+                                                (unsigned char*)sl.G + k * blk, sl.st, sl.ws, sl.ws_bytes);
+            if (st != BF_OK) return st;
+            if ((e = cudaEventRecord(sl.done[k], sl.st)) != cudaSuccess) return BF_ERR_CUDA;
+        }
+        for (int k = 0; k < kChunks; ++k) {
+            if ((e = cudaStreamWaitEvent(sl.down, sl.done[k], 0)) != cudaSuccess ||
+                (e = cudaMemcpy2DAsync((unsigned char*)r->G + k * w, pitch, (unsigned char*)sl.G + k * blk, w, w,
+                                       (size_t)N, cudaMemcpyDeviceToHost, sl.down)) != cudaSuccess)
+                return BF_ERR_CUDA;
+        }
+        if ((e = cudaEventRecord(sl.joined, sl.down)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(sl.st, sl.joined, 0)) != cudaSuccess || (e = cudaEventRecord(sl.ev, sl.st)) != cudaSuccess)
+            return BF_ERR_CUDA;
+        return BF_OK;
+    }
     // staged: each request's rows in one contiguous copy into sl.G (free until the apply
     // writes it), interleaved into sl.F; after the apply, G de-interleaved into sl.F (free
     // again) and copied out per request
@@ -277,7 +316,9 @@ void scheduler(bf_server* s)
                         it->second.status = st;
                     }
                 }
+                cudaStreamSynchronize(sl.up);
                 cudaStreamSynchronize(sl.st);
+                cudaStreamSynchronize(sl.down);
                 sl.reqs.clear();
                 sl.busy = false;
                 s->cv_done.notify_all();
@@ -462,12 +503,21 @@ bf_status bf_server_start(bf_server* s)
         sl.hi = (int)i < nhi;
         cudaError_t e;
         if ((e = cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, sl.hi ? pri_hi : pri_lo)) != cudaSuccess ||
+            (e = cudaStreamCreateWithPriority(&sl.up, cudaStreamNonBlocking, sl.hi ? pri_hi : pri_lo)) != cudaSuccess ||
+            (e = cudaStreamCreateWithPriority(&sl.down, cudaStreamNonBlocking, sl.hi ? pri_hi : pri_lo)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&sl.joined, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreate(&sl.ev)) != cudaSuccess || (e = cudaEventCreate(&sl.ev0)) != cudaSuccess ||
             (e = cudaMalloc(&sl.F, slab)) != cudaSuccess || (e = cudaMalloc(&sl.G, slab)) != cudaSuccess ||
             (e = cudaMalloc(&sl.ws, ws)) != cudaSuccess) {
             set_error("bf_server_start: slot allocation: %s", cudaGetErrorString(e));
             return e == cudaErrorMemoryAllocation ? BF_ERR_NOMEM : BF_ERR_CUDA;
         }
+        for (int k = 0; k < kChunks; ++k)
+            if ((e = cudaEventCreateWithFlags(&sl.in_ready[k], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&sl.done[k], cudaEventDisableTiming)) != cudaSuccess) {
+                set_error("bf_server_start: slot events: %s", cudaGetErrorString(e));
+                return BF_ERR_CUDA;
+            }
         sl.ws_bytes = ws;
     }
     if (cudaEventCreate(&s->base) != cudaSuccess || cudaEventRecord(s->base, s->slots[0].st) != cudaSuccess ||
@@ -648,12 +698,21 @@ void bf_server_destroy(bf_server* s)
     if (s->thr.joinable()) s->thr.join();
     cudaSetDevice(s->opt.device);
     for (auto& sl : s->slots) {
+        if (sl.up) cudaStreamSynchronize(sl.up);
         if (sl.st) cudaStreamSynchronize(sl.st);
+        if (sl.down) cudaStreamSynchronize(sl.down);
         cudaFree(sl.F);
         cudaFree(sl.G);
         cudaFree(sl.ws);
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.ev0) cudaEventDestroy(sl.ev0);
+        for (int k = 0; k < kChunks; ++k) {
+            if (sl.in_ready[k]) cudaEventDestroy(sl.in_ready[k]);
+            if (sl.done[k]) cudaEventDestroy(sl.done[k]);
+        }
+        if (sl.joined) cudaEventDestroy(sl.joined);
+        if (sl.up) cudaStreamDestroy(sl.up);
+        if (sl.down) cudaStreamDestroy(sl.down);
         if (sl.st) cudaStreamDestroy(sl.st);
     }
     if (s->base) cudaEventDestroy(s->base);
