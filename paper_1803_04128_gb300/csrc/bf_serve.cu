@@ -179,16 +179,19 @@ void reap(bf_server* s)
 }
 
 // Enqueue one batch on a slot (called without the lock; the slot is owned).
-bf_status enqueue_batch(bf_server* s, Slot& sl, Op& op, std::vector<Req*>& rs)
+bf_status enqueue_batch(bf_server* s, Slot& sl, Op& op, std::vector<Req*>& rs, bool idle_queue)
 {
     const int64_t N = op.N, M = sl.cols;
     const size_t elt = s->elt;
     cudaError_t e = cudaEventRecord(sl.ev0, sl.st);
     if (e != cudaSuccess) return BF_ERR_CUDA;
-    if (op.nufft && rs.size() == 1 && M >= kChunkMinCols && M % kChunks == 0 && N * M >= kChunkMinUnits) {
+    if (idle_queue && op.nufft && rs.size() == 1 && M >= kChunkMinCols && M % kChunks == 0 &&
+        N * M >= kChunkMinUnits) {
         // one request in column chunks: every column is computed on its own, so the chunks
         // give the request's result exactly; the copies of one chunk overlap the kernels of
-        // the other (strided host rows of M / kChunks elements)
+        // the other (strided host rows of M / kChunks elements).  Only with no other request
+        // waiting: under a backlog the other slots' work overlaps the copies already, and
+        // the NUFFT costs more per column at half the columns.
         const Req* r = rs[0];
         const int64_t mc = M / kChunks;
         const size_t w = (size_t)mc * elt, pitch = (size_t)M * elt, blk = (size_t)N * w;
@@ -303,8 +306,10 @@ void scheduler(bf_server* s)
             sl.cols = cols;
             s->launches += 1;
             s->batch_cols += cols;
+            bool idle_queue = true;
+            for (const Op& o : s->ops) idle_queue = idle_queue && o.pending.empty();
             lk.unlock();  // Req objects stay put: only this thread erases them after completion
-            bf_status st = enqueue_batch(s, sl, op, rs);
+            bf_status st = enqueue_batch(s, sl, op, rs, idle_queue);
             lk.lock();
             if (st != BF_OK) {
                 const auto now = Clock::now();

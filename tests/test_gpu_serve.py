@@ -198,20 +198,23 @@ def test_batch_copies_keep_results_bitwise(prec, max_rhs, ms, n):
 
 
 def test_large_nufft_requests_in_column_chunks_are_bitwise_alone():
-    # a single NUFFT request of m >= 32 columns (N m >= 2^20) runs in two column chunks whose
-    # copies overlap the other chunk's kernels; every column is computed on its own, so the
-    # result is that of the request's nufft_apply alone, and small requests beside it too
+    # a single NUFFT request of m >= 32 columns (N m >= 2^20), with no other request waiting,
+    # runs in two column chunks whose copies overlap the other chunk's kernels; every column is
+    # computed on its own, so the result is that of the request's nufft_apply alone.  The first
+    # two requests go one at a time (chunked), the rest back to back (a queue: not chunked).
     N = 16384
     plan = api.Plan(N, eps=1e-6, phase_kind=L.PHASE_FIO, amp_kind=L.AMP_SMOOTH)
     srv = api.Server(n_slots=2, max_batch_rhs=64, method=1, n_priority_slots=0)
     op = srv.add(plan)
     srv.start()
     reqs = []
-    for k, m in enumerate((64, 64, 4, 64)):
+    for k, m in enumerate((64, 32, 64, 4, 64)):
         F = torch.from_numpy(inputs.complex_gaussian(N, m, seed=700 + k).astype(np.complex64)).pin_memory()
         G = torch.full_like(F, float("nan")).pin_memory()
         reqs.append((F, G, srv.submit(op, F, G)))
-    for F, G, rid in reqs:
+        if k < 2:
+            srv.wait(reqs[-1][2], 120000.0)
+    for F, G, rid in reqs[2:]:
         srv.wait(rid, 120000.0)
     for F, G, _ in reqs:
         assert torch.equal(G, plan.nufft_apply(F.cuda()).cpu())
