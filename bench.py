@@ -218,6 +218,15 @@ def ncu_traffic(kernel, workload, m):
     return e.get("dram_bytes_per_launch")
 
 
+def host_cores():
+    """Host cores this process may run on (a multi-process launcher's one-thread default
+    for OpenMP does not limit the timed CPU baseline, which rank 0 runs alone)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def cpu_oracle_rate(w, F, G_gpu, budget_s, max_rows=None):
     """Time the FP64 direct oracle on sampled rows (all m RHS); also the rel.
     error of the GPU result on those rows.  Returns a dict."""
@@ -226,6 +235,7 @@ def cpu_oracle_rate(w, F, G_gpu, budget_s, max_rows=None):
     from paper_1803_04128_gb300 import inputs
     N, m = w["N"], w["m"]
     kind = w["phase"]
+    od.set_threads(host_cores())
     # enough rows to keep every host thread busy, fewer for very long rows
     probe = inputs.sample_rows(N, int(min(N, 64, max(8, (1 << 28) // (N * m)))), seed=11)
     t0 = time.perf_counter()
@@ -255,6 +265,7 @@ def run_reference(args, w, rank, world):
     from oracle import direct as od
     from paper_1803_04128_gb300 import inputs
     F = inputs.complex_gaussian(w["N"], w["m"], seed=0)
+    od.set_threads(host_cores())
     rows_all = inputs.sample_rows(w["N"], 4096, seed=13)
     probe = rows_all[:4]
     t0 = time.perf_counter()

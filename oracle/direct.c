@@ -164,6 +164,18 @@ void oracle_amplitude(int amp, int64_t N, const int64_t* ii, const int64_t* jj, 
     for (int64_t k = 0; k < n; ++k) out[k] = amplitude(amp, N, ii[k], jj[k]);
 }
 
+/* the host threads of the oracle's parallel loops from now on, for calls made from this thread
+   (a launcher that pins each process to one thread still lets the timed baseline use all cores) */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

@@ -54,6 +54,8 @@ def _load():
                                             ctypes.c_int64, ctypes.c_int, dp]
             lib.oracle_amplitude.argtypes = [ctypes.c_int, ctypes.c_int64, i64p, i64p, ctypes.c_int64, dp]
             lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = None
             _lib = lib
     return _lib
 
@@ -127,3 +129,8 @@ def amplitude(amp, N, i, j):
 
 def num_threads():
     return int(_load().oracle_num_threads())
+
+
+def set_threads(n):
+    """Host threads of the oracle's parallel loops for later calls from this thread."""
+    _load().oracle_set_threads(int(n))
