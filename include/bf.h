@@ -231,7 +231,9 @@ bf_status bf_nufft_decide(const bf_plan* plan, int block, int r, int r_eps, int 
  * `stream`: three kernels (the deconvolution fused into the first pass of a
  * four-step inverse FFT, the second pass, the interpolation).  Uses a
  * workspace of 4 N r_alpha m c64 numbers owned by the plan, grown with
- * cudaMalloc when m grows (so: not inside stream capture for a new m).
+ * cudaMalloc when m grows (so: not inside stream capture for a new m).  Each
+ * column is computed on its own: a column's result is bitwise the same for
+ * any m and any neighbouring columns.
  * Errors: BF_ERR_ARG, BF_ERR_STATE (no bf_nufft_prepare), BF_ERR_NOMEM,
  * BF_ERR_CUDA.
  *
